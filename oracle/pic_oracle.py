@@ -1,0 +1,331 @@
+"""FP64 CPU oracle for the electrostatic PIC step -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+import this module.  The product path (the CUDA library and its Python
+binding) never calls it and shares no code with it.
+
+It restates, in plain numpy FP64, the scheme of Section 3 of the paper
+(arXiv 2205.11052) as this project reads it:
+
+  * Section 3.1, steps 1-4 (Eq. Vlasov, Eq. potential, Eq. momentum_eqn):
+    scatter -> Poisson solve -> gather -> push, electrons in a uniform
+    neutralising ion background (the k = 0 mode of the charge is dropped).
+  * Section 3.2: normalised units (q/m = -1, eps0 = 1); a cell-centred grid
+    with constant spacing h_d = L_d / N_d per axis, nodes at (g + 1/2) h;
+    cloud-in-cell (CIC) shape for scatter and gather; periodic in x, y, z;
+    FFT spectral solve; the synchronised Boris integrator giving x and v at
+    integer steps.
+
+Readings where the paper is silent (each is listed in the design notes):
+  * CIC base index i = floor(x/h - 1/2) mod N, fraction f = x/h - 1/2 - i.
+    A particle on a node puts all its weight on that node.
+  * The deposit produces the charge density rho_g = sum_p q_p W / h^3.
+  * Poisson: -Lap(phi) = rho with the continuous symbol |k|^2,
+    k_d = 2 pi m_d / L_d, m_d in FFT order [-N/2, N/2).  E = -grad(phi) taken
+    spectrally, E^_d = -i k_d rho^ / |k|^2, with the k = 0 mode and each
+    axis' Nyquist component of k_d set to zero (so E is real and the
+    real-space kernel is antisymmetric).
+  * Time stepping: drift-kick-drift.  x_h = x_n + dt/2 v_n; the kick is the
+    Boris rotation with E evaluated at x_h (self field plus the external
+    quadrupole); x_{n+1} = x_h + dt/2 v_{n+1}.  Field diagnostics therefore
+    refer to t_{n+1/2}.
+  * External quadrupole E_ext = wz2 * (-(x-cx)/2, -(y-cy)/2, (z-cz)), the
+    paper's Penning field written with its axial frequency squared wz2
+    (Section 4.3 has wz2 = 30/L).
+  * Uniform particle charge q_p = Q / N_p and mass m_p = q_p / (q/m).
+
+Every function below cites the passage it follows.  Nothing here is blocked,
+fused or reordered beyond what those passages state.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = [
+    "Grid",
+    "Params",
+    "cic_stencil",
+    "deposit",
+    "deposit_bruteforce",
+    "solve_field",
+    "gather",
+    "external_field",
+    "boris_kick",
+    "wrap",
+    "step",
+    "run",
+    "diagnostics",
+    "mode_coefficient",
+]
+
+
+@dataclasses.dataclass(frozen=True)
+class Grid:
+    """Periodic cell-centred grid on [0, L)^3 (Section 3.2)."""
+
+    n: tuple   # (Nx, Ny, Nz)
+    L: tuple   # (Lx, Ly, Lz)
+
+    @property
+    def h(self) -> np.ndarray:
+        return np.asarray(self.L, dtype=np.float64) / np.asarray(self.n, dtype=np.float64)
+
+    @property
+    def cell_volume(self) -> float:
+        h = self.h
+        return float(h[0] * h[1] * h[2])
+
+    @property
+    def shape(self) -> tuple:
+        """numpy shape of a field array: (Nz, Ny, Nx), x fastest."""
+        return (self.n[2], self.n[1], self.n[0])
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.n[0] * self.n[1] * self.n[2])
+
+
+@dataclasses.dataclass(frozen=True)
+class Params:
+    """Physical parameters of one run (Section 3.1 and Section 4)."""
+
+    dt: float
+    q_over_m: float = -1.0             # Section 3.2 normalisation
+    Q: float = -1.0                    # total electron charge Q_e
+    B: tuple = (0.0, 0.0, 0.0)         # uniform external magnetic field
+    wz2: float = 0.0                   # quadrupole strength (axial frequency squared)
+
+
+def wrap(x: np.ndarray, grid: Grid) -> np.ndarray:
+    """Periodic boundary condition in all directions (Section 3.2)."""
+    L = np.asarray(grid.L, dtype=np.float64)
+    y = np.mod(x, L)
+    return np.where(y >= L, y - L, y)
+
+
+# ---------------------------------------------------------------------------
+# scatter (Section 3.1 step 1; Section 3.2: cell-centred grid, CIC shape)
+# ---------------------------------------------------------------------------
+
+def cic_stencil(x: np.ndarray, grid: Grid):
+    """CIC stencil of each particle on the cell-centred grid.
+
+    Returns (nodes, weights): nodes is (N, 8) int64 linear node indices
+    g = i + Nx (j + Ny k), weights is (N, 8) float64, both ordered by the
+    corner bits (a, b, c) = (bit0, bit1, bit2) of the corner number.
+    """
+    h = grid.h
+    n = np.asarray(grid.n, dtype=np.int64)
+    s = x / h - 0.5                      # node g sits at (g + 1/2) h
+    base = np.floor(s)
+    f = s - base
+    base = base.astype(np.int64) % n
+    nodes = np.empty((x.shape[0], 8), dtype=np.int64)
+    weights = np.empty((x.shape[0], 8), dtype=np.float64)
+    for corner in range(8):
+        a, b, c = corner & 1, (corner >> 1) & 1, (corner >> 2) & 1
+        ix = (base[:, 0] + a) % n[0]
+        iy = (base[:, 1] + b) % n[1]
+        iz = (base[:, 2] + c) % n[2]
+        wx = f[:, 0] if a else 1.0 - f[:, 0]
+        wy = f[:, 1] if b else 1.0 - f[:, 1]
+        wz = f[:, 2] if c else 1.0 - f[:, 2]
+        nodes[:, corner] = ix + n[0] * (iy + n[1] * iz)
+        weights[:, corner] = wx * wy * wz
+    return nodes, weights
+
+
+def deposit(x: np.ndarray, grid: Grid, q) -> np.ndarray:
+    """Electron charge density rho_g = sum_p q_p W(x_g - x_p) / h^3.
+
+    Section 3.1 step 1 ("scatter") with the CIC shape of Section 3.2.
+    ``q`` is a scalar particle charge or an (N,) array of per-particle
+    weights (the latter is the transpose of ``gather``).  Returns an array of
+    shape (Nz, Ny, Nx).
+    """
+    nodes, w = cic_stencil(x, grid)
+    qq = np.broadcast_to(np.asarray(q, dtype=np.float64), (x.shape[0],))
+    rho = np.bincount(nodes.ravel(), weights=(w * qq[:, None]).ravel(),
+                      minlength=grid.n_nodes)
+    return (rho / grid.cell_volume).reshape(grid.shape)
+
+
+def deposit_bruteforce(x: np.ndarray, grid: Grid, q: float) -> np.ndarray:
+    """Independent CIC deposit for tiny cases: node-by-node tent functions.
+
+    rho_g = sum_p q Prod_d max(0, 1 - |minimage(x_g,d - x_p,d)| / h_d) / h^3,
+    evaluated with explicit loops over every particle and every node (no
+    base-index arithmetic), so it shares no step with ``deposit``.
+    """
+    h = grid.h
+    L = np.asarray(grid.L, dtype=np.float64)
+    nx, ny, nz = grid.n
+    rho = np.zeros(grid.shape, dtype=np.float64)
+    for p in range(x.shape[0]):
+        for kz in range(nz):
+            for jy in range(ny):
+                for ix in range(nx):
+                    node = np.array([(ix + 0.5) * h[0], (jy + 0.5) * h[1], (kz + 0.5) * h[2]])
+                    d = node - x[p]
+                    d = d - L * np.round(d / L)
+                    w = np.prod(np.maximum(0.0, 1.0 - np.abs(d) / h))
+                    rho[kz, jy, ix] += q * w
+    return rho / grid.cell_volume
+
+
+# ---------------------------------------------------------------------------
+# field solve (Section 3.1 step 2; Eq. potential; Section 3.2: FFT solver)
+# ---------------------------------------------------------------------------
+
+def _wavenumbers(grid: Grid):
+    """Per-axis integer mode numbers in FFT order and the k vectors."""
+    ks, kgrad = [], []
+    for d in range(3):
+        N = grid.n[d]
+        m = np.fft.fftfreq(N, d=1.0 / N)        # 0, 1, ..., -N/2, ..., -1 (integers)
+        k = 2.0 * math.pi * m / grid.L[d]
+        kg = k.copy()
+        if N % 2 == 0:
+            kg[m == -(N // 2)] = 0.0             # Nyquist: no derivative
+        ks.append(k)
+        kgrad.append(kg)
+    return ks, kgrad
+
+
+def solve_field(rho: np.ndarray, grid: Grid, return_potential: bool = False):
+    """E = -grad(phi) with -Lap(phi) = rho - rho_i (Eq. potential, eps0 = 1).
+
+    The uniform ion background rho_i only cancels the k = 0 mode, which is set
+    to zero.  Spectral: E^_d = -i k_d rho^ / |k|^2.  Returns E with shape
+    (3, Nz, Ny, Nx) (components x, y, z).
+    """
+    rho_hat = np.fft.fftn(rho)                   # axes (z, y, x)
+    ks, kgrad = _wavenumbers(grid)
+    KZ, KY, KX = np.meshgrid(ks[2], ks[1], ks[0], indexing="ij")
+    GZ, GY, GX = np.meshgrid(kgrad[2], kgrad[1], kgrad[0], indexing="ij")
+    k2 = KX ** 2 + KY ** 2 + KZ ** 2
+    k2[0, 0, 0] = 1.0
+    phi_hat = rho_hat / k2
+    phi_hat[0, 0, 0] = 0.0
+    E = np.empty((3,) + grid.shape, dtype=np.float64)
+    for d, G in enumerate((GX, GY, GZ)):
+        E[d] = np.fft.ifftn(-1j * G * phi_hat).real
+    if return_potential:
+        return E, np.fft.ifftn(phi_hat).real
+    return E
+
+
+def mode_coefficient(field: np.ndarray, m: tuple) -> complex:
+    """Fourier coefficient (1/N_g) sum_g F_g exp(-2 pi i m.g/N) of one mode."""
+    F = np.fft.fftn(field) / field.size
+    nz, ny, nx = field.shape
+    return complex(F[m[2] % nz, m[1] % ny, m[0] % nx])
+
+
+# ---------------------------------------------------------------------------
+# gather and push (Section 3.1 steps 3-4, Eq. momentum_eqn; Section 3.2)
+# ---------------------------------------------------------------------------
+
+def gather(x: np.ndarray, E: np.ndarray, grid: Grid) -> np.ndarray:
+    """Interpolate grid E to the particles with the scatter's CIC weights."""
+    nodes, w = cic_stencil(x, grid)
+    out = np.empty((x.shape[0], 3), dtype=np.float64)
+    for d in range(3):
+        Ed = E[d].ravel()
+        out[:, d] = np.sum(w * Ed[nodes], axis=1)
+    return out
+
+
+def external_field(x: np.ndarray, grid: Grid, wz2: float) -> np.ndarray:
+    """Quadrupole trap field of Section 4.3, centred in the box."""
+    c = 0.5 * np.asarray(grid.L, dtype=np.float64)
+    d = x - c
+    return wz2 * np.stack([-0.5 * d[:, 0], -0.5 * d[:, 1], d[:, 2]], axis=1)
+
+
+def boris_kick(v: np.ndarray, e: np.ndarray, q_over_m: float, B, dt: float) -> np.ndarray:
+    """One velocity update of Eq. momentum_eqn over dt by the Boris rotation.
+
+    Solves v1 = v0 + dt (q/m) [e + (v0 + v1)/2 x B] exactly: half electric
+    kick, rotation about B by angle 2 arctan(|q/m| |B| dt / 2), half kick.
+    """
+    B = np.asarray(B, dtype=np.float64)
+    vm = v + 0.5 * dt * q_over_m * e
+    t = 0.5 * dt * q_over_m * B
+    s = 2.0 * t / (1.0 + float(np.dot(t, t)))
+    vprime = vm + np.cross(vm, t)
+    vp = vm + np.cross(vprime, s)
+    return vp + 0.5 * dt * q_over_m * e
+
+
+# ---------------------------------------------------------------------------
+# one synchronised step and the diagnostics
+# ---------------------------------------------------------------------------
+
+def diagnostics(rho: np.ndarray, E: np.ndarray, v_new: np.ndarray, grid: Grid,
+                params: Params, n_particles: int, mode=(1, 0, 0), mode_comp=0) -> dict:
+    """Field energies int E_d^2 dV (Figs. Landau_damping_rate, TSI_BTI),
+    total charge, momentum and kinetic energy of the electrons."""
+    dV = grid.cell_volume
+    qp = params.Q / n_particles if n_particles else 0.0
+    mp = qp / params.q_over_m
+    out = {
+        "Wx": dV * float(np.sum(E[0] ** 2)),
+        "Wy": dV * float(np.sum(E[1] ** 2)),
+        "Wz": dV * float(np.sum(E[2] ** 2)),
+        "Q": dV * float(np.sum(rho)),
+        "mode": mode_coefficient(E[mode_comp], mode),
+    }
+    if v_new is not None and n_particles:
+        P = mp * np.sum(v_new, axis=0)
+        out.update(Px=float(P[0]), Py=float(P[1]), Pz=float(P[2]),
+                   K=0.5 * mp * float(np.sum(v_new * v_new)))
+    return out
+
+
+def step(x: np.ndarray, v: np.ndarray, grid: Grid, params: Params, with_diag=False,
+         mode=(1, 0, 0), mode_comp=0):
+    """Advance synchronised (x_n, v_n) to (x_{n+1}, v_{n+1}).
+
+    Drift-kick-drift reading of the synchronised Boris scheme (Section 3.2):
+    1. x_h = x_n + dt/2 v_n, periodic wrap
+    2. scatter: rho = deposit(x_h)                  (Section 3.1 step 1)
+    3. solve: E = -grad phi, -Lap phi = rho - rho_i  (step 2)
+    4. gather: e = G(x_h) E + E_ext(x_h)             (step 3)
+    5. Boris kick v_n -> v_{n+1} with e and B_ext      (step 4)
+    6. x_{n+1} = x_h + dt/2 v_{n+1}, periodic wrap
+    """
+    N = x.shape[0]
+    dt = params.dt
+    qp = params.Q / N if N else 0.0
+    xh = wrap(x + 0.5 * dt * v, grid)
+    rho = deposit(xh, grid, qp)
+    E = solve_field(rho, grid)
+    e = gather(xh, E, grid)
+    if params.wz2 != 0.0:
+        e = e + external_field(xh, grid, params.wz2)
+    v1 = boris_kick(v, e, params.q_over_m, params.B, dt)
+    x1 = wrap(xh + 0.5 * dt * v1, grid)
+    if with_diag:
+        return x1, v1, diagnostics(rho, E, v1, grid, params, N, mode, mode_comp)
+    return x1, v1
+
+
+def run(x: np.ndarray, v: np.ndarray, grid: Grid, params: Params, n_steps: int,
+        mode=(1, 0, 0), mode_comp=0, diag_every: int = 1):
+    """n_steps synchronised steps; returns (x, v, list of per-step diagnostics)."""
+    hist = []
+    for n in range(n_steps):
+        want = diag_every > 0 and (n % diag_every == diag_every - 1 or diag_every == 1)
+        if want:
+            x, v, d = step(x, v, grid, params, True, mode, mode_comp)
+            d["step"] = n
+            d["t_field"] = (n + 0.5) * params.dt
+            d["t"] = (n + 1) * params.dt
+            hist.append(d)
+        else:
+            x, v = step(x, v, grid, params)
+    return x, v, hist

@@ -1,0 +1,288 @@
+"""Pins of the FP64 oracle against what the scheme and the physics fix.
+
+None of these compares the oracle with itself: each checks a closed form,
+an invariant, a brute-force evaluation or textbook plasma theory, chosen so
+that a dropped term, a wrong sign or index or a transposed axis fails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import pic_inputs as pi
+from oracle import pic_oracle as po
+from tests import dispersion
+
+RNG = np.random.default_rng(12345)
+
+# a deliberately non-cubic grid so transposed axes show up
+GRID = po.Grid(n=(6, 5, 8), L=(2.0, 3.1, 2.6))
+
+
+def _random_positions(grid, n, rng):
+    return rng.random((n, 3)) * np.asarray(grid.L)
+
+
+# ---------------------------------------------------------------- deposit
+
+def test_deposit_conserves_charge():
+    """CIC weights sum to one, so h^3 sum_g rho_g = sum_p q_p (Section 3.2)."""
+    x = _random_positions(GRID, 5000, RNG)
+    q = -0.37
+    rho = po.deposit(x, GRID, q)
+    total = rho.sum() * GRID.cell_volume
+    assert abs(total - q * x.shape[0]) <= 1e-13 * abs(q * x.shape[0])
+
+
+def test_deposit_matches_bruteforce_tent_functions():
+    """Floor-based stencil == node-by-node minimum-image tent functions."""
+    for grid in (po.Grid((4, 3, 5), (1.0, 1.5, 2.0)), po.Grid((2, 6, 3), (3.0, 1.0, 0.7))):
+        x = _random_positions(grid, 40, RNG)
+        # include boundary cases: exactly 0, just below L, exactly on a node
+        x[0] = 0.0
+        x[1] = np.nextafter(np.asarray(grid.L), 0.0)
+        x[2] = 0.5 * grid.h
+        a = po.deposit(x, grid, 1.3)
+        b = po.deposit_bruteforce(x, grid, 1.3)
+        assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
+
+
+def test_particle_on_node_deposits_to_that_node_only():
+    grid = GRID
+    h = grid.h
+    g = (3, 2, 5)
+    x = np.array([[(g[0] + 0.5) * h[0], (g[1] + 0.5) * h[1], (g[2] + 0.5) * h[2]]])
+    rho = po.deposit(x, grid, 2.0)
+    expect = np.zeros(grid.shape)
+    expect[g[2], g[1], g[0]] = 2.0 / grid.cell_volume
+    assert np.max(np.abs(rho - expect)) <= 1e-12 * expect.max()
+
+
+def test_particle_midway_splits_evenly_across_the_periodic_seam():
+    """x = 0 lies halfway between node N-1 (at L - h/2) and node 0 (at h/2)."""
+    grid = po.Grid((4, 4, 4), (1.0, 1.0, 1.0))
+    x = np.array([[0.0, 0.125, 0.125]])   # y, z on nodes 0
+    rho = po.deposit(x, grid, 1.0) * grid.cell_volume
+    assert rho[0, 0, 0] == pytest.approx(0.5, abs=1e-15)
+    assert rho[0, 0, 3] == pytest.approx(0.5, abs=1e-15)
+    assert rho.sum() == pytest.approx(1.0, abs=1e-15)
+
+
+# ---------------------------------------------------------------- field solve
+
+@pytest.mark.parametrize("m", [(1, 0, 0), (0, 2, 0), (0, 0, 3), (1, -2, 1), (2, 1, -3)])
+def test_single_mode_poisson_closed_form(m):
+    """rho = cos(k.x) -> phi = cos(k.x)/|k|^2 -> E = k sin(k.x)/|k|^2 (Eq. potential)."""
+    grid = po.Grid((8, 10, 12), (2.0, 3.0, 5.0))
+    h = grid.h
+    k = np.array([2 * math.pi * m[d] / grid.L[d] for d in range(3)])
+    zz, yy, xx = np.meshgrid(*[(np.arange(grid.n[d]) + 0.5) * h[d] for d in (2, 1, 0)], indexing="ij")
+    phase = k[0] * xx + k[1] * yy + k[2] * zz
+    rho = np.cos(phase)
+    E, phi = po.solve_field(rho, grid, return_potential=True)
+    k2 = float(np.dot(k, k))
+    for d in range(3):
+        assert np.max(np.abs(E[d] - k[d] * np.sin(phase) / k2)) < 1e-12
+    assert np.max(np.abs(phi - np.cos(phase) / k2)) < 1e-12
+
+
+def test_uniform_background_only_removes_the_mean():
+    grid = GRID
+    rho = RNG.standard_normal(grid.shape)
+    E1 = po.solve_field(rho, grid)
+    E2 = po.solve_field(rho + 7.5, grid)
+    assert np.max(np.abs(E1 - E2)) < 1e-12
+
+
+def test_nyquist_gradient_is_zeroed():
+    """A pure Nyquist density along x gives E_x = 0 (no derivative at k = pi/h)."""
+    grid = po.Grid((8, 4, 4), (1.0, 1.0, 1.0))
+    rho = np.zeros(grid.shape)
+    rho[:, :, :] = (-1.0) ** np.arange(8)[None, None, :]
+    E = po.solve_field(rho, grid)
+    assert np.max(np.abs(E)) < 1e-13
+
+
+# ------------------------------------------------- deposit / gather pairing
+
+def test_zero_self_force():
+    """A lone particle feels no force from its own field: the spectral
+    gradient with zeroed Nyquist modes is an antisymmetric circulant and the
+    gather uses the deposit's weights."""
+    grid = GRID
+    for _ in range(20):
+        x = _random_positions(grid, 1, RNG)
+        rho = po.deposit(x, grid, 1.0)
+        E = po.solve_field(rho, grid)
+        f = po.gather(x, E, grid)
+        scale = np.max(np.abs(E))
+        assert np.max(np.abs(f)) <= 1e-13 * scale
+
+
+def test_momentum_conservation_of_self_forces():
+    """sum_p q_p E(x_p) = h^3 sum_g rho_g E_g = 0 for any particle set."""
+    grid = GRID
+    x = _random_positions(grid, 3000, RNG)
+    q = -0.2
+    rho = po.deposit(x, grid, q)
+    E = po.solve_field(rho, grid)
+    F = q * po.gather(x, E, grid).sum(axis=0)
+    scale = abs(q) * x.shape[0] * np.max(np.abs(E))
+    assert np.max(np.abs(F)) <= 1e-13 * scale
+
+
+def test_gather_is_transpose_of_deposit():
+    """<G(x) E, w> = h^3 <E, D_w(x)> with the same CIC weights."""
+    grid = GRID
+    x = _random_positions(grid, 400, RNG)
+    E = RNG.standard_normal((3,) + grid.shape)
+    w = RNG.standard_normal((400, 3))
+    lhs = float(np.sum(po.gather(x, E, grid) * w))
+    rhs = sum(grid.cell_volume * float(np.sum(E[d] * po.deposit(x, grid, w[:, d]))) for d in range(3))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + 1.0)
+
+
+def test_mode_coefficient_of_a_cosine():
+    grid = po.Grid((16, 8, 8), (4.0, 1.0, 1.0))
+    xx = (np.arange(16) + 0.5) * grid.h[0]
+    f = np.broadcast_to(0.3 * np.cos(2 * math.pi * xx / 4.0)[None, None, :], grid.shape)
+    c = po.mode_coefficient(np.array(f), (1, 0, 0))
+    assert abs(c) == pytest.approx(0.15, rel=1e-12)
+
+
+# ---------------------------------------------------------------- push
+
+def test_boris_pure_magnetic_rotation_angle():
+    """With E = 0 the Boris rotation angle per step is 2 arctan(w_c dt / 2)."""
+    B = (0.0, 0.0, 5.0)
+    dt = 0.05       # w_c dt = |q/m| B dt = 0.25
+    v = np.array([[1.0, 0.0, 0.3]])
+    v1 = po.boris_kick(v, np.zeros((1, 3)), -1.0, B, dt)
+    ang = math.atan2(v1[0, 1], v1[0, 0])
+    assert abs(ang) == pytest.approx(2 * math.atan(0.125), abs=1e-14)
+    assert abs(2 * math.atan(0.125) - 0.24870999) < 1e-8
+    # q/m = -1, B along +z: electrons gyrate counter-clockwise seen from +z
+    assert ang > 0
+    assert np.linalg.norm(v1) == pytest.approx(np.linalg.norm(v), rel=1e-15)
+    assert v1[0, 2] == v[0, 2]
+
+
+def test_boris_without_b_is_a_plain_kick():
+    e = RNG.standard_normal((5, 3))
+    v = RNG.standard_normal((5, 3))
+    v1 = po.boris_kick(v, e, -1.0, (0.0, 0.0, 0.0), 0.05)
+    assert np.max(np.abs(v1 - (v - 0.05 * e))) < 1e-15
+
+
+def test_free_streaming_step_and_wrap():
+    grid = po.Grid((8, 8, 8), (1.0, 2.0, 3.0))
+    x = np.array([[0.99, 1.0, 0.01]])
+    v = np.array([[1.0, -0.5, -1.0]])
+    p = po.Params(dt=0.05, Q=0.0)
+    x1, v1 = po.step(x, v, grid, p)
+    expect = np.mod(x + 0.05 * v, np.asarray(grid.L))
+    assert np.max(np.abs(x1 - expect)) < 1e-15
+    assert np.all(v1 == v)
+
+
+def _trap_map(dt, wz2, Bz=5.0):
+    """The 6x6 linear one-step map of a lone particle about the trap centre."""
+    grid = po.Grid((8, 8, 8), (20.0, 20.0, 20.0))
+    p = po.Params(dt=dt, Q=0.0, B=(0.0, 0.0, Bz), wz2=wz2)
+    c = np.full(3, 10.0)
+    M = np.empty((6, 6))
+    eps = 1e-2
+    for col in range(6):
+        s = np.zeros(6)
+        s[col] = eps
+        x1, v1 = po.step((c + s[:3])[None], s[3:][None], grid, p)
+        M[:, col] = np.concatenate([x1[0] - c, v1[0]]) / eps
+    return M
+
+
+@pytest.mark.parametrize("wz2", [1.0, 1.5])
+def test_penning_single_particle_frequencies(wz2):
+    """Cyclotron, magnetron (E x B) and axial frequencies of the ideal trap:
+    w+- = (wc +- sqrt(wc^2 - 2 wz^2)) / 2, wz = sqrt(wz2) (Section 4.3)."""
+    wc = 5.0
+    dt = 0.005
+    lam = np.linalg.eigvals(_trap_map(dt, wz2))
+    freqs = sorted(set(np.round(np.abs(np.angle(lam)) / dt, 9)))
+    wp = 0.5 * (wc + math.sqrt(wc * wc - 2 * wz2))
+    wm = 0.5 * (wc - math.sqrt(wc * wc - 2 * wz2))
+    expect = sorted([wm, math.sqrt(wz2), wp])
+    assert len(freqs) == 3
+    for f, e in zip(freqs, expect):
+        assert f == pytest.approx(e, rel=1e-3)
+    if wz2 == 1.0:
+        assert wp == pytest.approx(4.89792, abs=1e-5)
+        assert wm == pytest.approx(0.10208, abs=1e-5)
+    # the map is symplectic-like: every eigenvalue on the unit circle
+    assert np.max(np.abs(np.abs(lam) - 1.0)) < 1e-12
+
+
+# ---------------------------------------------------------------- physics
+
+def test_dispersion_root_for_landau_k_half():
+    w = dispersion.root(0.5, 1.4 - 0.15j)
+    assert w.real == pytest.approx(1.41566, abs=2e-5)
+    assert w.imag == pytest.approx(-0.15336, abs=2e-5)
+
+
+@pytest.mark.slow
+def test_landau_damping_rate_and_frequency():
+    """Weak Landau damping, k = 0.5, alpha = 0.05 (Section 4.1): the x mode of
+    E_x oscillates at Re(w) and decays at Im(w) of the kinetic dispersion
+    relation.  Quiet 1D lattice start on a 32 x 1 x 1 grid, t in [0, 10]."""
+    from scipy.optimize import curve_fit
+
+    w = pi.landau_lattice_1d(nx=32, mx=32, mv=2048, n_steps=200)
+    grid = po.Grid(w.n, w.L)
+    p = po.Params(dt=w.dt, Q=w.Q, q_over_m=w.q_over_m)
+    _, _, hist = po.run(w.x, w.v, grid, p, w.n_steps)
+    t = np.array([d["t_field"] for d in hist])
+    c = np.array([d["mode"] for d in hist])
+    sig = (c * np.exp(-1j * np.angle(c[0]))).real
+
+    def model(tt, A, g, om, ph):
+        return A * np.exp(g * tt) * np.cos(om * tt + ph)
+
+    sel = t > 2.0
+    popt, _ = curve_fit(model, t[sel], sig[sel], p0=[sig[0], -0.15, 1.4, 0.0])
+    root = dispersion.root(0.5, 1.4 - 0.15j)
+    assert popt[1] == pytest.approx(root.imag, rel=0.05)
+    assert popt[2] == pytest.approx(root.real, rel=0.01)
+    # charge is exact and the lattice start has zero net momentum
+    assert hist[-1]["Q"] == pytest.approx(w.Q, rel=1e-13)
+    assert abs(hist[-1]["Px"]) < 1e-9 * abs(w.Q)
+
+
+def test_diagnostics_field_energy_of_a_known_field():
+    grid = po.Grid((8, 8, 8), (2.0, 2.0, 2.0))
+    E = np.zeros((3,) + grid.shape)
+    E[1] = 3.0
+    d = po.diagnostics(np.ones(grid.shape), E, None, grid, po.Params(dt=0.1, Q=-8.0), 0)
+    assert d["Wy"] == pytest.approx(9.0 * 8.0, rel=1e-14)
+    assert d["Wx"] == 0.0 and d["Wz"] == 0.0
+    assert d["Q"] == pytest.approx(8.0, rel=1e-14)
+
+
+@pytest.mark.parametrize("Bz", [0.0, 5.0])
+def test_time_reversibility_with_self_field(Bz):
+    """The drift-kick-drift step with the field taken at x_{n+1/2} is exactly
+    time-reversible: stepping (x_n, -v_n) under -B retraces the orbit.  An
+    evaluation of the self or external field at x_n instead breaks this."""
+    w = pi.landau(n=8, ppc=4, seed=7, alpha=0.3)
+    grid = po.Grid(w.n, w.L)
+    fwd = po.Params(dt=0.1, Q=w.Q, B=(0.0, 0.0, Bz), wz2=0.2)
+    bwd = po.Params(dt=0.1, Q=w.Q, B=(0.0, 0.0, -Bz), wz2=0.2)
+    x, v = w.x.copy(), w.v.copy()
+    for _ in range(5):
+        x, v = po.step(x, v, grid, fwd)
+    v = -v
+    for _ in range(5):
+        x, v = po.step(x, v, grid, bwd)
+    dx = x - w.x
+    dx -= np.asarray(grid.L) * np.round(dx / np.asarray(grid.L))
+    assert np.max(np.abs(dx)) < 1e-10
+    assert np.max(np.abs(-v - w.v)) < 1e-10
