@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 PIC hot path.
+
+One benchmark "step" is one pass of the whole hot path over the resident
+particle store: re-binning when due, CIC deposit, FFT field solve, fused
+gather + push, and the FP64 diagnostic reductions.  The default workload is
+Landau damping on a 128^3 grid with 64 particles per cell (134,217,728
+particles, L = 4 pi, alpha = 0.05, dt = 0.05), synthetic and seeded.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Rank 0 prints one JSON line.  With N > 1 (launched by torchrun) every rank
+runs an independent replica of the workload on its own GPU (replicas only:
+no data-path collective); the value is the particle-steps of all ranks over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (deposit+gather+push) & % HBM roofline; adjoint/forward time"
+UNIT = "particle-steps/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--grid", type=int, default=128)
+    ap.add_argument("--ppc", type=int, default=64)
+    ap.add_argument("--sort-period", type=int, default=4)
+    ap.add_argument("--diag-every", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 21,
+                    help="particles in the oracle's bounded sample")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(args):
+    n = args.grid
+    return (f"landau_damping_3d: {n}^3 grid, {args.ppc} particles/cell "
+            f"({n ** 3 * args.ppc:,} particles), L=4pi, alpha=0.05, k=0.5, dt=0.05")
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        mhz, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                maxes.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(maxes),
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ---------------------------------------------------------------- oracle arm
+
+def oracle_sample(args, n_particles):
+    import pic_inputs as pi
+
+    ppc = max(1, n_particles // args.grid ** 3)
+    w = pi.landau(n=args.grid, ppc=1, seed=1001)
+    # a bounded sample of the same workload: the full grid, fewer particles
+    w = pi.landau(n=args.grid, ppc=ppc, seed=1001) if ppc > 1 else w
+    if w.n_particles > n_particles:
+        w.x = w.x[:n_particles].copy()
+        w.v = w.v[:n_particles].copy()
+    w.Q = -(w.L[0] ** 3)
+    return w
+
+
+def time_oracle(w, steps, warmup=0):
+    from oracle import pic_oracle as po
+
+    g = po.Grid(w.n, w.L)
+    p = po.Params(dt=w.dt, q_over_m=w.q_over_m, Q=w.Q, B=w.B, wz2=w.wz2)
+    x, v = w.x, w.v
+    for _ in range(warmup):
+        x, v = po.step(x, v, g, p)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        x, v, _ = po.step(x, v, g, p, with_diag=True)
+    dt = time.perf_counter() - t0
+    return w.n_particles * steps / dt, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    w = oracle_sample(args, args.cpu_sample)
+    val, secs = time_oracle(w, args.steps, args.warmup)
+    sample = (f"{w.n_particles:,} particles of the workload on the full {args.grid}^3 grid, "
+              f"{args.steps} oracle steps (numpy FP64, single thread)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_name(args)},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- native arm
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import pic_inputs as pi
+    from paper_2205_11052_gb300 import capi
+    from paper_2205_11052_gb300.build import build
+    from paper_2205_11052_gb300.sim import Simulation
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build()
+
+    # ---- inputs: seeded synthetic Landau damping (per-rank seed offset)
+    w = pi.landau(n=args.grid, ppc=args.ppc, seed=1001 + rank, n_steps=args.steps)
+    N = w.n_particles
+    ng = args.grid ** 3
+    sim = Simulation.from_workload(w, sort_period=args.sort_period, diag_every=args.diag_every)
+    stream = sim.stream
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- warm-up
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, timers on, clocks sampled
+    capi.pic_enable_timers(sim.handle, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sim.step(1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    phases, launches = capi.pic_read_timers(sim.handle)
+    capi.pic_enable_timers(sim.handle, False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = N * world * args.steps / (ms * 1e-3)
+
+    hist = sim.diagnostics()
+    flags = sim.flags()
+
+    # ---- roofline of the dominant kernel (CUDA events inside the timed region)
+    peak, peak_kind = load_peaks()
+    algo = {"push": 56.0 * N + 16.0 * ng, "deposit": 16.0 * N + 4.0 * ng}
+    kernel_names = {"push": "k_gather_push", "deposit": "k_deposit_tiles"}
+    dom = max(algo, key=lambda k: phases[k][0])
+    avg_ms = phases[dom][0] / max(1, phases[dom][1])
+    achieved = algo[dom] / (avg_ms * 1e-3) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        try:
+            with open(tp) as f:
+                tj = json.load(f)
+            ent = tj.get(kernel_names[dom])
+            if ent and ent.get("source_sha") == _source_sha(ent.get("source")):
+                traffic = ent["bytes_per_launch_full_size"]
+        except Exception:
+            traffic = None
+    roof = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "peak_source": f"{peak_kind} hbm_gbs"}
+    phase_ms = {k: (v[0] / max(1, v[1]), v[1]) for k, v in phases.items()}
+
+    # ---- end-to-end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        xh = torch.from_numpy(w.x).pin_memory()
+        vh = torch.from_numpy(w.v).pin_memory()
+        del w
+        diag_buf = (capi.pic_diag_t * 1)()
+        import ctypes as C
+        lib = capi.load_library()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            capi.pic_load_particles(sim.handle, xh.data_ptr(), vh.data_ptr(), N, False)
+            sim.step(1)
+            n_out = C.c_int()
+            rc = lib.pic_diagnostics(sim.handle, diag_buf, 1, C.byref(n_out))
+            capi.check(rc, "pic_diagnostics")
+        torch.cuda.synchronize()
+        barrier()
+        secs = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([secs], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            secs = float(t.item())
+        e2e = {"value": N * world * args.e2e_steps / secs, "unit": UNIT,
+               "h2d_bytes_per_step": int(xh.numel() * 8 + vh.numel() * 8),
+               "d2h_bytes_per_step": C.sizeof(capi.pic_diag_t),
+               "what": "per step: pic_load_particles from pinned host FP64 (x, v), "
+                       "pic_step(1), pic_diagnostics readback"}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        ws = oracle_sample(args, args.cpu_sample)
+        val, secs = time_oracle(ws, 2)
+        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{ws.n_particles:,} particles of the workload on the full "
+                         f"{args.grid}^3 grid, 2 oracle steps ({secs:.1f} s, numpy FP64, "
+                         f"single thread)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args), "n_particles": N,
+                       "grid": [args.grid] * 3, "sort_period": args.sort_period,
+                       "diag_every": args.diag_every,
+                       "l2": f"inputs larger than L2 ({32 * N / 1e9:.2f} GB particle store "
+                             f"vs {L2_BYTES / 2**20:.0f} MiB L2), no flush",
+                       "parallelism": "replicas" if world > 1 else "single-gpu"},
+            "roofline": roof,
+            "phases_ms": {k: round(v[0], 4) for k, v in phase_ms.items()},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "device_flags": flags,
+            "diag_last": {k: hist[-1][k] for k in ("step", "Wx", "Q", "K")} if hist else None,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _source_sha(rel):
+    import hashlib
+
+    if not rel:
+        return None
+    p = os.path.join(ROOT, rel)
+    if not os.path.exists(p):
+        return None
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

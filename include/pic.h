@@ -1,0 +1,247 @@
+/*
+ * pic.h -- C ABI of the GB300 electrostatic particle-in-cell hot path.
+ *
+ * The library advances electrons in a periodic box [0,Lx) x [0,Ly) x [0,Lz)
+ * under their own space-charge field plus optional uniform external B and a
+ * quadrupole external E (the Vlasov-Poisson model of Section 3.1 of
+ * arXiv 2205.11052, Eq. Vlasov and Eq. potential, in the normalised units of
+ * Section 3.2: eps0 = 1).  One step is the PIC cycle of Section 3.1:
+ *   scatter (CIC deposit) -> FFT Poisson solve -> gather (CIC) -> push,
+ * with a cell-centred grid, periodic boundaries and the synchronised Boris
+ * integrator of Section 3.2 (read here as drift-kick-drift).
+ *
+ * Conventions shared by every call
+ *  - Status: every int-returning call returns PIC_OK (0) or a negative
+ *    PIC_ERR_* code; pic_last_error() then describes the failure.  No C++
+ *    exception crosses this boundary.
+ *  - Threads: a handle must not be used from two host threads at once.
+ *  - Memory: the library allocates no device memory of its own for the
+ *    simulation state.  pic_buffer_sizes() reports one arena size; the caller
+ *    allocates it (for instance as a torch tensor) and binds it with
+ *    pic_bind_workspace().  The caller owns the arena and the stream and must
+ *    keep both alive until pic_destroy().  cuFFT plans are created inside
+ *    pic_bind_workspace() with automatic work-area allocation disabled (their
+ *    work area lives in the arena; cuFFT may still keep small internal tables).
+ *  - Ordering: all device work is enqueued on the bound stream, asynchronously
+ *    with respect to the host, except where a call says it synchronises.
+ *    Calls that take host buffers synchronise before returning.
+ *  - Layouts: particle positions and velocities cross the boundary as FP64
+ *    arrays of shape (n, 3), row-major (x0 y0 z0 x1 y1 z1 ...).  Grid fields
+ *    are row-major (Nz, Ny, Nx) with x fastest: node (i, j, k) sits at
+ *    ((i + 1/2) hx, (j + 1/2) hy, (k + 1/2) hz), h_d = L_d / N_d
+ *    (cell-centred grid, Section 3.2).
+ */
+#ifndef PIC_GB300_PIC_H
+#define PIC_GB300_PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define PIC_OK               0
+#define PIC_ERR_ARG         -1  /* invalid argument or configuration           */
+#define PIC_ERR_CAPACITY    -2  /* more particles or larger buffers than bound  */
+#define PIC_ERR_CUDA        -3  /* a CUDA runtime call or kernel launch failed  */
+#define PIC_ERR_CUFFT       -4  /* a cuFFT call failed                          */
+#define PIC_ERR_DEVICE_FLAG -5  /* a kernel raised an error flag (NaN, bad cell) */
+#define PIC_ERR_TIMEOUT     -6  /* a bounded device-side wait ran out           */
+#define PIC_ERR_STATE       -7  /* call out of order (e.g. no workspace bound)  */
+
+/* device error flag bits reported by pic_device_flags() */
+#define PIC_FLAG_NONFINITE   1  /* a non-finite position, velocity or field value */
+#define PIC_FLAG_BAD_CELL    2  /* a particle cell index outside the grid          */
+
+typedef struct pic_ctx *pic_handle_t;
+
+/* Periodic cell-centred grid: n[d] nodes (1..1024; n[0] >= 2) on [0, L[d]). */
+typedef struct {
+    int32_t n[3];
+    double  L[3];
+} pic_grid_t;
+
+/* One electron species with uniform macro-particle charge (Section 3.1). */
+typedef struct {
+    double  q_over_m;      /* charge-to-mass ratio; -1 in normalised units      */
+    double  total_charge;  /* Q_e; each loaded particle carries Q_e / n_loaded  */
+    int64_t n_particles;   /* particle capacity, 0 .. 2^31 - 1                  */
+} pic_species_t;
+
+/* Time step, external fields and tuning knobs (0 selects the default). */
+typedef struct {
+    double  dt;            /* time step (> 0)                                    */
+    double  B_ext[3];      /* uniform external magnetic field                    */
+    double  wz2;           /* quadrupole external field (Section 4.3):
+                              E_ext = wz2 * (-(x-cx)/2, -(y-cy)/2, (z-cz)),
+                              c = box centre; wz2 is the axial frequency squared */
+    int32_t tile[3];       /* deposit tile, in cells per axis (default 8)        */
+    int32_t guard;         /* tile guard layers, in cells (default 2)            */
+    int32_t sort_period;   /* re-bin particles every K steps (default 1;
+                              negative = only when loaded)                      */
+    int32_t diag_every;    /* record diagnostics every K steps (0 = never)       */
+    int32_t diag_capacity; /* diagnostic records kept on the device (default 1024) */
+    int32_t mode[3];       /* Fourier mode tracked by the diagnostics            */
+    int32_t mode_comp;     /* component of E for that mode: 0 = x, 1 = y, 2 = z  */
+    int32_t block;         /* threads per block of the particle kernels (256)    */
+    int32_t chunk;         /* max particles per deposit work item (default 4096) */
+} pic_params_t;
+
+/* Sizes the caller must provide before any device work. */
+typedef struct {
+    size_t  workspace_bytes;     /* one device arena, 256-byte aligned start   */
+    size_t  workspace_align;     /* required alignment of the arena (bytes)    */
+    int64_t particle_capacity;   /* = species n_particles                       */
+    int64_t grid_nodes;          /* Nx * Ny * Nz                                */
+    int64_t staging_particles;   /* particles per host<->device transfer chunk  */
+} pic_bufsizes_t;
+
+/* One diagnostic record (FP64).  Field quantities refer to the field of
+ * step `step`, computed at the half step t_field = (step + 1/2) dt of the
+ * drift-kick-drift cycle; particle quantities use the synchronised
+ * velocities v_{step+1} at t = (step + 1) dt. */
+typedef struct {
+    int64_t step;
+    double  t_field;
+    double  Wx, Wy, Wz;      /* int E_d^2 dV = h^3 sum_g E_d,g^2 (Figs. of Section 4) */
+    double  Q;               /* h^3 sum_g rho_g: electron charge on the grid    */
+    double  mode_re, mode_im;/* (1/N_g) sum_g E_c,g exp(-2 pi i m.g/N)           */
+    double  t;
+    double  Px, Py, Pz;      /* m_p sum_p v_p                                    */
+    double  K;               /* (1/2) m_p sum_p |v_p|^2                           */
+} pic_diag_t;
+
+/* ------------------------------------------------------------ lifecycle */
+
+/* Validate the configuration and create a handle.  Host-only: no CUDA call
+ * is made, so this also works where no GPU is present.
+ * Errors: PIC_ERR_ARG for null pointers, grid sizes outside 1..1024 (or
+ * n[0] < 2), non-positive or non-finite lengths or dt, capacity outside
+ * 0..2^31-1, tiles < 1, negative guard, diag mode out of range. */
+int pic_create(const pic_grid_t *grid, const pic_species_t *species,
+               const pic_params_t *params, pic_handle_t *out);
+
+/* Report the device arena size (and derived sizes) for this handle. Host-only. */
+int pic_buffer_sizes(pic_handle_t h, pic_bufsizes_t *out);
+
+/* Bind the caller-allocated device arena (at least workspace_bytes, aligned
+ * to workspace_align) and a CUDA stream (cudaStream_t as void*, NULL = legacy
+ * default stream) on the current device; creates the cuFFT plans and clears
+ * the diagnostics and flags.  May be called again to rebind.
+ * Errors: PIC_ERR_ARG (null or misaligned pointer), PIC_ERR_CAPACITY
+ * (arena too small), PIC_ERR_CUDA, PIC_ERR_CUFFT. */
+int pic_bind_workspace(pic_handle_t h, void *dev_arena, size_t bytes, void *stream);
+
+/* Change the stream later work is enqueued on. */
+int pic_set_stream(pic_handle_t h, void *stream);
+
+/* Release host-side state and cuFFT plans (not the caller's arena). */
+void pic_destroy(pic_handle_t h);
+
+/* Thread-local text of the most recent failure on this host thread. */
+const char *pic_last_error(void);
+
+/* ------------------------------------------------------------ state I/O */
+
+/* Load n synchronised particles (x_0, v_0), FP64 arrays of shape (n, 3),
+ * from host memory (src_is_device = 0; copied in chunks through the arena)
+ * or device memory (src_is_device = 1).  Positions may lie outside [0, L)
+ * and are wrapped periodically.  Resets the step counter and diagnostics,
+ * half-drifts to x_{1/2} = x_0 + dt/2 v_0 (the drift-kick-drift state kept
+ * on the device), stores each particle as (cell, FP32 offset, FP32 velocity)
+ * and bins it (Section 3.2; particle storage as in Section 2's SoA layout).
+ * Host sources synchronise; device sources are enqueued.
+ * Errors: PIC_ERR_CAPACITY (n > capacity), PIC_ERR_ARG, PIC_ERR_CUDA. */
+int pic_load_particles(pic_handle_t h, const double *x, const double *v,
+                       int64_t n, int src_is_device);
+
+/* Write the synchronised state (x_n, v_n) of all loaded particles, in load
+ * order, as FP64 (n, 3) arrays to host (dst_is_device = 0) or device memory.
+ * Positions are wrapped into [0, L).  Synchronises for host destinations. */
+int pic_get_particles(pic_handle_t h, double *x, double *v, int dst_is_device);
+
+/* Copy the current grid fields: rho (N_g FP32, electron charge density of
+ * the last deposit) and E (N_g x 4 FP32: Ex, Ey, Ez, 0 of the last solve).
+ * Either pointer may be NULL.  Synchronises for host destinations. */
+int pic_get_field(pic_handle_t h, float *rho, float *E, int dst_is_device);
+
+/* Overwrite rho (N_g FP32 values, layout as above, electron charge density)
+ * from host (src_is_device = 0; synchronises) or device memory, e.g. to
+ * solve for the field of a given density with pic_field_solve(). */
+int pic_set_rho(pic_handle_t h, const float *rho, int src_is_device);
+
+/* Number of particles currently loaded and steps taken since the load. */
+int pic_get_counts(pic_handle_t h, int64_t *n_particles, int64_t *step);
+
+/* ------------------------------------------------------------ the cycle */
+
+/* Re-bin the particles: periodic counting sort by tile-major cell index and
+ * rebuild the deposit work list.  (Not in the paper; keeps particles
+ * cell-ordered so the deposit can accumulate in shared-memory tiles.) */
+int pic_sort(pic_handle_t h);
+
+/* Scatter (Section 3.1 step 1): rho_g = sum_p q_p W(x_g - x_p) / h^3 with the
+ * CIC shape on the cell-centred grid (Section 3.2), from the current
+ * half-step positions x_{n+1/2}.  Overwrites rho. */
+int pic_deposit(pic_handle_t h);
+
+/* Field solve (Section 3.1 step 2, Eq. potential; Section 3.2): the uniform
+ * ion background cancels the mean of rho; E^_d = -i k_d rho^ / |k|^2 with
+ * k_d = 2 pi m_d / L_d, the k = 0 mode and each axis' Nyquist gradient set to
+ * zero, then E = IFFT.  Overwrites E. */
+int pic_field_solve(pic_handle_t h);
+
+/* Gather + push (Section 3.1 steps 3-4, Eq. momentum_eqn; Section 3.2):
+ * interpolate E (+ E_ext) to x_{n+1/2} with the CIC weights, Boris-rotate
+ * v_n -> v_{n+1} about B_ext, drift x_{n+1/2} -> x_{n+3/2} = x_{n+1/2} + dt v_{n+1},
+ * apply the periodic boundary, and advance the step counter. */
+int pic_gather_push(pic_handle_t h);
+
+/* n full steps: [re-bin when due] deposit, solve, gather+push, and the FP64
+ * diagnostic reductions every diag_every steps.  Only kernel launches, cuFFT
+ * executions and memsets are enqueued (no host synchronisation), so the
+ * sequence can be captured in a CUDA graph by the caller. */
+int pic_step(pic_handle_t h, int n);
+
+/* ------------------------------------------------------------ diagnostics */
+
+/* Copy up to max_records diagnostic records (oldest first; at most the last
+ * diag_capacity are kept) to host memory and report how many were written.
+ * Synchronises, then returns PIC_ERR_DEVICE_FLAG if a kernel raised a flag. */
+int pic_diagnostics(pic_handle_t h, pic_diag_t *out, int max_records, int *n_out);
+
+/* Read (synchronising) and optionally clear the device error flag word. */
+int pic_device_flags(pic_handle_t h, int32_t *flags, int clear);
+
+/* ------------------------------------------------------------ timers */
+
+/* Per-phase device timers, in the spirit of the per-kernel timers the paper
+ * reports (Section 5.1, Table parallel_comm_kernels: scatter, solve, gather +
+ * push ...).  When enabled, every phase call records a CUDA event pair on the
+ * bound stream around its kernels; the library also counts its own kernel
+ * launches (cuFFT's kernels excluded).  Do not enable timers while the
+ * stream is being captured into a CUDA graph. */
+#define PIC_PHASE_SORT     0   /* binning: histogram, scan, scatter, work list   */
+#define PIC_PHASE_DEPOSIT  1   /* the deposit kernel                              */
+#define PIC_PHASE_SOLVE    2   /* R2C FFT, Green kernel, C2R FFT                  */
+#define PIC_PHASE_PUSH     3   /* the fused gather + push kernel                  */
+#define PIC_PHASE_DIAG     4   /* FP64 diagnostic reductions                      */
+#define PIC_PHASE_COUNT    5
+
+/* Enable (1) or disable (0) the timers; either way the accumulators and the
+ * launch counter are reset.  Errors: PIC_ERR_STATE before binding. */
+int pic_enable_timers(pic_handle_t h, int enable);
+
+/* Synchronise and report, per phase, the summed device time (ms) and the
+ * number of timed calls, plus the library kernels launched since enabling.
+ * Any pointer may be NULL. */
+int pic_read_timers(pic_handle_t h, double ms[PIC_PHASE_COUNT],
+                    int64_t calls[PIC_PHASE_COUNT], int64_t *kernel_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_GB300_PIC_H */

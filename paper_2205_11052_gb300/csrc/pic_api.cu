@@ -1,0 +1,699 @@
+// C ABI of the GB300 PIC library (declared in include/pic.h): configuration
+// validation, arena layout, cuFFT plans and the step driver.  Every device
+// operation is a launch of this library's kernels (k_*.cu), a cuFFT execution
+// or a memset/memcpy, enqueued on the caller's stream.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "pic_internal.cuh"
+
+using namespace pic;
+
+namespace {
+
+thread_local char g_err[512] = "no error";
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define PIC_CUDA(call)                                                                  \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(PIC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define PIC_CUFFT(call)                                                       \
+    do {                                                                      \
+        cufftResult r_ = (call);                                              \
+        if (r_ != CUFFT_SUCCESS)                                              \
+            return fail(PIC_ERR_CUFFT, "%s failed: cufftResult %d", #call, (int)r_); \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr int kTimerRing = 64;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Byte offsets of every device buffer inside the caller's arena.
+struct Layout {
+    size_t ctrl, sets, rho, rho_hat, E_hat, E4, bins, scan_tmp, tile_items, tile_range, items,
+        fpart, ppart, ring, inv, stage_x, stage_v, fft, total;
+    size_t set_stride;   // bytes of one per-particle array
+};
+
+}  // namespace
+
+struct pic_ctx {
+    pic_grid_t grid;
+    pic_species_t sp;
+    pic_params_t prm;
+    Geom geom;
+    double L[3], h[3], inv_h[3], dV;
+    int64_t cap, ng, nhalf, nbins, ntiles, max_items, staging;
+    int chunk, block, sparse_below, deposit_blocks;
+    int mode_idx[3], mode_conj;
+    size_t fft_reserve;
+    Layout lay;
+    // bound state
+    bool bound;
+    char *arena;
+    cudaStream_t st;
+    cufftHandle r2c, c2r;
+    bool plans;
+    // phase timers: a ring of event pairs per phase, drained when it wraps
+    bool timing;
+    bool events_made;
+    cudaEvent_t ev[PIC_PHASE_COUNT][kTimerRing][2];
+    int64_t ev_count[PIC_PHASE_COUNT];     // pairs recorded since enabling
+    int64_t ev_drained[PIC_PHASE_COUNT];   // pairs already summed
+    double ms[PIC_PHASE_COUNT];
+    int64_t launches;
+    // host mirror of the run
+    int64_t np;
+    int64_t step;
+    int since_sort;
+    bool loaded;
+
+    template <class T>
+    T *at(size_t off) const { return reinterpret_cast<T *>(arena + off); }
+    Ctrl *ctrl() const { return at<Ctrl>(lay.ctrl); }
+};
+
+namespace {
+
+bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
+
+// Plan dimensions, slowest first, dropping unit y/z axes (x is the R2C axis).
+int fft_dims(const pic_ctx *c, long long *n, long long *nin) {
+    int r = 0;
+    if (c->grid.n[2] > 1) { n[r] = c->grid.n[2]; nin[r] = c->grid.n[2]; ++r; }
+    if (c->grid.n[1] > 1) { n[r] = c->grid.n[1]; nin[r] = c->grid.n[1]; ++r; }
+    n[r] = c->grid.n[0];
+    nin[r] = c->grid.n[0] / 2 + 1;
+    ++r;
+    return r;
+}
+
+int make_plans(pic_ctx *c, bool estimate_only, size_t *ws_r2c, size_t *ws_c2r) {
+    long long n[3], nin[3], nout[3];
+    const int rank = fft_dims(c, n, nin);
+    for (int d = 0; d < rank; ++d) nout[d] = n[d];
+    cufftHandle a = 0, b = 0;
+    PIC_CUFFT(cufftCreate(&a));
+    cufftResult r = cufftCreate(&b);
+    if (r != CUFFT_SUCCESS) {
+        cufftDestroy(a);
+        return fail(PIC_ERR_CUFFT, "cufftCreate failed: %d", (int)r);
+    }
+    cufftSetAutoAllocation(a, 0);
+    cufftSetAutoAllocation(b, 0);
+    if (estimate_only) {
+        r = cufftGetSizeMany64(a, rank, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1, ws_r2c);
+        if (r == CUFFT_SUCCESS)
+            r = cufftGetSizeMany64(b, rank, n, nin, 1, c->nhalf, nout, 4, 1, CUFFT_C2R, 3, ws_c2r);
+        cufftDestroy(a);
+        cufftDestroy(b);
+        if (r != CUFFT_SUCCESS) return fail(PIC_ERR_CUFFT, "cufftGetSizeMany64 failed: %d", (int)r);
+        return PIC_OK;
+    }
+    r = cufftMakePlanMany64(a, rank, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1, ws_r2c);
+    if (r == CUFFT_SUCCESS)
+        r = cufftMakePlanMany64(b, rank, n, nin, 1, c->nhalf, nout, 4, 1, CUFFT_C2R, 3, ws_c2r);
+    if (r != CUFFT_SUCCESS) {
+        cufftDestroy(a);
+        cufftDestroy(b);
+        return fail(PIC_ERR_CUFFT, "cufftMakePlanMany64 failed: %d", (int)r);
+    }
+    c->r2c = a;
+    c->c2r = b;
+    c->plans = true;
+    return PIC_OK;
+}
+
+void compute_layout(pic_ctx *c) {
+    Layout &L = c->lay;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o += align_up(bytes ? bytes : 1);
+        return at;
+    };
+    const size_t capb = (size_t)std::max<int64_t>(c->cap, 1) * 4;
+    L.set_stride = align_up(capb);
+    L.ctrl = take(sizeof(Ctrl));
+    L.sets = take(2 * 8 * L.set_stride);
+    L.rho = take((size_t)c->ng * 4);
+    L.rho_hat = take((size_t)c->nhalf * 8);
+    L.E_hat = take((size_t)c->nhalf * 8 * 3);
+    L.E4 = take((size_t)c->ng * 16);
+    L.bins = take((size_t)(c->nbins + 1) * 4);
+    const int64_t scan_n = std::max(c->nbins, c->ntiles);
+    L.scan_tmp = take((size_t)((scan_n + 4095) / 4096 + 2) * 4);
+    L.tile_items = take((size_t)(c->ntiles + 1) * 4);
+    L.tile_range = take((size_t)c->ntiles * 8);
+    L.items = take((size_t)c->max_items * 16);
+    L.fpart = take((size_t)kDiagFieldBlocks * 4 * 8);
+    L.ppart = take((size_t)kMaxPushBlocks * 4 * 8);
+    L.ring = take((size_t)c->prm.diag_capacity * sizeof(pic_diag_t));
+    L.inv = take(capb);
+    L.stage_x = take((size_t)c->staging * 24);
+    L.stage_v = take((size_t)c->staging * 24);
+    L.fft = take(c->fft_reserve);
+    L.total = o;
+}
+
+int check_ready(const pic_ctx *c) {
+    if (!c) return fail(PIC_ERR_ARG, "null handle");
+    if (!c->bound) return fail(PIC_ERR_STATE, "no workspace bound (call pic_bind_workspace)");
+    return PIC_OK;
+}
+
+int check_loaded(const pic_ctx *c) {
+    int r = check_ready(c);
+    if (r) return r;
+    if (!c->loaded) return fail(PIC_ERR_STATE, "no particles loaded (call pic_load_particles)");
+    return PIC_OK;
+}
+
+float qscale_of(const pic_ctx *c) {
+    if (c->np <= 0) return 0.0f;
+    return (float)(c->sp.total_charge / (double)c->np / c->dV);
+}
+
+double mp_of(const pic_ctx *c) {
+    if (c->np <= 0) return 0.0;
+    return c->sp.total_charge / (double)c->np / c->sp.q_over_m;
+}
+
+int push_blocks_of(const pic_ctx *c) {
+    const int64_t b = (c->np + c->block - 1) / c->block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, kMaxPushBlocks));
+}
+
+PushConst push_const(const pic_ctx *c) {
+    PushConst pc;
+    const double qm = c->sp.q_over_m, dt = c->prm.dt;
+    pc.qm_half_dt = (float)(0.5 * dt * qm);
+    double t[3], t2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        pc.dt_over_h[d] = (float)(dt * c->inv_h[d]);
+        t[d] = 0.5 * dt * qm * c->prm.B_ext[d];
+        t2 += t[d] * t[d];
+    }
+    for (int d = 0; d < 3; ++d) {
+        pc.t[d] = (float)t[d];
+        pc.s[d] = (float)(2.0 * t[d] / (1.0 + t2));
+        pc.half_n[d] = (float)(0.5 * c->grid.n[d]);
+    }
+    pc.wz2 = (float)c->prm.wz2;
+    return pc;
+}
+
+// Sum the elapsed time of recorded pairs up to `upto` (exclusive).
+int drain_timer(pic_ctx *c, int ph, int64_t upto) {
+    for (; c->ev_drained[ph] < upto; ++c->ev_drained[ph]) {
+        const int slot = (int)(c->ev_drained[ph] % kTimerRing);
+        PIC_CUDA(cudaEventSynchronize(c->ev[ph][slot][1]));
+        float t = 0.f;
+        PIC_CUDA(cudaEventElapsedTime(&t, c->ev[ph][slot][0], c->ev[ph][slot][1]));
+        c->ms[ph] += t;
+    }
+    return PIC_OK;
+}
+
+int timer_begin(pic_ctx *c, int ph) {
+    if (!c->timing) return PIC_OK;
+    // reuse a slot only after its previous pair has been summed
+    int r = drain_timer(c, ph, c->ev_count[ph] - kTimerRing + 1);
+    if (r) return r;
+    const int slot = (int)(c->ev_count[ph] % kTimerRing);
+    PIC_CUDA(cudaEventRecord(c->ev[ph][slot][0], c->st));
+    return PIC_OK;
+}
+
+int timer_end(pic_ctx *c, int ph, int kernels) {
+    c->launches += kernels;
+    if (!c->timing) return PIC_OK;
+    const int slot = (int)(c->ev_count[ph] % kTimerRing);
+    PIC_CUDA(cudaEventRecord(c->ev[ph][slot][1], c->st));
+    c->ev_count[ph] += 1;
+    return PIC_OK;
+}
+
+int do_sort(pic_ctx *c) {
+    int r = timer_begin(c, PIC_PHASE_SORT);
+    if (r) return r;
+    PIC_CUDA(launch_sort(c->np, c->geom, c->chunk, c->ctrl(), c->at<int32_t>(c->lay.bins),
+                         c->nbins, c->at<int32_t>(c->lay.scan_tmp),
+                         c->at<int32_t>(c->lay.tile_items), c->at<int2>(c->lay.tile_range),
+                         c->at<int4>(c->lay.items), c->st));
+    c->since_sort = 0;
+    // histogram, 3 scan, scatter, ranges, 3 scan, fill (histogram/scatter skipped when empty)
+    return timer_end(c, PIC_PHASE_SORT, c->np > 0 ? 10 : 8);
+}
+
+int do_deposit(pic_ctx *c) {
+    PIC_CUDA(cudaMemsetAsync(c->at<float>(c->lay.rho), 0, (size_t)c->ng * 4, c->st));
+    if (c->np > 0) {
+        int r = timer_begin(c, PIC_PHASE_DEPOSIT);
+        if (r) return r;
+        PIC_CUDA(launch_deposit(c->np, c->geom, c->ctrl(), c->at<int4>(c->lay.items),
+                                (int)c->max_items, qscale_of(c), c->at<float>(c->lay.rho),
+                                c->ctrl(), c->deposit_blocks, c->sparse_below, c->st));
+        return timer_end(c, PIC_PHASE_DEPOSIT, 1);
+    }
+    return PIC_OK;
+}
+
+int do_solve(pic_ctx *c) {
+    int r = timer_begin(c, PIC_PHASE_SOLVE);
+    if (r) return r;
+    PIC_CUFFT(cufftExecR2C(c->r2c, c->at<cufftReal>(c->lay.rho), c->at<cufftComplex>(c->lay.rho_hat)));
+    PIC_CUDA(launch_green(c->geom, c->L, c->at<float2>(c->lay.rho_hat), c->at<float2>(c->lay.E_hat),
+                          c->nhalf, c->mode_idx, c->prm.mode_comp, c->mode_conj, c->ctrl(), c->st));
+    PIC_CUFFT(cufftExecC2R(c->c2r, c->at<cufftComplex>(c->lay.E_hat), c->at<cufftReal>(c->lay.E4)));
+    return timer_end(c, PIC_PHASE_SOLVE, 1);
+}
+
+int do_gather_push(pic_ctx *c, bool diag) {
+    int r = timer_begin(c, PIC_PHASE_PUSH);
+    if (r) return r;
+    PIC_CUDA(launch_gather_push(c->np, c->geom, push_const(c), diag, c->ctrl(),
+                                c->at<float4>(c->lay.E4), c->at<double>(c->lay.ppart),
+                                push_blocks_of(c), c->block, c->st));
+    c->step += 1;
+    c->since_sort += 1;
+    return timer_end(c, PIC_PHASE_PUSH, 1);
+}
+
+int do_diag(pic_ctx *c) {
+    int r = timer_begin(c, PIC_PHASE_DIAG);
+    if (r) return r;
+    PIC_CUDA(launch_diag_field(c->geom, c->at<float>(c->lay.rho), c->at<float4>(c->lay.E4),
+                               c->at<double>(c->lay.fpart), c->st));
+    PIC_CUDA(launch_diag_finalize(c->at<double>(c->lay.fpart), c->at<double>(c->lay.ppart),
+                                  push_blocks_of(c), c->dV, mp_of(c), c->prm.dt, c->ctrl(),
+                                  c->at<pic_diag_t>(c->lay.ring), c->prm.diag_capacity, c->st));
+    return timer_end(c, PIC_PHASE_DIAG, 2);
+}
+
+// Reset the resettable head of the control block (everything before `cur`).
+int reset_ctrl(pic_ctx *c) {
+    PIC_CUDA(cudaMemsetAsync(c->ctrl(), 0, offsetof(Ctrl, cur), c->st));
+    return PIC_OK;
+}
+
+}  // namespace
+
+// =============================================================================
+// C ABI
+// =============================================================================
+extern "C" {
+
+const char *pic_last_error(void) { return g_err; }
+
+int pic_create(const pic_grid_t *grid, const pic_species_t *species, const pic_params_t *params,
+               pic_handle_t *out) {
+    if (!grid || !species || !params || !out) return fail(PIC_ERR_ARG, "null argument");
+    *out = nullptr;
+    for (int d = 0; d < 3; ++d) {
+        if (grid->n[d] < 1 || grid->n[d] > kMaxN)
+            return fail(PIC_ERR_ARG, "grid n[%d] = %d outside 1..%d", d, grid->n[d], kMaxN);
+        if (!finite_pos(grid->L[d]))
+            return fail(PIC_ERR_ARG, "grid L[%d] must be finite and > 0", d);
+    }
+    if (grid->n[0] < 2) return fail(PIC_ERR_ARG, "grid n[0] must be >= 2 (R2C axis)");
+    if (species->n_particles < 0 || species->n_particles > 2147483647LL)
+        return fail(PIC_ERR_ARG, "n_particles %lld outside 0..2^31-1",
+                    (long long)species->n_particles);
+    if (!isfinite(species->q_over_m) || species->q_over_m == 0.0)
+        return fail(PIC_ERR_ARG, "q_over_m must be finite and nonzero");
+    if (!isfinite(species->total_charge)) return fail(PIC_ERR_ARG, "total_charge must be finite");
+    if (!finite_pos(params->dt)) return fail(PIC_ERR_ARG, "dt must be finite and > 0");
+    for (int d = 0; d < 3; ++d)
+        if (!isfinite(params->B_ext[d])) return fail(PIC_ERR_ARG, "B_ext must be finite");
+    if (!isfinite(params->wz2)) return fail(PIC_ERR_ARG, "wz2 must be finite");
+    for (int d = 0; d < 3; ++d)
+        if (params->tile[d] < 0) return fail(PIC_ERR_ARG, "tile[%d] must be >= 0", d);
+    if (params->guard < 0 || params->guard > 8) return fail(PIC_ERR_ARG, "guard outside 0..8");
+    if (params->diag_every < 0) return fail(PIC_ERR_ARG, "diag_every must be >= 0");
+    if (params->diag_capacity < 0) return fail(PIC_ERR_ARG, "diag_capacity must be >= 0");
+    if (params->mode_comp < 0 || params->mode_comp > 2)
+        return fail(PIC_ERR_ARG, "mode_comp must be 0, 1 or 2");
+    for (int d = 0; d < 3; ++d)
+        if (2 * abs(params->mode[d]) > grid->n[d])
+            return fail(PIC_ERR_ARG, "mode[%d] = %d beyond the Nyquist index", d, params->mode[d]);
+    if (params->block != 0 && (params->block < 32 || params->block > 256 || params->block % 32))
+        return fail(PIC_ERR_ARG, "block must be 0 or a multiple of 32 in 32..256");
+    if (params->chunk != 0 && params->chunk < 32) return fail(PIC_ERR_ARG, "chunk must be >= 32");
+
+    pic_ctx *c = new (std::nothrow) pic_ctx();
+    if (!c) return fail(PIC_ERR_ARG, "out of host memory");
+    c->grid = *grid;
+    c->sp = *species;
+    c->prm = *params;
+    pic_params_t &p = c->prm;
+    if (p.sort_period == 0) p.sort_period = 1;
+    if (p.diag_capacity == 0) p.diag_capacity = 1024;
+    if (p.guard == 0) p.guard = 2;
+    c->block = p.block ? p.block : 256;
+    c->chunk = p.chunk ? p.chunk : 4096;
+
+    Geom &g = c->geom;
+    int64_t nt = 1;
+    for (int d = 0; d < 3; ++d) {
+        g.n[d] = grid->n[d];
+        int T = p.tile[d] ? p.tile[d] : 8;
+        T = std::min(T, grid->n[d]);
+        g.tile[d] = T;
+        g.ntile[d] = (grid->n[d] + T - 1) / T;
+        nt *= g.ntile[d];
+        c->L[d] = grid->L[d];
+        c->h[d] = grid->L[d] / grid->n[d];
+        c->inv_h[d] = grid->n[d] / grid->L[d];
+        g.h[d] = (float)c->h[d];
+        g.inv_h[d] = (float)c->inv_h[d];
+    }
+    g.nh = grid->n[0] / 2 + 1;
+    g.guard = p.guard;
+    g.tvol = g.tile[0] * g.tile[1] * g.tile[2];
+    c->dV = c->h[0] * c->h[1] * c->h[2];
+    c->ntiles = nt;
+    c->nbins = nt * g.tvol;
+    if (c->nbins > 2147483647LL - 1) {
+        delete c;
+        return fail(PIC_ERR_ARG, "too many bins for this grid and tile");
+    }
+    c->cap = species->n_particles;
+    c->ng = (int64_t)grid->n[0] * grid->n[1] * grid->n[2];
+    c->nhalf = (int64_t)g.nh * grid->n[1] * grid->n[2];
+    c->max_items = c->ntiles + (c->cap + c->chunk - 1) / c->chunk + 1;
+    c->staging = std::max<int64_t>(1, std::min<int64_t>(c->cap, (int64_t)1 << 22));
+    c->sparse_below = 64;
+    c->deposit_blocks = 152 * 8;
+
+    int m[3] = {p.mode[0], p.mode[1], p.mode[2]};
+    c->mode_conj = 0;
+    if (m[0] < 0) {   // use the conjugate of the mirrored mode (real field)
+        for (int d = 0; d < 3; ++d) m[d] = -m[d];
+        c->mode_conj = 1;
+    }
+    c->mode_idx[0] = m[0];
+    c->mode_idx[1] = ((m[1] % grid->n[1]) + grid->n[1]) % grid->n[1];
+    c->mode_idx[2] = ((m[2] % grid->n[2]) + grid->n[2]) % grid->n[2];
+
+    // cuFFT work area: the library's own size query when it works here,
+    // never less than a conservative bound
+    size_t w1 = 0, w2 = 0;
+    size_t bound = (size_t)c->nhalf * 8 * 3 + ((size_t)4 << 20);
+    if (make_plans(c, true, &w1, &w2) == PIC_OK) bound = std::max(bound, std::max(w1, w2));
+    c->fft_reserve = bound;
+    compute_layout(c);
+    *out = c;
+    snprintf(g_err, sizeof(g_err), "no error");
+    return PIC_OK;
+}
+
+int pic_buffer_sizes(pic_handle_t c, pic_bufsizes_t *out) {
+    if (!c || !out) return fail(PIC_ERR_ARG, "null argument");
+    out->workspace_bytes = c->lay.total;
+    out->workspace_align = kAlign;
+    out->particle_capacity = c->cap;
+    out->grid_nodes = c->ng;
+    out->staging_particles = c->staging;
+    return PIC_OK;
+}
+
+int pic_bind_workspace(pic_handle_t c, void *arena, size_t bytes, void *stream) {
+    if (!c || !arena) return fail(PIC_ERR_ARG, "null argument");
+    if ((uintptr_t)arena % kAlign) return fail(PIC_ERR_ARG, "arena not %zu-byte aligned", kAlign);
+    if (bytes < c->lay.total)
+        return fail(PIC_ERR_CAPACITY, "arena of %zu bytes < required %zu", bytes, c->lay.total);
+    if (c->plans) {
+        cufftDestroy(c->r2c);
+        cufftDestroy(c->c2r);
+        c->plans = false;
+    }
+    c->bound = false;
+    c->loaded = false;
+    c->arena = static_cast<char *>(arena);
+    c->st = static_cast<cudaStream_t>(stream);
+    size_t w1 = 0, w2 = 0;
+    int r = make_plans(c, false, &w1, &w2);
+    if (r) return r;
+    if (std::max(w1, w2) > c->fft_reserve) {
+        cufftDestroy(c->r2c);
+        cufftDestroy(c->c2r);
+        c->plans = false;
+        return fail(PIC_ERR_CAPACITY, "cuFFT needs %zu work bytes, %zu reserved",
+                    std::max(w1, w2), c->fft_reserve);
+    }
+    void *work = c->arena + c->lay.fft;
+    PIC_CUFFT(cufftSetWorkArea(c->r2c, work));
+    PIC_CUFFT(cufftSetWorkArea(c->c2r, work));
+    PIC_CUFFT(cufftSetStream(c->r2c, c->st));
+    PIC_CUFFT(cufftSetStream(c->c2r, c->st));
+
+    Ctrl h;
+    memset(&h, 0, sizeof(h));
+    for (int s = 0; s < 2; ++s) {
+        char *base = c->arena + c->lay.sets + (size_t)s * 8 * c->lay.set_stride;
+        ParticleSet &ps = h.sets[s];
+        ps.cell = reinterpret_cast<int32_t *>(base);
+        for (int d = 0; d < 3; ++d) {
+            ps.o[d] = reinterpret_cast<float *>(base + (size_t)(1 + d) * c->lay.set_stride);
+            ps.v[d] = reinterpret_cast<float *>(base + (size_t)(4 + d) * c->lay.set_stride);
+        }
+        ps.pid = reinterpret_cast<int32_t *>(base + (size_t)7 * c->lay.set_stride);
+    }
+    PIC_CUDA(cudaMemcpyAsync(c->ctrl(), &h, sizeof(h), cudaMemcpyHostToDevice, c->st));
+    PIC_CUDA(cudaMemsetAsync(c->at<char>(c->lay.E4), 0, (size_t)c->ng * 16, c->st));
+    PIC_CUDA(cudaMemsetAsync(c->at<char>(c->lay.rho), 0, (size_t)c->ng * 4, c->st));
+    PIC_CUDA(cudaMemsetAsync(c->at<char>(c->lay.ring), 0,
+                             (size_t)c->prm.diag_capacity * sizeof(pic_diag_t), c->st));
+    PIC_CUDA(cudaStreamSynchronize(c->st));
+    c->bound = true;
+    c->np = 0;
+    c->step = 0;
+    c->since_sort = 0;
+    return PIC_OK;
+}
+
+int pic_set_stream(pic_handle_t c, void *stream) {
+    int r = check_ready(c);
+    if (r) return r;
+    c->st = static_cast<cudaStream_t>(stream);
+    PIC_CUFFT(cufftSetStream(c->r2c, c->st));
+    PIC_CUFFT(cufftSetStream(c->c2r, c->st));
+    return PIC_OK;
+}
+
+void pic_destroy(pic_handle_t c) {
+    if (!c) return;
+    if (c->events_made)
+        for (int p = 0; p < PIC_PHASE_COUNT; ++p)
+            for (int s = 0; s < kTimerRing; ++s)
+                for (int e = 0; e < 2; ++e) cudaEventDestroy(c->ev[p][s][e]);
+    if (c->plans) {
+        cufftDestroy(c->r2c);
+        cufftDestroy(c->c2r);
+    }
+    delete c;
+}
+
+int pic_load_particles(pic_handle_t c, const double *x, const double *v, int64_t n,
+                       int src_is_device) {
+    int r = check_ready(c);
+    if (r) return r;
+    if (n < 0) return fail(PIC_ERR_ARG, "negative particle count");
+    if (n > c->cap) return fail(PIC_ERR_CAPACITY, "%lld particles > capacity %lld",
+                                (long long)n, (long long)c->cap);
+    if (n > 0 && (!x || !v)) return fail(PIC_ERR_ARG, "null particle array");
+    if ((r = reset_ctrl(c))) return r;
+    if (src_is_device) {
+        PIC_CUDA(launch_load(x, v, n, 0, c->geom, c->inv_h, c->prm.dt, c->ctrl(), c->st));
+    } else {
+        double *sx = c->at<double>(c->lay.stage_x), *sv = c->at<double>(c->lay.stage_v);
+        for (int64_t o = 0; o < n; o += c->staging) {
+            const int64_t m = std::min<int64_t>(c->staging, n - o);
+            PIC_CUDA(cudaMemcpyAsync(sx, x + 3 * o, (size_t)m * 24, cudaMemcpyHostToDevice, c->st));
+            PIC_CUDA(cudaMemcpyAsync(sv, v + 3 * o, (size_t)m * 24, cudaMemcpyHostToDevice, c->st));
+            PIC_CUDA(launch_load(sx, sv, m, o, c->geom, c->inv_h, c->prm.dt, c->ctrl(), c->st));
+        }
+    }
+    c->np = n;
+    c->step = 0;
+    c->loaded = true;
+    if ((r = do_sort(c))) return r;
+    if (!src_is_device) PIC_CUDA(cudaStreamSynchronize(c->st));
+    return PIC_OK;
+}
+
+int pic_get_particles(pic_handle_t c, double *x, double *v, int dst_is_device) {
+    int r = check_loaded(c);
+    if (r) return r;
+    if (c->np > 0 && (!x || !v)) return fail(PIC_ERR_ARG, "null output array");
+    int32_t *inv = c->at<int32_t>(c->lay.inv);
+    PIC_CUDA(launch_invperm(c->np, c->ctrl(), inv, c->st));
+    if (dst_is_device) {
+        PIC_CUDA(launch_unload(0, c->np, inv, c->geom, c->h, c->L, c->prm.dt, c->ctrl(), x, v, c->st));
+        return PIC_OK;
+    }
+    double *sx = c->at<double>(c->lay.stage_x), *sv = c->at<double>(c->lay.stage_v);
+    for (int64_t o = 0; o < c->np; o += c->staging) {
+        const int64_t m = std::min<int64_t>(c->staging, c->np - o);
+        PIC_CUDA(launch_unload(o, m, inv, c->geom, c->h, c->L, c->prm.dt, c->ctrl(), sx, sv, c->st));
+        PIC_CUDA(cudaMemcpyAsync(x + 3 * o, sx, (size_t)m * 24, cudaMemcpyDeviceToHost, c->st));
+        PIC_CUDA(cudaMemcpyAsync(v + 3 * o, sv, (size_t)m * 24, cudaMemcpyDeviceToHost, c->st));
+    }
+    PIC_CUDA(cudaStreamSynchronize(c->st));
+    return PIC_OK;
+}
+
+int pic_get_field(pic_handle_t c, float *rho, float *E, int dst_is_device) {
+    int r = check_ready(c);
+    if (r) return r;
+    const cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (rho) PIC_CUDA(cudaMemcpyAsync(rho, c->at<float>(c->lay.rho), (size_t)c->ng * 4, k, c->st));
+    if (E) PIC_CUDA(cudaMemcpyAsync(E, c->at<float>(c->lay.E4), (size_t)c->ng * 16, k, c->st));
+    if (!dst_is_device) PIC_CUDA(cudaStreamSynchronize(c->st));
+    return PIC_OK;
+}
+
+int pic_set_rho(pic_handle_t c, const float *rho, int src_is_device) {
+    int r = check_ready(c);
+    if (r) return r;
+    if (!rho) return fail(PIC_ERR_ARG, "null rho");
+    const cudaMemcpyKind k = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    PIC_CUDA(cudaMemcpyAsync(c->at<float>(c->lay.rho), rho, (size_t)c->ng * 4, k, c->st));
+    if (!src_is_device) PIC_CUDA(cudaStreamSynchronize(c->st));
+    return PIC_OK;
+}
+
+int pic_get_counts(pic_handle_t c, int64_t *n_particles, int64_t *step) {
+    if (!c) return fail(PIC_ERR_ARG, "null handle");
+    if (n_particles) *n_particles = c->np;
+    if (step) *step = c->step;
+    return PIC_OK;
+}
+
+int pic_sort(pic_handle_t c) {
+    int r = check_loaded(c);
+    if (r) return r;
+    return do_sort(c);
+}
+
+int pic_deposit(pic_handle_t c) {
+    int r = check_loaded(c);
+    if (r) return r;
+    return do_deposit(c);
+}
+
+int pic_field_solve(pic_handle_t c) {
+    int r = check_ready(c);
+    if (r) return r;
+    return do_solve(c);
+}
+
+int pic_gather_push(pic_handle_t c) {
+    int r = check_loaded(c);
+    if (r) return r;
+    return do_gather_push(c, false);
+}
+
+int pic_step(pic_handle_t c, int n) {
+    int r = check_loaded(c);
+    if (r) return r;
+    if (n < 0) return fail(PIC_ERR_ARG, "negative step count");
+    for (int s = 0; s < n; ++s) {
+        if (c->prm.sort_period > 0 && c->since_sort >= c->prm.sort_period) {
+            if ((r = do_sort(c))) return r;
+        }
+        if ((r = do_deposit(c))) return r;
+        if ((r = do_solve(c))) return r;
+        const bool diag = c->prm.diag_every > 0 && ((c->step + 1) % c->prm.diag_every == 0);
+        if ((r = do_gather_push(c, diag))) return r;
+        if (diag && (r = do_diag(c))) return r;
+    }
+    return PIC_OK;
+}
+
+int pic_diagnostics(pic_handle_t c, pic_diag_t *out, int max_records, int *n_out) {
+    int r = check_ready(c);
+    if (r) return r;
+    if (n_out) *n_out = 0;
+    if (max_records < 0 || (max_records > 0 && !out)) return fail(PIC_ERR_ARG, "bad output buffer");
+    PIC_CUDA(cudaStreamSynchronize(c->st));
+    Ctrl h;
+    PIC_CUDA(cudaMemcpy(&h, c->ctrl(), sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    const long long cap = c->prm.diag_capacity;
+    const long long have = std::min<long long>(h.diag_written, cap);
+    const long long first = h.diag_written - have;     // oldest record kept
+    const long long want = std::min<long long>(have, max_records);
+    std::vector<pic_diag_t> all((size_t)std::max<long long>(cap, 1));
+    if (want > 0) {
+        PIC_CUDA(cudaMemcpy(all.data(), c->at<pic_diag_t>(c->lay.ring), (size_t)cap * sizeof(pic_diag_t),
+                            cudaMemcpyDeviceToHost));
+        for (long long q = 0; q < want; ++q) out[q] = all[(size_t)((first + q) % cap)];
+    }
+    if (n_out) *n_out = (int)want;
+    if (h.flags) return fail(PIC_ERR_DEVICE_FLAG, "device error flags 0x%x", h.flags);
+    return PIC_OK;
+}
+
+int pic_device_flags(pic_handle_t c, int32_t *flags, int clear) {
+    int r = check_ready(c);
+    if (r) return r;
+    PIC_CUDA(cudaStreamSynchronize(c->st));
+    int32_t f = 0;
+    PIC_CUDA(cudaMemcpy(&f, c->ctrl(), sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (flags) *flags = f;
+    if (clear) PIC_CUDA(cudaMemset(c->ctrl(), 0, sizeof(int32_t)));
+    return PIC_OK;
+}
+
+int pic_enable_timers(pic_handle_t c, int enable) {
+    int r = check_ready(c);
+    if (r) return r;
+    if (enable && !c->events_made) {
+        for (int p = 0; p < PIC_PHASE_COUNT; ++p)
+            for (int s = 0; s < kTimerRing; ++s)
+                for (int e = 0; e < 2; ++e) PIC_CUDA(cudaEventCreate(&c->ev[p][s][e]));
+        c->events_made = true;
+    }
+    if (c->timing) PIC_CUDA(cudaStreamSynchronize(c->st));
+    c->timing = enable != 0;
+    for (int p = 0; p < PIC_PHASE_COUNT; ++p) {
+        c->ev_count[p] = 0;
+        c->ev_drained[p] = 0;
+        c->ms[p] = 0.0;
+    }
+    c->launches = 0;
+    return PIC_OK;
+}
+
+int pic_read_timers(pic_handle_t c, double *ms, int64_t *calls, int64_t *kernel_launches) {
+    int r = check_ready(c);
+    if (r) return r;
+    for (int p = 0; p < PIC_PHASE_COUNT; ++p) {
+        if (c->timing && (r = drain_timer(c, p, c->ev_count[p]))) return r;
+        if (ms) ms[p] = c->ms[p];
+        if (calls) calls[p] = c->ev_count[p];
+    }
+    if (kernel_launches) *kernel_launches = c->launches;
+    return PIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+// Internal declarations of the GB300 PIC library: device data layout,
+// kernel launchers and the handle.  Not part of the C ABI (see pic.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include "pic.h"
+
+namespace pic {
+
+// ----------------------------------------------------------------------------
+// Particle store: structure of arrays, 32 bytes per particle.
+//   cell  packed stencil-base cell (i | j << 10 | k << 20), i.e. the node
+//         index of the lower corner of the particle's CIC stencil
+//   o[3]  FP32 offset in [0, 1) of the position from that node, in cells
+//   v[3]  FP32 velocity
+//   pid   load-order index (touched only by the sort and the readback)
+// Two sets exist; the sort scatters from the current one into the other and
+// flips Ctrl::cur on the device, so captured CUDA graphs stay valid.
+// ----------------------------------------------------------------------------
+struct ParticleSet {
+    int32_t *cell;
+    float *o[3];
+    float *v[3];
+    int32_t *pid;
+};
+
+// Device control block (lives in the arena).  Everything before `cur` is
+// cleared when particles are loaded.
+struct Ctrl {
+    int32_t flags;          // PIC_FLAG_* bits, OR-ed by kernels
+    int32_t n_items;        // deposit work items built by the last sort
+    unsigned long long stray;   // particles deposited outside their tile (stat)
+    long long step;         // steps since the last load
+    long long diag_written; // diagnostic records written since the load
+    double mode[2];         // tracked Fourier coefficient of the last solve
+    int32_t cur;            // which ParticleSet holds the particles
+    int32_t pad0;
+    ParticleSet sets[2];
+};
+
+constexpr int kCellBits = 10;
+constexpr int kCellMask = (1 << kCellBits) - 1;
+constexpr int kMaxN = 1 << kCellBits;      // 1024 nodes per axis
+
+__host__ __device__ __forceinline__ int32_t pack_cell(int i, int j, int k) {
+    return i | (j << kCellBits) | (k << (2 * kCellBits));
+}
+__host__ __device__ __forceinline__ int cell_i(int32_t c) { return c & kCellMask; }
+__host__ __device__ __forceinline__ int cell_j(int32_t c) { return (c >> kCellBits) & kCellMask; }
+__host__ __device__ __forceinline__ int cell_k(int32_t c) { return (c >> (2 * kCellBits)) & kCellMask; }
+
+// Grid geometry passed by value to kernels.
+struct Geom {
+    int n[3];          // nodes per axis
+    int nh;            // Nx/2 + 1 (R2C innermost length)
+    int tile[3];       // deposit tile (cells per axis)
+    int ntile[3];      // tiles per axis = ceil(n / tile)
+    int guard;         // guard layers around a tile
+    int tvol;          // tile[0]*tile[1]*tile[2]
+    float h[3];        // cell size
+    float inv_h[3];
+};
+
+// Per-step push constants (FP32, precomputed on the host in FP64).
+struct PushConst {
+    float qm_half_dt;      // (q/m) dt / 2
+    float dt_over_h[3];    // dt / h_d
+    float t[3];            // (q/m) B dt / 2
+    float s[3];            // 2 t / (1 + |t|^2)
+    float wz2;             // quadrupole strength
+    float half_n[3];       // N_d / 2 (box centre in cells)
+};
+
+// Diagnostic partial layout: 4 doubles per block.
+constexpr int kDiagFieldBlocks = 512;
+constexpr int kMaxPushBlocks = 152 * 8;
+
+// ----------------------------------------------------------------------------
+// kernel launchers (defined in the k_*.cu files); all enqueue on `st`.
+// ----------------------------------------------------------------------------
+cudaError_t launch_load(const double *x, const double *v, int64_t m, int64_t base,
+                        const Geom &g, const double *inv_h_d, double dt, Ctrl *ctrl,
+                        cudaStream_t st);
+cudaError_t launch_invperm(int64_t n, Ctrl *ctrl, int32_t *inv, cudaStream_t st);
+cudaError_t launch_unload(int64_t o0, int64_t m, const int32_t *inv, const Geom &g,
+                          const double *h_d, const double *L_d, double dt, const Ctrl *ctrl,
+                          double *x, double *v, cudaStream_t st);
+
+cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t *bins,
+                        int64_t nbins, int32_t *scan_tmp, int32_t *tile_items,
+                        int2 *tile_range, int4 *items, cudaStream_t st);
+
+cudaError_t launch_deposit(int64_t n, const Geom &g, const Ctrl *ctrl, const int4 *items,
+                           int max_items, float qscale, float *rho, Ctrl *ctrl_w,
+                           int grid_blocks, int sparse_below, cudaStream_t st);
+cudaError_t launch_deposit_direct(int64_t n, const Geom &g, const Ctrl *ctrl, float qscale,
+                                  float *rho, cudaStream_t st);
+
+cudaError_t launch_gather_push(int64_t n, const Geom &g, const PushConst &pc, bool diag,
+                               Ctrl *ctrl, const float4 *E4, double *part, int blocks,
+                               int threads, cudaStream_t st);
+
+cudaError_t launch_green(const Geom &g, const double *L_d, const float2 *rho_hat,
+                         float2 *E_hat, int64_t nhalf, const int *mode_idx, int mode_comp,
+                         int mode_conj, Ctrl *ctrl, cudaStream_t st);
+cudaError_t launch_diag_field(const Geom &g, const float *rho, const float4 *E4,
+                              double *part, cudaStream_t st);
+cudaError_t launch_diag_finalize(const double *field_part, const double *push_part,
+                                 int push_blocks, double dV, double mp, double dt,
+                                 Ctrl *ctrl, pic_diag_t *ring, int ring_cap, cudaStream_t st);
+
+}  // namespace pic

@@ -1,0 +1,98 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every function declared in include/pic.h, and validates configurations."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2205_11052_gb300 import build, capi
+from paper_2205_11052_gb300.sim import make_structs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return capi.load_library()
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(pic_\w+)\s*\(", src, re.M))
+    return names
+
+
+def test_every_declared_function_is_exported(lib):
+    declared = _declared()
+    assert "pic_step" in declared and "pic_create" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    # and the binding knows each of them under the same name
+    assert declared == set(capi.exported_symbols())
+
+
+def _create(**kw):
+    args = dict(n=(16, 16, 16), L=(1.0, 1.0, 1.0), n_particles=1000, dt=0.1)
+    args.update(kw)
+    return capi.pic_create(*make_structs(**args))
+
+
+def test_create_and_sizes_without_gpu(lib):
+    h = _create()
+    s = capi.pic_buffer_sizes(h)
+    assert s.workspace_bytes > 16 ** 3 * (4 + 16) + 2 * 1000 * 32
+    assert s.workspace_align == 256
+    assert s.grid_nodes == 16 ** 3
+    assert s.particle_capacity == 1000
+    capi.pic_destroy(h)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(n=(0, 4, 4)), dict(n=(1, 4, 4)), dict(n=(4, 2000, 4)), dict(L=(1.0, -1.0, 1.0)),
+    dict(L=(1.0, float("nan"), 1.0)), dict(dt=0.0), dict(dt=float("inf")),
+    dict(n_particles=-1), dict(n_particles=2 ** 31), dict(q_over_m=0.0),
+    dict(mode=(9, 0, 0)), dict(mode_comp=3), dict(block=48), dict(block=512),
+    dict(chunk=8), dict(guard=-1), dict(B=(0.0, float("nan"), 0.0)),
+])
+def test_create_rejects_bad_configs(lib, kw):
+    with pytest.raises(capi.PicError) as e:
+        _create(**kw)
+    assert e.value.code == capi.PIC_ERR_ARG
+    assert capi.pic_last_error()
+
+
+def test_calls_before_binding_are_state_errors(lib):
+    h = _create()
+    with pytest.raises(capi.PicError) as e:
+        capi.pic_step(h, 1)
+    assert e.value.code == capi.PIC_ERR_STATE
+    with pytest.raises(capi.PicError) as e:
+        capi.pic_deposit(h)
+    assert e.value.code == capi.PIC_ERR_STATE
+    capi.pic_destroy(h)
+
+
+def test_small_arena_is_a_capacity_error_before_any_device_work(lib):
+    h = _create()
+    s = capi.pic_buffer_sizes(h)
+    rc = lib.pic_bind_workspace(h, C.c_void_p(256), C.c_size_t(s.workspace_bytes - 1), None)
+    assert rc == capi.PIC_ERR_CAPACITY
+    rc = lib.pic_bind_workspace(h, C.c_void_p(100), C.c_size_t(s.workspace_bytes), None)
+    assert rc == capi.PIC_ERR_ARG
+    capi.pic_destroy(h)
+
+
+def test_library_missing_fails_loudly(tmp_path):
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        # a fresh loader pointed at a path that does not exist
+        capi._lib_saved = capi._lib
+        try:
+            capi._lib = None
+            capi.load_library(str(tmp_path / "nope.so"))
+        finally:
+            capi._lib = capi._lib_saved
