@@ -133,16 +133,15 @@ class ClockSampler:
 # ---------------------------------------------------------------- oracle arm
 
 def oracle_sample(args, n_particles):
+    """A bounded sample of the benchmark workload: the same grid and physics,
+    n_particles drawn from the same Landau distribution."""
     import pic_inputs as pi
 
-    ppc = max(1, n_particles // args.grid ** 3)
-    w = pi.landau(n=args.grid, ppc=1, seed=1001)
-    # a bounded sample of the same workload: the full grid, fewer particles
-    w = pi.landau(n=args.grid, ppc=ppc, seed=1001) if ppc > 1 else w
+    ppc = max(1, -(-n_particles // args.grid ** 3))
+    w = pi.landau(n=args.grid, ppc=ppc, seed=1001)
     if w.n_particles > n_particles:
         w.x = w.x[:n_particles].copy()
         w.v = w.v[:n_particles].copy()
-    w.Q = -(w.L[0] ** 3)
     return w
 
 

@@ -329,3 +329,157 @@ def run(x: np.ndarray, v: np.ndarray, grid: Grid, params: Params, n_steps: int,
         else:
             x, v = step(x, v, grid, params)
     return x, v, hist
+
+
+# ---------------------------------------------------------------------------
+# discrete adjoint (not in the paper: gradient of the final field energy)
+#
+# The step above, written on the half-step positions y_n = x_{n+1/2}:
+#     e_n     = G(y_n) S D(y_n) + E_ext(y_n)
+#     v_{n+1} = v_n + c e_n,            c = dt q/m      (B = 0)
+#     y_{n+1} = y_n + dt v_{n+1}
+# with y_0 = x_0 + dt/2 v_0.  The objective is the weighted field energy of
+# the field the last of n_steps steps uses,
+#     J = sum_d w_d h^3 sum_g E_d,g^2,   E = S D(y_{n_steps - 1}).
+# Its reverse sweep, step by step, is the plain chain rule of these lines:
+#     lv_tot = lv' + dt ly'
+#     le     = c lv_tot                          (adjoint of e)
+#     ly     = ly' + (dG/dy . E)^T le            (weight gradients, E fixed)
+#              + Ext^T le                        (linear quadrupole)
+#              + (dD/dy)^T S^T G^T le            (through the self field)
+#     lv     = lv_tot
+# with S^T = -S for the spectral gradient (purely imaginary, odd symbol).
+# ---------------------------------------------------------------------------
+
+def cic_weight_gradients(x: np.ndarray, grid: Grid):
+    """(nodes, weights, dweights): dweights[:, corner, j] = dW/dx_j."""
+    h = grid.h
+    n = np.asarray(grid.n, dtype=np.int64)
+    s = x / h - 0.5
+    base = np.floor(s)
+    f = s - base
+    base = base.astype(np.int64) % n
+    N = x.shape[0]
+    nodes = np.empty((N, 8), dtype=np.int64)
+    w = np.empty((N, 8), dtype=np.float64)
+    dw = np.empty((N, 8, 3), dtype=np.float64)
+    for corner in range(8):
+        bits = (corner & 1, (corner >> 1) & 1, (corner >> 2) & 1)
+        fac = []
+        dfac = []
+        for d in range(3):
+            if bits[d]:
+                fac.append(f[:, d])
+                dfac.append(np.full(N, 1.0 / h[d]))
+            else:
+                fac.append(1.0 - f[:, d])
+                dfac.append(np.full(N, -1.0 / h[d]))
+        ix = (base[:, 0] + bits[0]) % n[0]
+        iy = (base[:, 1] + bits[1]) % n[1]
+        iz = (base[:, 2] + bits[2]) % n[2]
+        nodes[:, corner] = ix + n[0] * (iy + n[1] * iz)
+        w[:, corner] = fac[0] * fac[1] * fac[2]
+        dw[:, corner, 0] = dfac[0] * fac[1] * fac[2]
+        dw[:, corner, 1] = fac[0] * dfac[1] * fac[2]
+        dw[:, corner, 2] = fac[0] * fac[1] * dfac[2]
+    return nodes, w, dw
+
+
+def solve_field_transpose(lamE: np.ndarray, grid: Grid) -> np.ndarray:
+    """S^T applied to a field adjoint (3, Nz, Ny, Nx) -> rho adjoint.
+
+    S_d has the symbol -i k_d / |k|^2 (k = 0 and the Nyquist gradient zeroed);
+    as a real operator its transpose has the conjugate symbol +i k_d / |k|^2.
+    """
+    ks, kgrad = _wavenumbers(grid)
+    KZ, KY, KX = np.meshgrid(ks[2], ks[1], ks[0], indexing="ij")
+    GZ, GY, GX = np.meshgrid(kgrad[2], kgrad[1], kgrad[0], indexing="ij")
+    k2 = KX ** 2 + KY ** 2 + KZ ** 2
+    k2[0, 0, 0] = 1.0
+    acc = np.zeros(grid.shape, dtype=np.complex128)
+    for d, G in enumerate((GX, GY, GZ)):
+        acc += 1j * G / k2 * np.fft.fftn(lamE[d])
+    acc[0, 0, 0] = 0.0
+    return np.fft.ifftn(acc).real
+
+
+def field_energy(y: np.ndarray, grid: Grid, params: Params, weights=(1.0, 1.0, 1.0)) -> float:
+    """J = sum_d w_d h^3 sum_g E_d^2 with E = S D(y)."""
+    qp = params.Q / y.shape[0]
+    E = solve_field(deposit(y, grid, qp), grid)
+    return float(sum(weights[d] * grid.cell_volume * np.sum(E[d] ** 2) for d in range(3)))
+
+
+def field_energy_gradient(y: np.ndarray, grid: Grid, params: Params, weights=(1.0, 1.0, 1.0)):
+    """dJ/dy for J = field_energy(y): (dD/dy)^T S^T (2 h^3 w E)."""
+    N = y.shape[0]
+    qp = params.Q / N
+    E = solve_field(deposit(y, grid, qp), grid)
+    lamE = np.stack([2.0 * weights[d] * grid.cell_volume * E[d] for d in range(3)])
+    lamrho = solve_field_transpose(lamE, grid)
+    nodes, _, dw = cic_weight_gradients(y, grid)
+    lr = lamrho.ravel()[nodes]                      # (N, 8)
+    return (qp / grid.cell_volume) * np.einsum("pc,pcj->pj", lr, dw)
+
+
+def adjoint_step(y: np.ndarray, lam_y: np.ndarray, lam_v: np.ndarray, grid: Grid,
+                 params: Params):
+    """Pull (lam_y, lam_v) of (y_{n+1}, v_{n+1}) back to (y_n, v_n)."""
+    if any(b != 0.0 for b in params.B):
+        raise NotImplementedError("adjoint of the magnetic rotation")
+    N = y.shape[0]
+    qp = params.Q / N if N else 0.0
+    c = params.dt * params.q_over_m
+    E = solve_field(deposit(y, grid, qp), grid)
+    lv_tot = lam_v + params.dt * lam_y
+    le = c * lv_tot
+    nodes, w, dw = cic_weight_gradients(y, grid)
+    # (dG/dy . E)^T le : sum_corner dW/dy_j (le . E_corner)
+    Eg = np.stack([E[d].ravel()[nodes] for d in range(3)], axis=-1)     # (N, 8, 3)
+    s = np.einsum("pcd,pd->pc", Eg, le)
+    ly = lam_y + np.einsum("pc,pcj->pj", s, dw)
+    if params.wz2 != 0.0:
+        ly = ly + params.wz2 * le * np.array([-0.5, -0.5, 1.0])
+    # through the self field: G^T le -> S^T -> (dD/dy)^T
+    lamE = np.stack([deposit(y, grid, le[:, d]) * grid.cell_volume for d in range(3)])
+    lamrho = solve_field_transpose(lamE, grid)
+    lr = lamrho.ravel()[nodes]
+    ly = ly + (qp / grid.cell_volume) * np.einsum("pc,pcj->pj", lr, dw)
+    return ly, lv_tot
+
+
+def run_with_gradient(x0: np.ndarray, v0: np.ndarray, grid: Grid, params: Params,
+                      n_steps: int, weights=(1.0, 1.0, 1.0)):
+    """J of the field used by the last of n_steps steps, and dJ/dx0, dJ/dv0.
+
+    Forward: y_0 = x_0 + dt/2 v_0, then n_steps - 1 updates of (y, v); the
+    objective is the field energy at y_{n_steps-1}.  The forward states are
+    kept (the oracle stores them all; it has no checkpointing)."""
+    dt = params.dt
+    N = x0.shape[0]
+    qp = params.Q / N
+    c = dt * params.q_over_m
+    ys = [wrap(x0 + 0.5 * dt * v0, grid)]
+    v = v0.copy()
+    for _ in range(n_steps - 1):
+        y = ys[-1]
+        E = solve_field(deposit(y, grid, qp), grid)
+        e = gather(y, E, grid)
+        if params.wz2 != 0.0:
+            e = e + external_field(y, grid, params.wz2)
+        v = v + c * e
+        ys.append(wrap(y + dt * v, grid))
+    J = field_energy(ys[-1], grid, params, weights)
+    ly = field_energy_gradient(ys[-1], grid, params, weights)
+    lv = np.zeros_like(ly)
+    for n in range(n_steps - 2, -1, -1):
+        ly, lv = adjoint_step(ys[n], ly, lv, grid, params)
+    dx0 = ly
+    dv0 = lv + 0.5 * dt * ly
+    return J, dx0, dv0
+
+
+def cosine_sample_dalpha(x: np.ndarray, alpha: float, k: float) -> np.ndarray:
+    """d x / d alpha of the inverse-transform sample x(u; alpha) of
+    1 + alpha cos(k x): from x + (alpha/k) sin(k x) = u L at fixed u."""
+    return -(np.sin(k * x) / k) / (1.0 + alpha * np.cos(k * x))

@@ -88,12 +88,6 @@ def halton(n: int, dim: int, rng: np.random.Generator, start: int = 1) -> np.nda
     return np.stack(cols, axis=1)
 
 
-def _uniforms(n: int, dim: int, rng: np.random.Generator, quiet: bool) -> np.ndarray:
-    if quiet:
-        return halton(n, dim, rng)
-    return rng.random((n, dim))
-
-
 def _normals_from_uniform(u: np.ndarray) -> np.ndarray:
     from scipy.special import ndtri
 
@@ -107,22 +101,45 @@ def _normals_from_uniform(u: np.ndarray) -> np.ndarray:
 # --------------------------------------------------------------------------
 
 def sample_cosine_density(u: np.ndarray, L: float, alpha: float, k: float,
-                          iters: int = 12) -> np.ndarray:
-    """Invert F(x) = (x + (alpha/k) sin(k x)) / L = u by safeguarded Newton.
+                          iters: int = 4) -> np.ndarray:
+    """Invert F(x) = (x + (alpha/k) sin(k x)) / L = u by Newton iteration.
 
     Valid when k L is a multiple of 2 pi (the perturbation integrates to zero)
-    and |alpha| < 1 (F strictly increasing).  The map u -> x is smooth in
-    alpha, which the adjoint's derivative with respect to alpha relies on.
+    and |alpha| < 1 (F strictly increasing).  The start x0 = uL - (alpha/k)
+    sin(k uL) is exact to first order in alpha, so a few quadratically
+    converging steps reach rounding level; more are taken if the residual says
+    so.  The map u -> x is smooth in alpha.
     """
     target = u * L
-    x = target.copy()
-    for _ in range(iters):
+    x = target - (alpha / k) * np.sin(k * target)
+    for it in range(64):
         g = x + (alpha / k) * np.sin(k * x) - target
         dg = 1.0 + alpha * np.cos(k * x)
-        x = x - g / dg
+        x -= g / dg
         np.clip(x, 0.0, L, out=x)
+        if it + 1 >= iters and np.max(np.abs(g), initial=0.0) < 1e-13 * L:
+            break
     x = np.where(x >= L, 0.0, x)
     return x
+
+
+def _chunked(N: int, seed: int, chunk: int, fill, workers=None):
+    """Run fill(rng, start, stop) over [0, N) in chunks, each with its own
+    stream spawned from ``seed`` (deterministic for any worker count)."""
+    import concurrent.futures as cf
+    import os
+
+    starts = list(range(0, N, chunk))
+    seqs = np.random.SeedSequence(seed).spawn(max(1, len(starts)))
+    jobs = [(np.random.Generator(np.random.PCG64(seqs[i])), s, min(N, s + chunk))
+            for i, s in enumerate(starts)]
+    nw = workers or min(len(jobs), os.cpu_count() or 1, 32)
+    if nw <= 1 or len(jobs) <= 1:
+        for j in jobs:
+            fill(*j)
+        return
+    with cf.ThreadPoolExecutor(max_workers=nw) as ex:
+        list(ex.map(lambda j: fill(*j), jobs))
 
 
 def _wrap(x: np.ndarray, L) -> np.ndarray:
@@ -136,7 +153,7 @@ def _wrap(x: np.ndarray, L) -> np.ndarray:
 # --------------------------------------------------------------------------
 
 def landau(n=16, ppc=8, alpha=0.05, k=0.5, seed=1000, dt=0.05, n_steps=20,
-           form="product", quiet=False, chunk=1 << 22) -> Workload:
+           form="product", quiet=False, chunk=1 << 20) -> Workload:
     """Landau damping initial condition (Section 4.1, Eq. landau_f).
 
     ``form="product"`` draws the paper's density
@@ -152,18 +169,24 @@ def landau(n=16, ppc=8, alpha=0.05, k=0.5, seed=1000, dt=0.05, n_steps=20,
     x = np.empty((N, 3), dtype=np.float64)
     v = np.empty((N, 3), dtype=np.float64)
     if form == "product":
-        shift = rng.random(6) if quiet else None
-        for s in range(0, N, chunk):
-            e = min(N, s + chunk)
-            if quiet:
+        if quiet:
+            shift = rng.random(6)
+            for s in range(0, N, chunk):
+                e = min(N, s + chunk)
                 idx = np.arange(s + 1, e + 1, dtype=np.int64)
                 u = np.stack([np.mod(_vdc(idx, _PRIMES[d]) + shift[d], 1.0)
                               for d in range(6)], axis=1)
-            else:
-                u = rng.random((e - s, 3))
-            for d in range(3):
-                x[s:e, d] = sample_cosine_density(u[:, d], L, alpha, k)
-            v[s:e] = _normals_from_uniform(u[:, 3:6]) if quiet else rng.standard_normal((e - s, 3))
+                for d in range(3):
+                    x[s:e, d] = sample_cosine_density(u[:, d], L, alpha, k)
+                v[s:e] = _normals_from_uniform(u[:, 3:6])
+        else:
+            def fill(g, s, e):
+                u = g.random((e - s, 3))
+                for d in range(3):
+                    x[s:e, d] = sample_cosine_density(u[:, d], L, alpha, k)
+                v[s:e] = g.standard_normal((e - s, 3))
+
+            _chunked(N, seed, chunk, fill)
     elif form == "literal":
         filled = 0
         while filled < N:
@@ -186,8 +209,7 @@ def landau(n=16, ppc=8, alpha=0.05, k=0.5, seed=1000, dt=0.05, n_steps=20,
 
 
 def bump_on_tail(n=64, ppc=16, alpha=0.05, k=0.1, seed=1003, dt=0.05, n_steps=200,
-                 eps=0.1, v_beam=4.0, sigma_beam=0.3, sigma_bulk=1.0,
-                 bulk_scale=None, chunk=1 << 22) -> Workload:
+                 eps=0.1, v_beam=4.0, sigma_beam=0.3, sigma_bulk=1.0, chunk=1 << 20) -> Workload:
     """Bump-on-tail initial condition on [0, 2 pi / k)^3.
 
     Density 1 + alpha cos(k z) (Eq. twostream_f's spatial factor) drawn by
@@ -203,18 +225,19 @@ def bump_on_tail(n=64, ppc=16, alpha=0.05, k=0.1, seed=1003, dt=0.05, n_steps=20
     rng = np.random.Generator(np.random.PCG64(seed))
     x = np.empty((N, 3), dtype=np.float64)
     v = np.empty((N, 3), dtype=np.float64)
-    for s in range(0, N, chunk):
-        e = min(N, s + chunk)
+    def fill(r, s, e):
         m = e - s
-        u = rng.random((m, 3))
+        u = r.random((m, 3))
         x[s:e, 0] = u[:, 0] * L
         x[s:e, 1] = u[:, 1] * L
         x[s:e, 2] = sample_cosine_density(u[:, 2], L, alpha, k)
-        g = rng.standard_normal((m, 3))
-        beam = rng.random(m) < eps
+        g = r.standard_normal((m, 3))
+        beam = r.random(m) < eps
         v[s:e, 0] = sigma_bulk * g[:, 0]
         v[s:e, 1] = sigma_bulk * g[:, 1]
         v[s:e, 2] = np.where(beam, v_beam + sigma_beam * g[:, 2], sigma_bulk * g[:, 2])
+
+    _chunked(N, seed, chunk, fill)
     x = _wrap(x, Ls)
     return Workload(name=f"bump_on_tail_{nn[0]}x{nn[1]}x{nn[2]}_ppc{ppc}", n=nn, L=Ls, x=x, v=v,
                     q_over_m=-1.0, Q=-(L ** 3), dt=dt, n_steps=n_steps, mode=(0, 0, 1),
@@ -223,7 +246,7 @@ def bump_on_tail(n=64, ppc=16, alpha=0.05, k=0.1, seed=1003, dt=0.05, n_steps=20
 
 
 def two_stream(n=32, ppc=8, alpha=0.01, k=0.5, seed=1005, dt=0.05, n_steps=200,
-               eps=0.5, sigma=0.1, vb1=-math.pi / 2, vb2=math.pi / 2, chunk=1 << 22) -> Workload:
+               eps=0.5, sigma=0.1, vb1=-math.pi / 2, vb2=math.pi / 2, chunk=1 << 20) -> Workload:
     """Two-stream / bump-on-tail family with equal thermal spread (Eq. twostream_f).
 
     The paper's two-stream case is eps = 0.5, sigma = 0.1, k = 0.5,
@@ -237,17 +260,18 @@ def two_stream(n=32, ppc=8, alpha=0.01, k=0.5, seed=1005, dt=0.05, n_steps=200,
     rng = np.random.Generator(np.random.PCG64(seed))
     x = np.empty((N, 3), dtype=np.float64)
     v = np.empty((N, 3), dtype=np.float64)
-    for s in range(0, N, chunk):
-        e = min(N, s + chunk)
+    def fill(r, s, e):
         m = e - s
-        u = rng.random((m, 3))
+        u = r.random((m, 3))
         x[s:e, 0] = u[:, 0] * L
         x[s:e, 1] = u[:, 1] * L
         x[s:e, 2] = sample_cosine_density(u[:, 2], L, alpha, k)
-        g = rng.standard_normal((m, 3))
-        second = rng.random(m) < eps
+        g = r.standard_normal((m, 3))
+        second = r.random(m) < eps
         v[s:e] = sigma * g
         v[s:e, 2] += np.where(second, vb2, vb1)
+
+    _chunked(N, seed, chunk, fill)
     x = _wrap(x, Ls)
     return Workload(name=f"two_stream_{nn[0]}x{nn[1]}x{nn[2]}_ppc{ppc}", n=nn, L=Ls, x=x, v=v,
                     q_over_m=-1.0, Q=-(L ** 3), dt=dt, n_steps=n_steps, mode=(0, 0, 1),
@@ -255,7 +279,7 @@ def two_stream(n=32, ppc=8, alpha=0.01, k=0.5, seed=1005, dt=0.05, n_steps=200,
 
 
 def penning(n=256, n_particles=130_000_000, L=20.0, sigma=(1.0, 1.0, 2.0), Bz=5.0,
-            wz2=1.0, Q=-1562.5, seed=1002, dt=0.05, n_steps=100, chunk=1 << 22) -> Workload:
+            wz2=1.0, Q=-1562.5, seed=1002, dt=0.05, n_steps=100, chunk=1 << 20) -> Workload:
     """Penning trap bunch (Section 4.3): Gaussian in all phase-space variables.
 
     Positions ~ N(L/2, sigma_d^2) per axis (wrapped into the periodic box),
@@ -271,11 +295,12 @@ def penning(n=256, n_particles=130_000_000, L=20.0, sigma=(1.0, 1.0, 2.0), Bz=5.
     x = np.empty((N, 3), dtype=np.float64)
     v = np.empty((N, 3), dtype=np.float64)
     sig = np.asarray(sigma, dtype=np.float64)
-    for s in range(0, N, chunk):
-        e = min(N, s + chunk)
+    def fill(r, s, e):
         m = e - s
-        x[s:e] = 0.5 * L + sig * rng.standard_normal((m, 3))
-        v[s:e] = rng.standard_normal((m, 3))
+        x[s:e] = 0.5 * L + sig * r.standard_normal((m, 3))
+        v[s:e] = r.standard_normal((m, 3))
+
+    _chunked(N, seed, chunk, fill)
     x = _wrap(x, Ls)
     return Workload(name=f"penning_{nn[0]}x{nn[1]}x{nn[2]}_np{N}", n=nn, L=Ls, x=x, v=v,
                     q_over_m=-1.0, Q=float(Q), dt=dt, B=(0.0, 0.0, float(Bz)), wz2=float(wz2),
@@ -283,7 +308,7 @@ def penning(n=256, n_particles=130_000_000, L=20.0, sigma=(1.0, 1.0, 2.0), Bz=5.
                     meta=dict(sigma=tuple(sig), seed=seed))
 
 
-def uniform_plasma(n=32, ppc=8, L=None, seed=1004, dt=0.05, n_steps=20, chunk=1 << 22) -> Workload:
+def uniform_plasma(n=32, ppc=8, L=None, seed=1004, dt=0.05, n_steps=20, chunk=1 << 20) -> Workload:
     """Uniform positions and unit Maxwellian velocities (Section 4.4's layout)."""
     nn = (n, n, n) if np.isscalar(n) else tuple(int(a) for a in n)
     if L is None:
@@ -294,10 +319,11 @@ def uniform_plasma(n=32, ppc=8, L=None, seed=1004, dt=0.05, n_steps=20, chunk=1 
     x = np.empty((N, 3), dtype=np.float64)
     v = np.empty((N, 3), dtype=np.float64)
     Lv = np.asarray(Ls)
-    for s in range(0, N, chunk):
-        e = min(N, s + chunk)
-        x[s:e] = rng.random((e - s, 3)) * Lv
-        v[s:e] = rng.standard_normal((e - s, 3))
+    def fill(r, s, e):
+        x[s:e] = r.random((e - s, 3)) * Lv
+        v[s:e] = r.standard_normal((e - s, 3))
+
+    _chunked(N, seed, chunk, fill)
     x = _wrap(x, Ls)
     return Workload(name=f"uniform_{nn[0]}x{nn[1]}x{nn[2]}_ppc{ppc}", n=nn, L=Ls, x=x, v=v,
                     q_over_m=-1.0, Q=-float(np.prod(Lv)), dt=dt, n_steps=n_steps,

@@ -286,3 +286,70 @@ def test_time_reversibility_with_self_field(Bz):
     dx -= np.asarray(grid.L) * np.round(dx / np.asarray(grid.L))
     assert np.max(np.abs(dx)) < 1e-10
     assert np.max(np.abs(-v - w.v)) < 1e-10
+
+
+# ---------------------------------------------------------------- adjoint
+
+def test_field_solve_transpose_identity():
+    """<S rho, lamE> = <rho, S^T lamE> for the spectral field operator."""
+    grid = GRID
+    rho = RNG.standard_normal(grid.shape)
+    lamE = RNG.standard_normal((3,) + grid.shape)
+    lhs = float(np.sum(po.solve_field(rho, grid) * lamE))
+    rhs = float(np.sum(rho * po.solve_field_transpose(lamE, grid)))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + 1.0)
+
+
+def test_cic_weight_gradients_are_derivatives_of_the_weights():
+    grid = GRID
+    x = _random_positions(grid, 50, RNG)
+    nodes, w, dw = po.cic_weight_gradients(x, grid)
+    eps = 1e-7 * float(np.min(grid.h))
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = eps
+        n_p, w_p = po.cic_stencil(x + e, grid)
+        n_m, w_m = po.cic_stencil(x - e, grid)
+        same = np.all(n_p == nodes, axis=1) & np.all(n_m == nodes, axis=1)
+        fd = (w_p - w_m) / (2 * eps)
+        assert np.max(np.abs(fd[same] - dw[same, :, j])) < 1e-6 / float(np.min(grid.h))
+
+
+@pytest.mark.parametrize("wz2,weights", [(0.0, (0.0, 0.0, 1.0)), (0.3, (1.0, 1.0, 1.0))])
+def test_adjoint_matches_central_differences(wz2, weights):
+    """Directional derivative of J along a random (dx0, dv0) equals the
+    adjoint's inner product (J = final weighted field energy, 6 steps)."""
+    w = pi.bump_on_tail(n=8, ppc=4, seed=5, alpha=0.2, k=0.5)
+    grid = po.Grid(w.n, w.L)
+    p = po.Params(dt=0.1, Q=w.Q, wz2=wz2)
+    J, dx, dv = po.run_with_gradient(w.x, w.v, grid, p, 6, weights)
+    rng = np.random.default_rng(1)
+    dX = rng.standard_normal(w.x.shape)
+    dV = rng.standard_normal(w.v.shape)
+    eps = 1e-5
+    Jp = po.run_with_gradient(w.x + eps * dX, w.v + eps * dV, grid, p, 6, weights)[0]
+    Jm = po.run_with_gradient(w.x - eps * dX, w.v - eps * dV, grid, p, 6, weights)[0]
+    fd = (Jp - Jm) / (2 * eps)
+    ad = float(np.sum(dx * dX) + np.sum(dv * dV))
+    assert abs(fd - ad) <= 1e-6 * abs(ad)
+
+
+def test_gradient_with_respect_to_the_perturbation_amplitude():
+    """dJ/dalpha through the inverse-transform sample x0(u; alpha) (fixed u)
+    equals the central difference of J over regenerated particles."""
+    alpha, k = 0.2, 0.5
+    grid_args = dict(n=8, ppc=4, seed=5, k=k)
+    w = pi.bump_on_tail(alpha=alpha, **grid_args)
+    grid = po.Grid(w.n, w.L)
+    p = po.Params(dt=0.1, Q=w.Q)
+    wts = (0.0, 0.0, 1.0)
+    J, dx, _ = po.run_with_gradient(w.x, w.v, grid, p, 6, wts)
+    dadz = po.cosine_sample_dalpha(w.x[:, 2], alpha, k)
+    ad = float(np.sum(dx[:, 2] * dadz))
+    eps = 1e-6
+    wp = pi.bump_on_tail(alpha=alpha + eps, **grid_args)
+    wm = pi.bump_on_tail(alpha=alpha - eps, **grid_args)
+    assert np.array_equal(wp.v, w.v) and np.array_equal(wp.x[:, :2], w.x[:, :2])
+    fd = (po.run_with_gradient(wp.x, wp.v, grid, p, 6, wts)[0]
+          - po.run_with_gradient(wm.x, wm.v, grid, p, 6, wts)[0]) / (2 * eps)
+    assert abs(fd - ad) <= 1e-5 * abs(ad)
