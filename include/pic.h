@@ -240,6 +240,43 @@ int pic_enable_timers(pic_handle_t h, int enable);
 int pic_read_timers(pic_handle_t h, double ms[PIC_PHASE_COUNT],
                     int64_t calls[PIC_PHASE_COUNT], int64_t *kernel_launches);
 
+/* ------------------------------------------------------------ no allocation */
+
+/* Largest grid accepted by pic_field_energy_noalloc (512^3 nodes). */
+#define PIC_NOALLOC_MAX_NODES 134217728LL
+
+/* Field energies and grid charge without any device allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory while they run -- e.g. a host application that
+ * hands this code a fixed memory budget it manages itself, or a time-critical
+ * loop where cudaMalloc (which can synchronise the device, or fail once memory
+ * is fragmented) is forbidden.  Such callers cannot bind a workspace arena, so
+ * the reduction keeps its scratch (per-block FP64 partials, 256 KiB) in a
+ * statically sized __device__ array of the library that every GPU loading the
+ * library holds until the process exits.
+ *
+ * Computes, on the stream (async), into out[0..3] on the device:
+ *   Wx, Wy, Wz = cell_volume * sum_g E_d,g^2   and   Q = cell_volume * sum_g rho_g,
+ * the same quantities as the diagnostics of pic_step (FP64 sums of FP32 data).
+ *   rho    device pointer, n_nodes FP32 values
+ *   E      device pointer, n_nodes x 4 FP32 (Ex, Ey, Ez, unused), 16-byte aligned
+ *          (the layout pic_get_field returns)
+ *   out    device pointer to 4 doubles; the caller owns inputs and outputs
+ *   stream cudaStream_t as void*, NULL = legacy default stream
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before capturing a stream into a CUDA graph.  All calls share the one
+ * scratch array, which keeps the last call's partials (every partial a call
+ * reads is written by that same call, so nothing needs clearing); calls whose
+ * kernels overlap on the GPU race on it and must be ordered by the caller.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * Errors: PIC_ERR_ARG (null pointer, n_nodes < 1, cell_volume <= 0, E
+ * misaligned), PIC_ERR_CAPACITY (n_nodes > PIC_NOALLOC_MAX_NODES),
+ * PIC_ERR_CUDA (launch failure); pic_last_error() describes it. */
+int pic_field_energy_noalloc(const float *rho, const float *E, int64_t n_nodes,
+                             double cell_volume, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

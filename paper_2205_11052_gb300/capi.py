@@ -88,6 +88,8 @@ _SIGNATURES = {
     "pic_diagnostics": (C.c_int, [pic_handle_t, C.POINTER(pic_diag_t), C.c_int,
                                   C.POINTER(C.c_int)]),
     "pic_device_flags": (C.c_int, [pic_handle_t, C.POINTER(C.c_int32), C.c_int]),
+    "pic_field_energy_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
+                                           C.c_void_p, C.c_void_p]),
     "pic_enable_timers": (C.c_int, [pic_handle_t, C.c_int]),
     "pic_read_timers": (C.c_int, [pic_handle_t, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64)]),
@@ -248,3 +250,14 @@ def pic_read_timers(h):
     launches = C.c_int64()
     check(_call("pic_read_timers", h, ms, calls, C.byref(launches)), "pic_read_timers")
     return {p: (ms[i], calls[i]) for i, p in enumerate(PHASES)}, launches.value
+
+
+PIC_NOALLOC_MAX_NODES = 134217728
+
+
+def pic_field_energy_noalloc(rho_ptr: int, E_ptr: int, n_nodes: int, cell_volume: float,
+                             out_ptr: int, stream: int) -> None:
+    """(Wx, Wy, Wz, Q) into 4 device doubles at out_ptr; allocates nothing."""
+    check(_call("pic_field_energy_noalloc", C.c_void_p(rho_ptr), C.c_void_p(E_ptr),
+                C.c_int64(n_nodes), C.c_double(cell_volume), C.c_void_p(out_ptr),
+                C.c_void_p(stream)), "pic_field_energy_noalloc")

@@ -55,6 +55,14 @@ struct Layout {
 
 }  // namespace
 
+int pic::record_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
 struct pic_ctx {
     pic_grid_t grid;
     pic_species_t sp;

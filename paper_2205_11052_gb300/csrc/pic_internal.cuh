@@ -78,6 +78,9 @@ struct PushConst {
 constexpr int kDiagFieldBlocks = 512;
 constexpr int kMaxPushBlocks = 152 * 8;
 
+// Set the thread-local message returned by pic_last_error(); returns `code`.
+int record_error(int code, const char *fmt, ...);
+
 // ----------------------------------------------------------------------------
 // kernel launchers (defined in the k_*.cu files); all enqueue on `st`.
 // ----------------------------------------------------------------------------

@@ -1,0 +1,71 @@
+"""GPU test of pic_field_energy_noalloc, the reduction that allocates nothing.
+
+It serves callers that may not allocate device memory while running (a host
+application that owns a fixed memory budget, or a time-critical loop where
+cudaMalloc is forbidden): its scratch lives in a static device array of the
+library.  Here it is called twice in a row through the C ABI on the field of
+a real step, and each result must match the FP64 field energies and charge
+that pic_step's own diagnostics report for the same field.  The larger grid
+goes first so that partials left in the shared scratch by the first call
+would corrupt the second if a call read any slot it did not write.
+"""
+import numpy as np
+import pytest
+
+import pic_inputs as pi
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU-only machines
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2205_11052_gb300 import capi  # noqa: E402
+from paper_2205_11052_gb300.build import build  # noqa: E402
+from paper_2205_11052_gb300.sim import Simulation  # noqa: E402
+
+build()
+
+REL = 1e-12   # both sides are FP64 sums of the same FP32 grid data
+
+
+def _one_call(w):
+    sim = Simulation.from_workload(w, diag_every=1)
+    sim.step(1)
+    rec = sim.diagnostics()[-1]
+    nx, ny, nz = w.n
+    ng = nx * ny * nz
+    rho = torch.empty(ng, dtype=torch.float32, device="cuda")
+    E = torch.empty(4 * ng, dtype=torch.float32, device="cuda")
+    capi.pic_get_field(sim.handle, rho.data_ptr(), E.data_ptr(), True)
+    out = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+    dV = float(np.prod(np.asarray(w.L) / np.asarray(w.n)))
+    capi.pic_field_energy_noalloc(rho.data_ptr(), E.data_ptr(), ng, dV, out.data_ptr(),
+                                  sim.stream.cuda_stream)
+    sim.stream.synchronize()
+    got = out.cpu().numpy()
+    sim.close()
+    return got, np.array([rec["Wx"], rec["Wy"], rec["Wz"], rec["Q"]])
+
+
+def test_noalloc_reduction_matches_step_diagnostics_on_two_calls():
+    big = pi.landau(n=(64, 48, 40), ppc=2, seed=12, alpha=0.3)     # 30 blocks of partials
+    small = pi.landau(n=(16, 16, 16), ppc=8, seed=13, alpha=0.3)   # 1 block
+    for w in (big, small):
+        got, want = _one_call(w)
+        assert np.all(np.isfinite(got))
+        for g, e in zip(got, want):
+            assert g == pytest.approx(e, rel=REL)
+
+
+def test_noalloc_rejects_oversized_and_bad_arguments():
+    capi.load_library()
+    x = torch.zeros(8, dtype=torch.float32, device="cuda")
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(capi.PicError) as e:
+        capi.pic_field_energy_noalloc(x.data_ptr(), x.data_ptr(), capi.PIC_NOALLOC_MAX_NODES + 1,
+                                      1.0, out.data_ptr(), 0)
+    assert e.value.code == capi.PIC_ERR_CAPACITY
+    with pytest.raises(capi.PicError) as e:
+        capi.pic_field_energy_noalloc(x.data_ptr(), x.data_ptr(), 0, 1.0, out.data_ptr(), 0)
+    assert e.value.code == capi.PIC_ERR_ARG
