@@ -31,6 +31,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s (deposit+gather+push) & % HBM roofline; adjoint/forward time"
+
+# launch configuration of the timed step (also used by the full-size parity test)
+LAUNCH = dict(sort_period=4, options=1)
 UNIT = "particle-steps/s"
 L2_BYTES = 129 * 2 ** 20
 
@@ -43,13 +46,16 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--ppc", type=int, default=64)
-    ap.add_argument("--sort-period", type=int, default=4)
+    ap.add_argument("--sort-period", type=int, default=LAUNCH["sort_period"])
+    ap.add_argument("--options", type=int, default=LAUNCH["options"])
     ap.add_argument("--diag-every", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=1 << 21,
                     help="particles in the oracle's bounded sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="landau", choices=["landau", "ensemble"])
+    ap.add_argument("--ens-count", type=int, default=512, help="ensemble instances")
     return ap.parse_args()
 
 
@@ -179,6 +185,91 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- ensemble
+
+def ensemble_members(count, seed=1_000_000):
+    """Landau-damping instances: grids U{16,24,32,48}^3, 8..64 particles per
+    cell, alpha U[0.01, 0.1], independent seeds (seed + i)."""
+    import numpy as np
+
+    import pic_inputs as pi
+
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice([16, 24, 32, 48]))
+        ppc = int(rng.integers(8, 65))
+        alpha = float(rng.uniform(0.01, 0.1))
+        out.append((n, ppc, alpha, seed + i))
+    members = []
+    for n, ppc, alpha, s in out:
+        w = pi.landau(n=n, ppc=ppc, alpha=alpha, seed=s, chunk=1 << 18)
+        members.append(w)
+    return members
+
+
+def run_ensemble(args):
+    """Batched ensemble vs the same instances stepped one launch sequence
+    per instance; both timed on the device over the same steps."""
+    import torch
+
+    from paper_2205_11052_gb300 import capi
+    from paper_2205_11052_gb300.batch import Ensemble
+    from paper_2205_11052_gb300.build import build
+    from paper_2205_11052_gb300.sim import Simulation
+
+    build()
+    t0 = time.perf_counter()
+    ws = ensemble_members(args.ens_count)
+    gen_s = time.perf_counter() - t0
+    N = sum(w.n_particles for w in ws)
+    opts = dict(sort_period=args.sort_period, options=args.options)
+    ens = Ensemble([(w.n, w.L, w.x, w.v, w.Q) for w in ws], dt=0.05, **opts)
+    ens.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0.record(ens.stream)
+    ens.step(args.steps)
+    e1.record(ens.stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_batch = e0.elapsed_time(e1)
+    ens.close()
+    del ens
+    torch.cuda.empty_cache()
+    sims = [Simulation.from_workload(w, **opts) for w in ws]
+    for s in sims:
+        s.step(args.warmup)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for s in sims:
+            s.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_single = e0.elapsed_time(e1)
+    for s in sims:
+        s.close()
+    v_batch = N * args.steps / (ms_batch * 1e-3)
+    v_single = N * args.steps / (ms_single * 1e-3)
+    line = {
+        "metric": "ensemble particle-steps/s (batched launch vs one launch sequence per instance)",
+        "value": v_batch, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_batch / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"ensemble of {len(ws)} Landau instances, grids U{{16,24,32,48}}^3, "
+                               f"8-64 particles/cell, alpha U[0.01,0.1], {N:,} particles",
+                   "generation_s": round(gen_s, 1), **opts},
+        "per_instance_launches": {"value": v_single, "ms_per_step": ms_single / args.steps},
+        "speedup": ms_single / ms_batch,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- native arm
 
 def main():
@@ -188,6 +279,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "ensemble":
+        run_ensemble(args)
         return
 
     import numpy as np
@@ -210,7 +304,8 @@ def main():
     w = pi.landau(n=args.grid, ppc=args.ppc, seed=1001 + rank, n_steps=args.steps)
     N = w.n_particles
     ng = args.grid ** 3
-    sim = Simulation.from_workload(w, sort_period=args.sort_period, diag_every=args.diag_every)
+    sim = Simulation.from_workload(w, sort_period=args.sort_period, options=args.options,
+                                   diag_every=args.diag_every)
     stream = sim.stream
 
     def barrier():
@@ -251,8 +346,10 @@ def main():
 
     # ---- roofline of the dominant kernel (CUDA events inside the timed region)
     peak, peak_kind = load_peaks()
-    algo = {"push": 56.0 * N + 16.0 * ng, "deposit": 16.0 * N + 4.0 * ng}
-    kernel_names = {"push": "k_gather_push", "deposit": "k_deposit_tiles"}
+    # fused gather + push + deposit: particle store read and written once (56 B
+    # per particle), E read once (16 B per node), rho written once (4 B per node)
+    algo = {"push": 56.0 * N + 20.0 * ng, "deposit": 16.0 * N + 4.0 * ng}
+    kernel_names = {"push": "k_push_deposit", "deposit": "k_deposit_tiles"}
     dom = max(algo, key=lambda k: phases[k][0])
     avg_ms = phases[dom][0] / max(1, phases[dom][1])
     achieved = algo[dom] / (avg_ms * 1e-3) / 1e9
@@ -321,6 +418,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": workload_name(args), "n_particles": N,
                        "grid": [args.grid] * 3, "sort_period": args.sort_period,
+                       "deposit": "fixed-point" if args.options & 1 else "fp32",
                        "diag_every": args.diag_every,
                        "l2": f"inputs larger than L2 ({32 * N / 1e9:.2f} GB particle store "
                              f"vs {L2_BYTES / 2**20:.0f} MiB L2), no flush",

@@ -86,8 +86,16 @@ typedef struct {
     int32_t mode[3];       /* Fourier mode tracked by the diagnostics            */
     int32_t mode_comp;     /* component of E for that mode: 0 = x, 1 = y, 2 = z  */
     int32_t block;         /* threads per block of the particle kernels (256)    */
-    int32_t chunk;         /* max particles per deposit work item (default 4096) */
+    int32_t chunk;         /* max particles per deposit work item, 32..4095
+                              (default 4095)                                     */
+    int32_t options;       /* PIC_OPT_* bits (default 0)                         */
 } pic_params_t;
+
+/* options: accumulate the deposit in 2^-20 fixed point (u32 shared-memory
+ * tile, u64 grid) instead of FP32.  Integer sums are order independent, so
+ * the deposit is then deterministic and conserves charge exactly; weights are
+ * rounded to 2^-20 (relative error below 1e-6 of a node's charge). */
+#define PIC_OPT_FIXED_DEPOSIT 1
 
 /* Sizes the caller must provide before any device work. */
 typedef struct {
@@ -239,6 +247,90 @@ int pic_enable_timers(pic_handle_t h, int enable);
  * Any pointer may be NULL. */
 int pic_read_timers(pic_handle_t h, double ms[PIC_PHASE_COUNT],
                     int64_t calls[PIC_PHASE_COUNT], int64_t *kernel_launches);
+
+/* ------------------------------------------------------------ adjoint */
+
+/* Gradient of the final field energy (not in the paper).
+ *
+ * Objective: J = sum_d w_d h^3 sum_g E_d,g^2, the weighted field energy of
+ * the field used by the last of n_steps steps (the W_d of pic_diag_t for that
+ * step), as a function of the synchronised state (x_0, v_0) loaded last.
+ * The gradient is the exact discrete adjoint of the drift-kick-drift step of
+ * pic_step (B_ext must be zero): the gather and the deposit appear as each
+ * other's transposes and the spectral operator as its conjugate symbol.
+ * Memory: the forward pass stores a checkpoint of the particle state every
+ * `checkpoint_every` steps; the reverse sweep recomputes one segment at a
+ * time from its checkpoint, keeping that segment's positions and fields.
+ * Particles are not re-binned during these calls (their order is fixed), so
+ * the deposits of long gradient runs take more global atomics.  With
+ * PIC_OPT_FIXED_DEPOSIT the recomputation reproduces the forward pass bit
+ * for bit.  FP32 particle and grid arithmetic; J and the final reductions in
+ * FP64. */
+
+/* Bytes of the caller-owned device buffer for pic_adjoint_forward/backward. */
+int pic_adjoint_buffer_bytes(pic_handle_t h, int n_steps, int checkpoint_every, size_t *bytes);
+
+/* Run n_steps >= 1 steps from the loaded state without re-binning, storing
+ * checkpoints in `buf` (device, >= pic_adjoint_buffer_bytes), and write J to
+ * host memory (synchronises).  weights: 3 non-negative finite doubles.
+ * Leaves the particles at the state after n_steps - 1 steps.
+ * Errors: PIC_ERR_ARG (B_ext nonzero, bad counts or weights, null buffer),
+ * PIC_ERR_CAPACITY (buffer too small), PIC_ERR_STATE (nothing loaded). */
+int pic_adjoint_forward(pic_handle_t h, int n_steps, int checkpoint_every,
+                        const double weights[3], void *buf, size_t bytes, double *J);
+
+/* Reverse sweep of the last pic_adjoint_forward (which must be the last call
+ * that changed the particles): writes scale * dJ/dx_0 and scale * dJ/dv_0 as
+ * FP64 (n, 3) arrays in load order to host (dst_is_device = 0, synchronises)
+ * or device memory, then restores the initial state x_0, v_0 (as loaded, up
+ * to its FP32 storage) and the step counter. */
+int pic_adjoint_backward(pic_handle_t h, double scale, double *dJdx, double *dJdv,
+                         int dst_is_device);
+
+/* sum_i a_i b_i over n FP64 device values, accumulated in FP64 in a fixed
+ * order (e.g. dJ/dalpha = <dJ/dx_0, dx_0/dalpha>); result to host memory. */
+int pic_dot_f64(pic_handle_t h, const double *a, const double *b, int64_t n, double *out);
+
+/* ------------------------------------------------------------ batched ensembles */
+
+/* Many independent runs of uneven size (not in the paper): every instance is
+ * the scheme above on its own periodic grid with its own particles and total
+ * charge; all share q/m, dt, external fields and the tuning knobs of
+ * pic_params_t.  Each phase of a step (binning, deposit, field solve per
+ * grid size, fused gather + push + deposit, diagnostics) is one launch over
+ * all instances -- a persistent kernel walks the work items of every
+ * instance -- so a whole step of the ensemble can be captured in one CUDA
+ * graph.  Memory follows the single-run rules: one caller-owned arena. */
+typedef struct pic_batch *pic_batch_t;
+
+typedef struct {
+    int32_t n[3];          /* grid nodes per axis (1..1024; n[0] >= 2) */
+    double  L[3];          /* box lengths */
+    int64_t n_particles;   /* particles of this instance */
+    double  total_charge;  /* Q_e of this instance */
+} pic_instance_t;
+
+/* Validate and lay out the ensemble (host-only).  Errors: PIC_ERR_ARG. */
+int pic_batch_create(const pic_instance_t *inst, int n_inst, double q_over_m,
+                     const pic_params_t *params, pic_batch_t *out);
+int pic_batch_buffer_sizes(pic_batch_t b, pic_bufsizes_t *out);
+int pic_batch_bind_workspace(pic_batch_t b, void *dev_arena, size_t bytes, void *stream);
+int pic_batch_set_stream(pic_batch_t b, void *stream);
+void pic_batch_destroy(pic_batch_t b);
+
+/* x, v: FP64 (N_total, 3), the instances' particles concatenated in the order
+ * of the pic_instance_t array; host (synchronises) or device memory. */
+int pic_batch_load_particles(pic_batch_t b, const double *x, const double *v, int src_is_device);
+
+/* n steps of every instance (enqueue only, capturable). */
+int pic_batch_step(pic_batch_t b, int n);
+
+/* Up to max_records diagnostic records per instance, oldest first, written
+ * as out[record * n_inst + instance]; synchronises. */
+int pic_batch_diagnostics(pic_batch_t b, pic_diag_t *out, int max_records, int *n_out);
+
+/* Synchronised (x_n, v_n) of every instance, in the load layout. */
+int pic_batch_get_particles(pic_batch_t b, double *x, double *v, int dst_is_device);
 
 /* ------------------------------------------------------------ no allocation */
 

@@ -48,7 +48,10 @@ class pic_params_t(C.Structure):
                 ("tile", C.c_int32 * 3), ("guard", C.c_int32), ("sort_period", C.c_int32),
                 ("diag_every", C.c_int32), ("diag_capacity", C.c_int32),
                 ("mode", C.c_int32 * 3), ("mode_comp", C.c_int32), ("block", C.c_int32),
-                ("chunk", C.c_int32)]
+                ("chunk", C.c_int32), ("options", C.c_int32)]
+
+
+PIC_OPT_FIXED_DEPOSIT = 1
 
 
 class pic_bufsizes_t(C.Structure):
@@ -64,7 +67,13 @@ class pic_diag_t(C.Structure):
                 ("Px", C.c_double), ("Py", C.c_double), ("Pz", C.c_double), ("K", C.c_double)]
 
 
+class pic_instance_t(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("L", C.c_double * 3), ("n_particles", C.c_int64),
+                ("total_charge", C.c_double)]
+
+
 pic_handle_t = C.c_void_p
+pic_batch_t = C.c_void_p
 
 # name -> (restype, argtypes)
 _SIGNATURES = {
@@ -90,6 +99,23 @@ _SIGNATURES = {
     "pic_device_flags": (C.c_int, [pic_handle_t, C.POINTER(C.c_int32), C.c_int]),
     "pic_field_energy_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
                                            C.c_void_p, C.c_void_p]),
+    "pic_adjoint_buffer_bytes": (C.c_int, [pic_handle_t, C.c_int, C.c_int, C.POINTER(C.c_size_t)]),
+    "pic_adjoint_forward": (C.c_int, [pic_handle_t, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                      C.c_void_p, C.c_size_t, C.POINTER(C.c_double)]),
+    "pic_adjoint_backward": (C.c_int, [pic_handle_t, C.c_double, C.c_void_p, C.c_void_p, C.c_int]),
+    "pic_dot_f64": (C.c_int, [pic_handle_t, C.c_void_p, C.c_void_p, C.c_int64,
+                              C.POINTER(C.c_double)]),
+    "pic_batch_create": (C.c_int, [C.POINTER(pic_instance_t), C.c_int, C.c_double,
+                                   C.POINTER(pic_params_t), C.POINTER(pic_batch_t)]),
+    "pic_batch_buffer_sizes": (C.c_int, [pic_batch_t, C.POINTER(pic_bufsizes_t)]),
+    "pic_batch_bind_workspace": (C.c_int, [pic_batch_t, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "pic_batch_set_stream": (C.c_int, [pic_batch_t, C.c_void_p]),
+    "pic_batch_destroy": (None, [pic_batch_t]),
+    "pic_batch_load_particles": (C.c_int, [pic_batch_t, C.c_void_p, C.c_void_p, C.c_int]),
+    "pic_batch_step": (C.c_int, [pic_batch_t, C.c_int]),
+    "pic_batch_diagnostics": (C.c_int, [pic_batch_t, C.POINTER(pic_diag_t), C.c_int,
+                                        C.POINTER(C.c_int)]),
+    "pic_batch_get_particles": (C.c_int, [pic_batch_t, C.c_void_p, C.c_void_p, C.c_int]),
     "pic_enable_timers": (C.c_int, [pic_handle_t, C.c_int]),
     "pic_read_timers": (C.c_int, [pic_handle_t, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64)]),
@@ -261,3 +287,81 @@ def pic_field_energy_noalloc(rho_ptr: int, E_ptr: int, n_nodes: int, cell_volume
     check(_call("pic_field_energy_noalloc", C.c_void_p(rho_ptr), C.c_void_p(E_ptr),
                 C.c_int64(n_nodes), C.c_double(cell_volume), C.c_void_p(out_ptr),
                 C.c_void_p(stream)), "pic_field_energy_noalloc")
+
+
+def pic_adjoint_buffer_bytes(h, n_steps: int, checkpoint_every: int) -> int:
+    out = C.c_size_t()
+    check(_call("pic_adjoint_buffer_bytes", h, C.c_int(n_steps), C.c_int(checkpoint_every),
+                C.byref(out)), "pic_adjoint_buffer_bytes")
+    return out.value
+
+
+def pic_adjoint_forward(h, n_steps: int, checkpoint_every: int, weights, buf_ptr: int,
+                        nbytes: int) -> float:
+    w = (C.c_double * 3)(*[float(a) for a in weights])
+    J = C.c_double()
+    check(_call("pic_adjoint_forward", h, C.c_int(n_steps), C.c_int(checkpoint_every), w,
+                C.c_void_p(buf_ptr), C.c_size_t(nbytes), C.byref(J)), "pic_adjoint_forward")
+    return J.value
+
+
+def pic_adjoint_backward(h, scale: float, gx_ptr: int, gv_ptr: int, dst_is_device: bool) -> None:
+    check(_call("pic_adjoint_backward", h, C.c_double(scale), C.c_void_p(gx_ptr),
+                C.c_void_p(gv_ptr), C.c_int(1 if dst_is_device else 0)), "pic_adjoint_backward")
+
+
+def pic_dot_f64(h, a_ptr: int, b_ptr: int, n: int) -> float:
+    out = C.c_double()
+    check(_call("pic_dot_f64", h, C.c_void_p(a_ptr), C.c_void_p(b_ptr), C.c_int64(n),
+                C.byref(out)), "pic_dot_f64")
+    return out.value
+
+
+def pic_batch_create(instances, q_over_m: float, params: pic_params_t):
+    arr = (pic_instance_t * len(instances))(*instances)
+    b = pic_batch_t()
+    check(_call("pic_batch_create", arr, C.c_int(len(instances)), C.c_double(q_over_m),
+                C.byref(params), C.byref(b)), "pic_batch_create")
+    return b
+
+
+def pic_batch_buffer_sizes(b) -> pic_bufsizes_t:
+    out = pic_bufsizes_t()
+    check(_call("pic_batch_buffer_sizes", b, C.byref(out)), "pic_batch_buffer_sizes")
+    return out
+
+
+def pic_batch_bind_workspace(b, dev_ptr: int, nbytes: int, stream: int) -> None:
+    check(_call("pic_batch_bind_workspace", b, C.c_void_p(dev_ptr), C.c_size_t(nbytes),
+                C.c_void_p(stream)), "pic_batch_bind_workspace")
+
+
+def pic_batch_set_stream(b, stream: int) -> None:
+    check(_call("pic_batch_set_stream", b, C.c_void_p(stream)), "pic_batch_set_stream")
+
+
+def pic_batch_destroy(b) -> None:
+    _call("pic_batch_destroy", b)
+
+
+def pic_batch_load_particles(b, x_ptr: int, v_ptr: int, src_is_device: bool) -> None:
+    check(_call("pic_batch_load_particles", b, C.c_void_p(x_ptr), C.c_void_p(v_ptr),
+                C.c_int(1 if src_is_device else 0)), "pic_batch_load_particles")
+
+
+def pic_batch_step(b, n: int) -> None:
+    check(_call("pic_batch_step", b, C.c_int(n)), "pic_batch_step")
+
+
+def pic_batch_diagnostics(b, max_records: int, n_inst: int):
+    buf = (pic_diag_t * max(1, max_records * n_inst))()
+    n = C.c_int()
+    code = _call("pic_batch_diagnostics", b, buf, C.c_int(max_records), C.byref(n))
+    recs = [[buf[r * n_inst + i] for i in range(n_inst)] for r in range(n.value)]
+    check(code, "pic_batch_diagnostics")
+    return recs
+
+
+def pic_batch_get_particles(b, x_ptr: int, v_ptr: int, dst_is_device: bool) -> None:
+    check(_call("pic_batch_get_particles", b, C.c_void_p(x_ptr), C.c_void_p(v_ptr),
+                C.c_int(1 if dst_is_device else 0)), "pic_batch_get_particles")

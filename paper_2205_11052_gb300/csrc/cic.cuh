@@ -1,0 +1,175 @@
+// Device helpers of the cloud-in-cell shape on the cell-centred grid
+// (Section 3.2 of arXiv 2205.11052), shared by the deposit, the fused
+// push + deposit and the adjoint kernels.
+//
+// A particle with stencil base (i, j, k) and offsets (fx, fy, fz) in [0, 1)
+// has weight w_a(fx) w_b(fy) w_c(fz) on node (i + a, j + b, k + c), a, b, c in
+// {0, 1}, with w_0(f) = 1 - f and w_1(f) = f; corners are numbered
+// a | b << 1 | c << 2.
+#pragma once
+
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace cic {
+
+constexpr float kFixScale = 1048576.0f;   // 2^20: fixed-point unit of a weight
+constexpr uint32_t kFixOne = 1u << 20;
+
+__device__ __forceinline__ bool decode_cell(int32_t c, const Geom &g, int &i, int &j, int &k) {
+    i = cell_i(c);
+    j = cell_j(c);
+    k = cell_k(c);
+    if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) {   // never produced by the kernels
+        i = j = k = 0;
+        return false;
+    }
+    return true;
+}
+
+// place axis index a (0 <= a < n) relative to tile origin o with guard G:
+// the slot in [0, T + 2G), or -1 if farther than G cells from the tile
+__device__ __forceinline__ int tile_slot(int a, int o, int n, int T, int G) {
+    int d = a - o;
+    if (d < 0) d += n;
+    if (d >= T + G) {
+        d -= n;
+        if (d < -G) return -1;
+    }
+    return d + G;
+}
+
+__device__ __forceinline__ void weights(float fx, float fy, float fz, float w[8]) {
+    const float x0 = 1.0f - fx, y0 = 1.0f - fy, z0 = 1.0f - fz;
+    const float a = y0 * z0, b = fy * z0, c = y0 * fz, d = fy * fz;
+    w[0] = x0 * a; w[1] = fx * a;
+    w[2] = x0 * b; w[3] = fx * b;
+    w[4] = x0 * c; w[5] = fx * c;
+    w[6] = x0 * d; w[7] = fx * d;
+}
+
+// fixed-point weights: all eight rounded to multiples of 2^-20, then the
+// heaviest corner (weight >= 1/8, picked by which half of the cell each
+// offset lies in) absorbs the rounding remainder, so the corners sum to
+// exactly 2^20 and none is negative
+__device__ __forceinline__ void fixed_weights(const float w[8], float fx, float fy, float fz,
+                                              uint32_t q[8]) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        q[c] = __float2uint_rn(w[c] * kFixScale);
+        s += q[c];
+    }
+    const int big = (fx >= 0.5f ? 1 : 0) | (fy >= 0.5f ? 2 : 0) | (fz >= 0.5f ? 4 : 0);
+    const uint32_t adj = kFixOne - s;   // a few units either way (mod 2^32)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) q[c] += (c == big) ? adj : 0u;
+}
+
+// the eight stencil node indices (periodic)
+__device__ __forceinline__ void nodes(const Geom &g, int i, int j, int k, int64_t nd[8]) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int i1 = (i + 1 == nx) ? 0 : i + 1;
+    const int j1 = (j + 1 == ny) ? 0 : j + 1;
+    const int k1 = (k + 1 == nz) ? 0 : k + 1;
+    const int64_t nxy = (int64_t)nx * ny;
+    const int64_t r00 = (int64_t)j * nx + k * nxy, r10 = (int64_t)j1 * nx + k * nxy;
+    const int64_t r01 = (int64_t)j * nx + k1 * nxy, r11 = (int64_t)j1 * nx + k1 * nxy;
+    nd[0] = r00 + i; nd[1] = r00 + i1; nd[2] = r10 + i; nd[3] = r10 + i1;
+    nd[4] = r01 + i; nd[5] = r01 + i1; nd[6] = r11 + i; nd[7] = r11 + i1;
+}
+
+// add one particle's weights straight to the grid (global atomics)
+template <bool FIXED>
+__device__ __forceinline__ void deposit_global(float *rho, unsigned long long *rho64, const Geom &g,
+                                               int i, int j, int k, const float w[8], float fx,
+                                               float fy, float fz, float qscale) {
+    int64_t nd[8];
+    nodes(g, i, j, k, nd);
+    if (FIXED) {
+        uint32_t q[8];
+        fixed_weights(w, fx, fy, fz, q);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) atomicAdd(rho64 + nd[c], (unsigned long long)q[c]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) atomicAdd(rho + nd[c], w[c] * qscale);
+    }
+}
+
+// Shared-memory tile of one work item: (T + 1 + 2G)^3 slots around tile
+// origin o; add one particle (or send it to the grid if it left the guard).
+struct Tile {
+    int ox, oy, oz, S0, S01, S;
+};
+
+__host__ __device__ __forceinline__ Tile tile_of(const Geom &g, int tile) {
+    Tile t;
+    const int tx = tile % g.ntile[0];
+    const int ty = (tile / g.ntile[0]) % g.ntile[1];
+    const int tz = tile / (g.ntile[0] * g.ntile[1]);
+    t.ox = tx * g.tile[0];
+    t.oy = ty * g.tile[1];
+    t.oz = tz * g.tile[2];
+    const int G = g.guard;
+    t.S0 = g.tile[0] + 2 * G + 1;
+    t.S01 = t.S0 * (g.tile[1] + 2 * G + 1);
+    t.S = t.S01 * (g.tile[2] + 2 * G + 1);
+    return t;
+}
+
+// returns true if the particle went to the shared tile, false if to the grid
+template <bool FIXED>
+__device__ __forceinline__ bool tile_add(uint32_t *acc, const Tile &t, const Geom &g, int i, int j,
+                                         int k, float fx, float fy, float fz, float *rho,
+                                         unsigned long long *rho64, float qscale) {
+    float w[8];
+    weights(fx, fy, fz, w);
+    const int G = g.guard;
+    const int si = tile_slot(i, t.ox, g.n[0], g.tile[0], G);
+    const int sj = tile_slot(j, t.oy, g.n[1], g.tile[1], G);
+    const int sk = tile_slot(k, t.oz, g.n[2], g.tile[2], G);
+    if (si >= 0 && sj >= 0 && sk >= 0) {
+        const int s = si + t.S0 * sj + t.S01 * sk;
+        const int off[8] = {0, 1, t.S0, t.S0 + 1, t.S01, t.S01 + 1, t.S01 + t.S0,
+                            t.S01 + t.S0 + 1};
+        if (FIXED) {
+            uint32_t q[8];
+            fixed_weights(w, fx, fy, fz, q);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) atomicAdd(acc + s + off[c], q[c]);
+        } else {
+            float *accf = reinterpret_cast<float *>(acc);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) atomicAdd(accf + s + off[c], w[c]);
+        }
+        return true;
+    }
+    deposit_global<FIXED>(rho, rho64, g, i, j, k, w, fx, fy, fz, qscale);
+    return false;
+}
+
+// add the shared tile to the grid: one global atomic per touched slot
+template <bool FIXED>
+__device__ __forceinline__ void tile_flush(const uint32_t *acc, const Tile &t, const Geom &g,
+                                           float *rho, unsigned long long *rho64, float qscale) {
+    const int G = g.guard;
+    for (int s = threadIdx.x; s < t.S; s += blockDim.x) {
+        const uint32_t raw = acc[s];
+        if (raw != 0u) {
+            const int a = s % t.S0, b = (s / t.S0) % (t.S01 / t.S0), cz = s / t.S01;
+            int gi = (t.ox - G + a) % g.n[0];
+            int gj = (t.oy - G + b) % g.n[1];
+            int gk = (t.oz - G + cz) % g.n[2];
+            if (gi < 0) gi += g.n[0];
+            if (gj < 0) gj += g.n[1];
+            if (gk < 0) gk += g.n[2];
+            const int64_t node = gi + (int64_t)g.n[0] * (gj + (int64_t)g.n[1] * gk);
+            if (FIXED) atomicAdd(rho64 + node, (unsigned long long)raw);
+            else atomicAdd(rho + node, __uint_as_float(raw) * qscale);
+        }
+    }
+}
+
+}  // namespace cic
+}  // namespace pic

@@ -9,7 +9,10 @@
 // x_{n+3/2} = x_{n+1/2} + dt v_{n+1}.
 #include <math.h>
 
-#include "pic_internal.cuh"
+#include <algorithm>
+
+#include "cic.cuh"
+#include "push.cuh"
 
 namespace pic {
 
@@ -92,97 +95,57 @@ __global__ void k_unload(int64_t o0, int64_t m, const int32_t *__restrict__ inv,
 }
 
 // ---------------------------------------------------------------------------
-// fused gather + Boris push + drift + periodic wrap
+// gather + Boris push + drift + periodic wrap (push_one in push.cuh)
+//
+// Each thread owns groups of 4 consecutive particles: the seven SoA streams
+// are read and written as 16-byte vectors with evict-first hints (they are
+// touched once per step), while the float4 field is read through the
+// read-only path so it stays cached (the whole 128^3 field is 32 MiB).
 // ---------------------------------------------------------------------------
 template <bool DIAG, bool EXT, bool MAG>
-__global__ void __launch_bounds__(256) k_gather_push(int64_t n, Geom g, PushConst pc, Ctrl *ctrl,
+__global__ void __launch_bounds__(256, 3) k_gather_push(int64_t n, Geom g, PushConst pc, Ctrl *ctrl,
                                                       const float4 *__restrict__ E4,
                                                       double *__restrict__ part) {
     const ParticleSet ps = ctrl->sets[ctrl->cur];
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const int nxy = nx * ny;
     float a_vx = 0.f, a_vy = 0.f, a_vz = 0.f, a_v2 = 0.f;
     int bad = 0;
+    const int64_t ngroups = n >> 2;                      // full groups of 4
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-        const int32_t c = ps.cell[p];
-        int i = cell_i(c), j = cell_j(c), k = cell_k(c);
-        if (i >= nx || j >= ny || k >= nz) {   // never produced by the kernels
-            bad |= PIC_FLAG_BAD_CELL;
-            i = j = k = 0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ngroups; q += stride) {
+        int4 c = __ldcs(reinterpret_cast<const int4 *>(ps.cell) + q);
+        float4 ox = __ldcs(reinterpret_cast<const float4 *>(ps.o[0]) + q);
+        float4 oy = __ldcs(reinterpret_cast<const float4 *>(ps.o[1]) + q);
+        float4 oz = __ldcs(reinterpret_cast<const float4 *>(ps.o[2]) + q);
+        float4 ux = __ldcs(reinterpret_cast<const float4 *>(ps.v[0]) + q);
+        float4 uy = __ldcs(reinterpret_cast<const float4 *>(ps.v[1]) + q);
+        float4 uz = __ldcs(reinterpret_cast<const float4 *>(ps.v[2]) + q);
+        push_one<EXT, MAG>(g, pc, E4, c.x, ox.x, oy.x, oz.x, ux.x, uy.x, uz.x, bad);
+        push_one<EXT, MAG>(g, pc, E4, c.y, ox.y, oy.y, oz.y, ux.y, uy.y, uz.y, bad);
+        push_one<EXT, MAG>(g, pc, E4, c.z, ox.z, oy.z, oz.z, ux.z, uy.z, uz.z, bad);
+        push_one<EXT, MAG>(g, pc, E4, c.w, ox.w, oy.w, oz.w, ux.w, uy.w, uz.w, bad);
+        __stcs(reinterpret_cast<int4 *>(ps.cell) + q, c);
+        __stcs(reinterpret_cast<float4 *>(ps.o[0]) + q, ox);
+        __stcs(reinterpret_cast<float4 *>(ps.o[1]) + q, oy);
+        __stcs(reinterpret_cast<float4 *>(ps.o[2]) + q, oz);
+        __stcs(reinterpret_cast<float4 *>(ps.v[0]) + q, ux);
+        __stcs(reinterpret_cast<float4 *>(ps.v[1]) + q, uy);
+        __stcs(reinterpret_cast<float4 *>(ps.v[2]) + q, uz);
+        if (DIAG) {
+            a_vx += (ux.x + ux.y) + (ux.z + ux.w);
+            a_vy += (uy.x + uy.y) + (uy.z + uy.w);
+            a_vz += (uz.x + uz.y) + (uz.z + uz.w);
+            a_v2 += (ux.x * ux.x + uy.x * uy.x + uz.x * uz.x) + (ux.y * ux.y + uy.y * uy.y + uz.y * uz.y) +
+                    (ux.z * ux.z + uy.z * uy.z + uz.z * uz.z) + (ux.w * ux.w + uy.w * uy.w + uz.w * uz.w);
         }
+    }
+    // the n mod 4 particles after the last full group: first threads of block 0
+    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+        const int64_t p = (ngroups << 2) + threadIdx.x;
+        int32_t c = ps.cell[p];
         float fx = ps.o[0][p], fy = ps.o[1][p], fz = ps.o[2][p];
         float vx = ps.v[0][p], vy = ps.v[1][p], vz = ps.v[2][p];
-
-        // CIC stencil nodes (periodic)
-        const int i1 = (i + 1 == nx) ? 0 : i + 1;
-        const int j1 = (j + 1 == ny) ? 0 : j + 1;
-        const int k1 = (k + 1 == nz) ? 0 : k + 1;
-        const int r00 = j * nx + k * nxy, r10 = j1 * nx + k * nxy;
-        const int r01 = j * nx + k1 * nxy, r11 = j1 * nx + k1 * nxy;
-        const float4 e000 = __ldg(E4 + r00 + i), e100 = __ldg(E4 + r00 + i1);
-        const float4 e010 = __ldg(E4 + r10 + i), e110 = __ldg(E4 + r10 + i1);
-        const float4 e001 = __ldg(E4 + r01 + i), e101 = __ldg(E4 + r01 + i1);
-        const float4 e011 = __ldg(E4 + r11 + i), e111 = __ldg(E4 + r11 + i1);
-        const float wx1 = fx, wx0 = 1.0f - fx;
-        const float wy1 = fy, wy0 = 1.0f - fy;
-        const float wz1 = fz, wz0 = 1.0f - fz;
-        const float w00 = wy0 * wz0, w10 = wy1 * wz0, w01 = wy0 * wz1, w11 = wy1 * wz1;
-        float ex = w00 * (wx0 * e000.x + wx1 * e100.x) + w10 * (wx0 * e010.x + wx1 * e110.x) +
-                   w01 * (wx0 * e001.x + wx1 * e101.x) + w11 * (wx0 * e011.x + wx1 * e111.x);
-        float ey = w00 * (wx0 * e000.y + wx1 * e100.y) + w10 * (wx0 * e010.y + wx1 * e110.y) +
-                   w01 * (wx0 * e001.y + wx1 * e101.y) + w11 * (wx0 * e011.y + wx1 * e111.y);
-        float ez = w00 * (wx0 * e000.z + wx1 * e100.z) + w10 * (wx0 * e010.z + wx1 * e110.z) +
-                   w01 * (wx0 * e001.z + wx1 * e101.z) + w11 * (wx0 * e011.z + wx1 * e111.z);
-        if (EXT) {
-            // quadrupole about the box centre: (x - c)/h = i - N/2 + 1/2 + f
-            const float dx = ((float)i - pc.half_n[0] + 0.5f + fx) * g.h[0];
-            const float dy = ((float)j - pc.half_n[1] + 0.5f + fy) * g.h[1];
-            const float dz = ((float)k - pc.half_n[2] + 0.5f + fz) * g.h[2];
-            ex += -0.5f * pc.wz2 * dx;
-            ey += -0.5f * pc.wz2 * dy;
-            ez += pc.wz2 * dz;
-        }
-        // Boris: half kick, rotation, half kick
-        float mx = vx + pc.qm_half_dt * ex;
-        float my = vy + pc.qm_half_dt * ey;
-        float mz = vz + pc.qm_half_dt * ez;
-        if (MAG) {
-            const float px = mx + (my * pc.t[2] - mz * pc.t[1]);
-            const float py = my + (mz * pc.t[0] - mx * pc.t[2]);
-            const float pz = mz + (mx * pc.t[1] - my * pc.t[0]);
-            mx += py * pc.s[2] - pz * pc.s[1];
-            my += pz * pc.s[0] - px * pc.s[2];
-            mz += px * pc.s[1] - py * pc.s[0];
-        }
-        vx = mx + pc.qm_half_dt * ex;
-        vy = my + pc.qm_half_dt * ey;
-        vz = mz + pc.qm_half_dt * ez;
-
-        // drift a full step in cell units, carry into the cell index, wrap
-        float sx = fx + pc.dt_over_h[0] * vx;
-        float sy = fy + pc.dt_over_h[1] * vy;
-        float sz = fz + pc.dt_over_h[2] * vz;
-        float flx = floorf(sx), fly = floorf(sy), flz = floorf(sz);
-        fx = sx - flx;
-        fy = sy - fly;
-        fz = sz - flz;
-        if (fx >= 1.0f) { fx = 0.0f; flx += 1.0f; }
-        if (fy >= 1.0f) { fy = 0.0f; fly += 1.0f; }
-        if (fz >= 1.0f) { fz = 0.0f; flz += 1.0f; }
-        if (!(fabsf(flx) < 1.0e6f && fabsf(fly) < 1.0e6f && fabsf(flz) < 1.0e6f)) {
-            bad |= PIC_FLAG_NONFINITE;
-            flx = fly = flz = 0.0f;
-            fx = fy = fz = 0.0f;
-        }
-        i += (int)flx;
-        j += (int)fly;
-        k += (int)flz;
-        if ((unsigned)i >= (unsigned)nx) { i %= nx; if (i < 0) i += nx; }
-        if ((unsigned)j >= (unsigned)ny) { j %= ny; if (j < 0) j += ny; }
-        if ((unsigned)k >= (unsigned)nz) { k %= nz; if (k < 0) k += nz; }
-
-        ps.cell[p] = pack_cell(i, j, k);
+        push_one<EXT, MAG>(g, pc, E4, c, fx, fy, fz, vx, vy, vz, bad);
+        ps.cell[p] = c;
         ps.o[0][p] = fx;
         ps.o[1][p] = fy;
         ps.o[2][p] = fz;
@@ -214,6 +177,136 @@ __global__ void __launch_bounds__(256) k_gather_push(int64_t n, Geom g, PushCons
             const int nw = blockDim.x >> 5;
             for (int w = 0; w < nw; ++w) t += red[threadIdx.x][w];
             part[4 * blockIdx.x + threadIdx.x] = t;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->step += 1;
+}
+
+
+// ---------------------------------------------------------------------------
+// fused gather + push + deposit of the new positions (one pass per step)
+//
+// Scatter of step n+1 needs exactly the positions this push writes, so the
+// CTA that pushes a work item's particles also deposits them into the
+// item's shared-memory tile (the sort's tile plus guard cells) and flushes
+// it at the end: per step the particle store is read and written once (56
+// bytes per particle) instead of being read again by a separate deposit.
+// ---------------------------------------------------------------------------
+template <bool DIAG, bool EXT, bool MAG, bool FIXED>
+__device__ __forceinline__ void pd_one(const Geom &g, const PushConst &pc, const float4 *E4,
+                                       bool sparse, uint32_t *acc, const cic::Tile &t, float *rho,
+                                       unsigned long long *rho64, float qscale, int32_t &c,
+                                       float &fx, float &fy, float &fz, float &vx, float &vy,
+                                       float &vz, int &bad, unsigned long long &strays,
+                                       float (&a)[4]) {
+    push_one<EXT, MAG>(g, pc, E4, c, fx, fy, fz, vx, vy, vz, bad);
+    const int i = cell_i(c), j = cell_j(c), k = cell_k(c);
+    if (sparse) {
+        float w[8];
+        cic::weights(fx, fy, fz, w);
+        cic::deposit_global<FIXED>(rho, rho64, g, i, j, k, w, fx, fy, fz, qscale);
+    } else if (!cic::tile_add<FIXED>(acc, t, g, i, j, k, fx, fy, fz, rho, rho64, qscale)) {
+        ++strays;
+    }
+    if (DIAG) {
+        a[0] += vx;
+        a[1] += vy;
+        a[2] += vz;
+        a[3] += vx * vx + vy * vy + vz * vz;
+    }
+}
+
+template <bool DIAG, bool EXT, bool MAG, bool FIXED>
+__global__ void __launch_bounds__(256, 3) k_push_deposit(Geom g, PushConst pc, Ctrl *ctrl,
+                                                          const int4 *__restrict__ items,
+                                                          const float4 *__restrict__ E4,
+                                                          float *rho, unsigned long long *rho64,
+                                                          float qscale, int sparse_below,
+                                                          double *__restrict__ part) {
+    extern __shared__ uint32_t acc[];
+    const ParticleSet ps = ctrl->sets[ctrl->cur];
+    const int n_items = ctrl->n_items;
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    int bad = 0;
+    unsigned long long strays = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int4 item = items[it];
+        const bool sparse = item.z - item.y < sparse_below;
+        const cic::Tile t = cic::tile_of(g, item.x);
+        if (!sparse) {
+            for (int s = threadIdx.x; s < t.S; s += blockDim.x) acc[s] = 0u;
+            __syncthreads();
+        }
+        // 16-byte groups of 4 over the aligned interior [q0*4, q1*4) of the
+        // item, single particles for its unaligned head and tail
+        const int q0 = (item.y + 3) >> 2, q1 = item.z >> 2;
+        for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+            int4 c = __ldcs(reinterpret_cast<const int4 *>(ps.cell) + q);
+            float4 ox = __ldcs(reinterpret_cast<const float4 *>(ps.o[0]) + q);
+            float4 oy = __ldcs(reinterpret_cast<const float4 *>(ps.o[1]) + q);
+            float4 oz = __ldcs(reinterpret_cast<const float4 *>(ps.o[2]) + q);
+            float4 ux = __ldcs(reinterpret_cast<const float4 *>(ps.v[0]) + q);
+            float4 uy = __ldcs(reinterpret_cast<const float4 *>(ps.v[1]) + q);
+            float4 uz = __ldcs(reinterpret_cast<const float4 *>(ps.v[2]) + q);
+            pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E4, sparse, acc, t, rho, rho64, qscale, c.x, ox.x,
+                                          oy.x, oz.x, ux.x, uy.x, uz.x, bad, strays, a);
+            pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E4, sparse, acc, t, rho, rho64, qscale, c.y, ox.y,
+                                          oy.y, oz.y, ux.y, uy.y, uz.y, bad, strays, a);
+            pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E4, sparse, acc, t, rho, rho64, qscale, c.z, ox.z,
+                                          oy.z, oz.z, ux.z, uy.z, uz.z, bad, strays, a);
+            pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E4, sparse, acc, t, rho, rho64, qscale, c.w, ox.w,
+                                          oy.w, oz.w, ux.w, uy.w, uz.w, bad, strays, a);
+            __stcs(reinterpret_cast<int4 *>(ps.cell) + q, c);
+            __stcs(reinterpret_cast<float4 *>(ps.o[0]) + q, ox);
+            __stcs(reinterpret_cast<float4 *>(ps.o[1]) + q, oy);
+            __stcs(reinterpret_cast<float4 *>(ps.o[2]) + q, oz);
+            __stcs(reinterpret_cast<float4 *>(ps.v[0]) + q, ux);
+            __stcs(reinterpret_cast<float4 *>(ps.v[1]) + q, uy);
+            __stcs(reinterpret_cast<float4 *>(ps.v[2]) + q, uz);
+        }
+        // head [item.y, 4 q0) and tail [4 q1, item.z); when the item lies
+        // inside one group (q0 > q1) the head covers all of it
+        const int head_end = min(4 * q0, item.z);
+        const int tail_beg = max(4 * q1, head_end);
+        const int nh = head_end - item.y, nt = item.z - tail_beg;
+        if ((int)threadIdx.x < nh + nt) {
+            const int p = (int)threadIdx.x < nh ? item.y + (int)threadIdx.x
+                                                : tail_beg + ((int)threadIdx.x - nh);
+            int32_t c = ps.cell[p];
+            float fx = ps.o[0][p], fy = ps.o[1][p], fz = ps.o[2][p];
+            float vx = ps.v[0][p], vy = ps.v[1][p], vz = ps.v[2][p];
+            pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E4, sparse, acc, t, rho, rho64, qscale, c, fx, fy,
+                                          fz, vx, vy, vz, bad, strays, a);
+            ps.cell[p] = c;
+            ps.o[0][p] = fx;
+            ps.o[1][p] = fy;
+            ps.o[2][p] = fz;
+            ps.v[0][p] = vx;
+            ps.v[1][p] = vy;
+            ps.v[2][p] = vz;
+        }
+        if (!sparse) {
+            __syncthreads();
+            cic::tile_flush<FIXED>(acc, t, g, rho, rho64, qscale);
+            __syncthreads();
+        }
+    }
+    if (bad) raise_flag(ctrl, bad);
+    if (strays) atomicAdd(&ctrl->stray, strays);
+    if (DIAG) {
+        double d[4] = {(double)a[0], (double)a[1], (double)a[2], (double)a[3]};
+        __shared__ double red[4][8];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (int q = 0; q < 4; ++q) {
+            double tt = d[q];
+            for (int o = 16; o > 0; o >>= 1) tt += __shfl_down_sync(0xffffffffu, tt, o);
+            if (lane == 0) red[q][wid] = tt;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            double tt = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tt += red[threadIdx.x][w];
+            part[4 * blockIdx.x + threadIdx.x] = tt;
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->step += 1;
@@ -263,6 +356,45 @@ cudaError_t launch_gather_push(int64_t n, const Geom &g, const PushConst &pc, bo
     }
 #undef PIC_GP
     return cudaGetLastError();
+}
+
+}  // namespace pic
+
+namespace pic {
+
+cudaError_t launch_push_deposit(const Geom &g, const PushConst &pc, bool diag, bool fixed,
+                                Ctrl *ctrl, const int4 *items, int max_items, const float4 *E4,
+                                float *rho, unsigned long long *rho64, double qscale,
+                                int sparse_below, double *part, int blocks, cudaStream_t st) {
+    const bool ext = pc.wz2 != 0.0f;
+    const bool mag = pc.t[0] != 0.0f || pc.t[1] != 0.0f || pc.t[2] != 0.0f;
+    const cic::Tile t0 = cic::tile_of(g, 0);
+    const size_t smem = sizeof(uint32_t) * (size_t)t0.S;
+    const int nb = std::max(1, std::min(blocks, max_items));
+    const float qs = (float)qscale;
+    cudaError_t e = cudaSuccess;
+#define PIC_PD(D, X, M, F)                                                                      \
+    do {                                                                                        \
+        auto kern = k_push_deposit<D, X, M, F>;                                                 \
+        if (smem > 48 * 1024 &&                                                                 \
+            (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                      (int)smem)) != cudaSuccess)                               \
+            return e;                                                                           \
+        kern<<<nb, 256, smem, st>>>(g, pc, ctrl, items, E4, rho, rho64, qs, sparse_below, part); \
+    } while (0)
+#define PIC_PD_F(D, X, M) \
+    do { if (fixed) PIC_PD(D, X, M, true); else PIC_PD(D, X, M, false); } while (0)
+    if (diag) {
+        if (ext) { if (mag) PIC_PD_F(true, true, true); else PIC_PD_F(true, true, false); }
+        else     { if (mag) PIC_PD_F(true, false, true); else PIC_PD_F(true, false, false); }
+    } else {
+        if (ext) { if (mag) PIC_PD_F(false, true, true); else PIC_PD_F(false, true, false); }
+        else     { if (mag) PIC_PD_F(false, false, true); else PIC_PD_F(false, false, false); }
+    }
+#undef PIC_PD_F
+#undef PIC_PD
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return fixed ? launch_rho_finish(g, rho64, rho, qscale, st) : cudaSuccess;
 }
 
 }  // namespace pic

@@ -1,17 +1,21 @@
-// Periodic binning: counting sort of the particle store by tile-major cell
-// index, followed by the deposit work list (tile, particle range) build.
+// Periodic binning: counting sort of the particle store by deposit tile,
+// followed by the deposit work list (tile, particle range) build.
 //
 // The paper has no sort (its nearest step is the particle-to-rank search of
-// Section 5.2.1); binning keeps particles grouped by deposit tile and ordered
-// by cell within a tile, so the deposit can accumulate each tile in shared
-// memory and aggregate equal cells within a warp.
+// Section 5.2.1); binning keeps particles grouped by deposit tile so the
+// deposit can accumulate each tile in shared memory.
 //
 // Key of a particle with stencil base (i, j, k), tile T = (Tx, Ty, Tz):
-//   tile id = ti + ntx (tj + nty tk),   (ti, tj, tk) = (i/Tx, j/Ty, k/Tz)
-//   key     = tile id * Tx Ty Tz + li + Tx (lj + Ty lk),  (li, ...) = (i mod Tx, ...)
+//   key = ti + ntx (tj + nty tk),   (ti, tj, tk) = (i/Tx, j/Ty, k/Tz).
+// Between sorts particles drift by a fraction of a cell per step, so a warp
+// of consecutive particles mostly shares one tile: its lanes claim one
+// contiguous destination range with a single atomic and the scatter writes
+// stay coalesced.  (Cell-level keys would send the 32 lanes of a warp to ~32
+// different cells after any drift, i.e. 4-byte scattered stores.)
 // Passes: histogram (warp-aggregated atomics) -> exclusive scan (in place) ->
 // scatter (the scanned offsets serve as cursors; afterwards bins[key] holds
 // the end of bin key) -> per-tile ranges -> scan of items per tile -> items.
+// Order within a tile is the claim order (not deterministic).
 #include <algorithm>
 
 #include "pic_internal.cuh"
@@ -31,65 +35,183 @@ __device__ __forceinline__ int tile_key(int32_t c, const Geom &g, int &bad) {
         i = j = k = 0;
     }
     const int ti = i / g.tile[0], tj = j / g.tile[1], tk = k / g.tile[2];
-    const int li = i - ti * g.tile[0], lj = j - tj * g.tile[1], lk = k - tk * g.tile[2];
-    const int tid = ti + g.ntile[0] * (tj + g.ntile[1] * tk);
-    return tid * g.tvol + li + g.tile[0] * (lj + g.tile[1] * lk);
+    return ti + g.ntile[0] * (tj + g.ntile[1] * tk);
 }
 
-// atomicAdd(&base[key], 1) for every active lane, aggregated over lanes that
-// share a key; returns each lane's old value plus its rank among those lanes.
-__device__ __forceinline__ int warp_agg_increment(int32_t *base, int key, unsigned active) {
-    const int lane = threadIdx.x & 31;
-    const unsigned peers = __match_any_sync(active, key);
-    const int leader = __ffs(peers) - 1;
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    int old = 0;
-    if (lane == leader) old = atomicAdd(base + key, __popc(peers));
-    old = __shfl_sync(peers, old, leader);
-    return old + rank;
-}
+// Block-staged scatter.  A block takes kStage consecutive particles into
+// shared memory, finds the slice's distinct destination tiles with a small
+// shared hash table (a slice comes from one or two tiles plus strays into
+// their neighbours, i.e. a few dozen keys), claims one global range per tile
+// with one atomic, and writes every tile's particles contiguously.  A slice
+// with more distinct tiles than the table holds (the first binning of
+// particles in arbitrary order) falls back to per-warp claims.
+constexpr int kStage = 2048;
+constexpr int kHash = 256;
 
-__global__ void k_histogram(int64_t n, Geom g, Ctrl *ctrl, int32_t *bins) {
-    const ParticleSet ps = ctrl->sets[ctrl->cur];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+__global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl *ctrl,
+                                                         int32_t *bins) {
+    extern __shared__ uint32_t smem[];
+    int32_t *sc = reinterpret_cast<int32_t *>(smem);          // kStage cells
+    float *so = reinterpret_cast<float *>(sc + kStage);        // 3 x kStage offsets
+    float *sv = so + 3 * kStage;                               // 3 x kStage velocities
+    int32_t *sid = reinterpret_cast<int32_t *>(sv + 3 * kStage);   // kStage ids
+    uint16_t *slid = reinterpret_cast<uint16_t *>(sid + kStage);   // kStage table slots
+    uint16_t *srank = slid + kStage;                               // kStage ranks
+    int32_t *hkey = reinterpret_cast<int32_t *>(srank + kStage);   // kHash keys
+    int32_t *hcnt = hkey + kHash;                                  // kHash counts
+    int32_t *hbase = hcnt + kHash;                                 // kHash global bases
+    __shared__ int overflow;
+
+    const int cur = ctrl->cur;
+    const ParticleSet src = ctrl->sets[cur];
+    const ParticleSet dst = ctrl->sets[1 - cur];
+    const int64_t nslices = (n + kStage - 1) / kStage;
     int bad = 0;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int64_t p = base + threadIdx.x;
-        const bool act = p < n;
-        const unsigned active = __ballot_sync(0xffffffffu, act);
-        if (act) {
-            const int key = tile_key(ps.cell[p], g, bad);
-            warp_agg_increment(bins, key, active);
+    for (int64_t sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+        const int64_t s0 = sl * kStage;
+        const int m = (int)(s0 + kStage <= n ? kStage : n - s0);
+        for (int h = threadIdx.x; h < kHash; h += blockDim.x) {
+            hkey[h] = -1;
+            hcnt[h] = 0;
         }
+        if (threadIdx.x == 0) overflow = 0;
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            const int64_t p = s0 + j;
+            sc[j] = __ldcs(src.cell + p);
+            so[j] = __ldcs(src.o[0] + p);
+            so[kStage + j] = __ldcs(src.o[1] + p);
+            so[2 * kStage + j] = __ldcs(src.o[2] + p);
+            sv[j] = __ldcs(src.v[0] + p);
+            sv[kStage + j] = __ldcs(src.v[1] + p);
+            sv[2 * kStage + j] = __ldcs(src.v[2] + p);
+            sid[j] = __ldcs(src.pid + p);
+        }
+        __syncthreads();
+        // slot of each particle's tile in the table, and its rank there
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            const int key = tile_key(sc[j], g, bad);
+            int h = (int)(((unsigned)key * 2654435761u) >> 24) & (kHash - 1);
+            int probes = 0;
+            while (true) {
+                const int k = hkey[h];
+                if (k == key) break;
+                if (k == -1) {
+                    const int prev = atomicCAS(&hkey[h], -1, key);
+                    if (prev == -1 || prev == key) break;
+                }
+                h = (h + 1) & (kHash - 1);
+                if (++probes >= kHash) {   // table full
+                    h = -1;
+                    break;
+                }
+            }
+            if (h < 0) {
+                overflow = 1;
+                slid[j] = 0xffff;
+            } else {
+                slid[j] = (uint16_t)h;
+                srank[j] = (uint16_t)atomicAdd(&hcnt[h], 1);
+            }
+        }
+        __syncthreads();
+        if (overflow) {
+            // arbitrary input order: claim per particle (aggregated per warp)
+            const int lane = threadIdx.x & 31;
+            for (int jb = 0; jb < m; jb += blockDim.x) {
+                const int j = jb + threadIdx.x;
+                const bool act = j < m;
+                const unsigned active = __ballot_sync(0xffffffffu, act);
+                if (act) {
+                    const int key = tile_key(sc[j], g, bad);
+                    const unsigned peers = __match_any_sync(active, key);
+                    const int leader = __ffs(peers) - 1;
+                    int old = 0;
+                    if (lane == leader) old = atomicAdd(bins + key, __popc(peers));
+                    const int q = __shfl_sync(peers, old, leader) + __popc(peers & ((1u << lane) - 1u));
+                    dst.cell[q] = sc[j];
+                    dst.o[0][q] = so[j];
+                    dst.o[1][q] = so[kStage + j];
+                    dst.o[2][q] = so[2 * kStage + j];
+                    dst.v[0][q] = sv[j];
+                    dst.v[1][q] = sv[kStage + j];
+                    dst.v[2][q] = sv[2 * kStage + j];
+                    dst.pid[q] = sid[j];
+                }
+            }
+        } else {
+            for (int h = threadIdx.x; h < kHash; h += blockDim.x)
+                if (hcnt[h] > 0) hbase[h] = atomicAdd(bins + hkey[h], hcnt[h]);
+            __syncthreads();
+            for (int j = threadIdx.x; j < m; j += blockDim.x) {
+                const int q = hbase[slid[j]] + srank[j];
+                dst.cell[q] = sc[j];
+                dst.o[0][q] = so[j];
+                dst.o[1][q] = so[kStage + j];
+                dst.o[2][q] = so[2 * kStage + j];
+                dst.v[0][q] = sv[j];
+                dst.v[1][q] = sv[kStage + j];
+                dst.v[2][q] = sv[2 * kStage + j];
+                dst.pid[q] = sid[j];
+            }
+        }
+        __syncthreads();
     }
     if (bad) atomicOr(&ctrl->flags, PIC_FLAG_BAD_CELL);
 }
 
-__global__ void k_scatter(int64_t n, Geom g, Ctrl *ctrl, int32_t *bins) {
-    const int cur = ctrl->cur;
-    const ParticleSet src = ctrl->sets[cur];
-    const ParticleSet dst = ctrl->sets[1 - cur];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int64_t p = base + threadIdx.x;
-        const bool act = p < n;
-        const unsigned active = __ballot_sync(0xffffffffu, act);
-        if (act) {
-            const int32_t c = src.cell[p];
-            int bad = 0;
-            const int key = tile_key(c, g, bad);
-            const int q = warp_agg_increment(bins, key, active);
-            dst.cell[q] = c;
-            dst.o[0][q] = src.o[0][p];
-            dst.o[1][q] = src.o[1][p];
-            dst.o[2][q] = src.o[2][p];
-            dst.v[0][q] = src.v[0][p];
-            dst.v[1][q] = src.v[1][p];
-            dst.v[2][q] = src.v[2][p];
-            dst.pid[q] = src.pid[p];
+// Histogram with the same per-slice aggregation: counts of the slice's
+// distinct tiles in a shared hash table, one global atomic per tile and
+// slice (per-warp aggregated atomics when the table overflows).
+__global__ void __launch_bounds__(256) k_histogram_staged(int64_t n, Geom g, Ctrl *ctrl,
+                                                           int32_t *bins) {
+    __shared__ int32_t hkey[kHash];
+    __shared__ int32_t hcnt[kHash];
+    const ParticleSet ps = ctrl->sets[ctrl->cur];
+    const int64_t nslices = (n + kStage - 1) / kStage;
+    int bad = 0;
+    for (int64_t sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+        const int64_t s0 = sl * kStage;
+        const int m = (int)(s0 + kStage <= n ? kStage : n - s0);
+        for (int h = threadIdx.x; h < kHash; h += blockDim.x) {
+            hkey[h] = -1;
+            hcnt[h] = 0;
         }
+        __syncthreads();
+        for (int jb = 0; jb < m; jb += blockDim.x) {
+            const int j = jb + threadIdx.x;
+            const bool act = j < m;
+            int key = 0;
+            if (act) key = tile_key(__ldcs(ps.cell + s0 + j), g, bad);
+            int h = -2;
+            if (act) {
+                h = (int)(((unsigned)key * 2654435761u) >> 24) & (kHash - 1);
+                int probes = 0;
+                while (true) {
+                    const int k = hkey[h];
+                    if (k == key) break;
+                    if (k == -1) {
+                        const int prev = atomicCAS(&hkey[h], -1, key);
+                        if (prev == -1 || prev == key) break;
+                    }
+                    h = (h + 1) & (kHash - 1);
+                    if (++probes >= kHash) {
+                        h = -1;
+                        break;
+                    }
+                }
+                if (h >= 0) atomicAdd(&hcnt[h], 1);
+                else atomicAdd(bins + key, 1);   // table full: straight to the grid
+            }
+        }
+        __syncthreads();
+        for (int h = threadIdx.x; h < kHash; h += blockDim.x)
+            if (hcnt[h] > 0) atomicAdd(bins + hkey[h], hcnt[h]);
+        __syncthreads();
     }
+    if (bad) atomicOr(&ctrl->flags, PIC_FLAG_BAD_CELL);
 }
+
+constexpr size_t kStageSmem = (size_t)kStage * (4 + 12 + 12 + 4 + 2 + 2) + (size_t)kHash * 12;
 
 // ---- exclusive scan of int32 (in place), total written to data[n] -------------
 
@@ -173,7 +295,7 @@ __global__ void k_scan_apply(int32_t *data, int64_t n, const int32_t *sums, int 
     if (blockIdx.x == 0 && threadIdx.x == 0) data[n] = sums[nb];
 }
 
-cudaError_t exclusive_scan(int32_t *data, int64_t n, int32_t *tmp, cudaStream_t st) {
+cudaError_t exclusive_scan_impl(int32_t *data, int64_t n, int32_t *tmp, cudaStream_t st) {
     const int nb = (int)((n + kScanSeg - 1) / kScanSeg);
     if (nb == 0) {
         return cudaMemsetAsync(data, 0, sizeof(int32_t), st);
@@ -186,12 +308,12 @@ cudaError_t exclusive_scan(int32_t *data, int64_t n, int32_t *tmp, cudaStream_t 
 
 // ---- work list ----------------------------------------------------------------
 
-__global__ void k_tile_ranges(const int32_t *__restrict__ bin_end, int ntiles, int tvol,
-                              int chunk, int32_t *tile_items, int2 *tile_range) {
+__global__ void k_tile_ranges(const int32_t *__restrict__ bin_end, int ntiles, int chunk,
+                              int32_t *tile_items, int2 *tile_range) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
-    const int s = (t == 0) ? 0 : bin_end[(int64_t)t * tvol - 1];
-    const int e = bin_end[(int64_t)(t + 1) * tvol - 1];
+    const int s = (t == 0) ? 0 : bin_end[t - 1];
+    const int e = bin_end[t];
     tile_range[t] = make_int2(s, e);
     tile_items[t] = (e - s + chunk - 1) / chunk;
 }
@@ -214,27 +336,52 @@ __global__ void k_fill_items(int ntiles, int chunk, const int32_t *__restrict__ 
 
 }  // namespace
 
+cudaError_t exclusive_scan(int32_t *data, int64_t n, int32_t *tmp, cudaStream_t st) {
+    return exclusive_scan_impl(data, n, tmp, st);
+}
+
+// per-tile ranges from the bin ends left by a scatter, then the work items
+cudaError_t launch_worklist(const int32_t *bin_end, int ntiles, int chunk, int32_t *tile_items,
+                            int2 *tile_range, int4 *items, int32_t *scan_tmp, Ctrl *ctrl, int flip,
+                            cudaStream_t st) {
+    const int T = 256;
+    const int tb = (ntiles + T - 1) / T;
+    k_tile_ranges<<<tb, T, 0, st>>>(bin_end, ntiles, chunk, tile_items, tile_range);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = exclusive_scan_impl(tile_items, ntiles, scan_tmp, st)) != cudaSuccess) return e;
+    k_fill_items<<<tb, T, 0, st>>>(ntiles, chunk, tile_items, tile_range, items, ctrl, flip);
+    return cudaGetLastError();
+}
+
+// One-time set-up outside any stream capture: the staged scatter's shared memory.
+cudaError_t sort_prepare() {
+    return cudaFuncSetAttribute(k_scatter_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kStageSmem);
+}
+
 cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t *bins,
                         int64_t nbins, int32_t *scan_tmp, int32_t *tile_items,
                         int2 *tile_range, int4 *items, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(nbins + 1), st);
     if (e != cudaSuccess) return e;
     const int T = 256;
-    const int blocks = (int)std::min<int64_t>((n + T - 1) / T, 152 * 16);
     if (n > 0) {
-        k_histogram<<<blocks, T, 0, st>>>(n, g, ctrl, bins);
+        const int hblocks = (int)std::min<int64_t>((n + kStage - 1) / kStage, 152 * 8);
+        k_histogram_staged<<<hblocks, T, 0, st>>>(n, g, ctrl, bins);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if ((e = exclusive_scan(bins, nbins, scan_tmp, st)) != cudaSuccess) return e;
+    if ((e = exclusive_scan_impl(bins, nbins, scan_tmp, st)) != cudaSuccess) return e;
     if (n > 0) {
-        k_scatter<<<blocks, T, 0, st>>>(n, g, ctrl, bins);
+        const int sblocks = (int)std::min<int64_t>((n + kStage - 1) / kStage, 152 * 3);
+        k_scatter_staged<<<sblocks, T, kStageSmem, st>>>(n, g, ctrl, bins);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int ntiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
     const int tb = (ntiles + T - 1) / T;
-    k_tile_ranges<<<tb, T, 0, st>>>(bins, ntiles, g.tvol, chunk, tile_items, tile_range);
+    k_tile_ranges<<<tb, T, 0, st>>>(bins, ntiles, chunk, tile_items, tile_range);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = exclusive_scan(tile_items, ntiles, scan_tmp, st)) != cudaSuccess) return e;
+    if ((e = exclusive_scan_impl(tile_items, ntiles, scan_tmp, st)) != cudaSuccess) return e;
     k_fill_items<<<tb, T, 0, st>>>(ntiles, chunk, tile_items, tile_range, items, ctrl,
                                    n > 0 ? 1 : 0);
     return cudaGetLastError();

@@ -48,8 +48,8 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Byte offsets of every device buffer inside the caller's arena.
 struct Layout {
-    size_t ctrl, sets, rho, rho_hat, E_hat, E4, bins, scan_tmp, tile_items, tile_range, items,
-        fpart, ppart, ring, inv, stage_x, stage_v, fft, total;
+    size_t ctrl, sets, rho, rho64, rho_hat, E_hat, E4, bins, scan_tmp, tile_items, tile_range,
+        items, fpart, ppart, ring, inv, stage_x, stage_v, adjE4, fft, total;
     size_t set_stride;   // bytes of one per-particle array
 };
 
@@ -78,8 +78,20 @@ struct pic_ctx {
     bool bound;
     char *arena;
     cudaStream_t st;
-    cufftHandle r2c, c2r;
+    cufftHandle r2c, c2r;     // rho -> rho^ ; 3 x E^ -> E4 (stride 4)
+    cufftHandle r2c3, c2r1;   // adjoint: lE4 (stride 4) -> 3 x lE^ ; lrho^ -> lrho
     bool plans;
+    ParticleSet hsets[2];     // host copies of the device set descriptors
+    // state of the last pic_adjoint_forward
+    struct {
+        bool ready;
+        int n_steps, K, nseg, cur;
+        double w[3];
+        char *buf;
+        int64_t step0;
+        int since0;
+        long long step0_dev;
+    } adj;
     // phase timers: a ring of event pairs per phase, drained when it wraps
     bool timing;
     bool events_made;
@@ -93,6 +105,7 @@ struct pic_ctx {
     int64_t step;
     int since_sort;
     bool loaded;
+    bool rho_current;   // rho holds the deposit of the current positions
 
     template <class T>
     T *at(size_t off) const { return reinterpret_cast<T *>(arena + off); }
@@ -114,40 +127,56 @@ int fft_dims(const pic_ctx *c, long long *n, long long *nin) {
     return r;
 }
 
-int make_plans(pic_ctx *c, bool estimate_only, size_t *ws_r2c, size_t *ws_c2r) {
-    long long n[3], nin[3], nout[3];
-    const int rank = fft_dims(c, n, nin);
-    for (int d = 0; d < rank; ++d) nout[d] = n[d];
-    cufftHandle a = 0, b = 0;
-    PIC_CUFFT(cufftCreate(&a));
-    cufftResult r = cufftCreate(&b);
-    if (r != CUFFT_SUCCESS) {
-        cufftDestroy(a);
-        return fail(PIC_ERR_CUFFT, "cufftCreate failed: %d", (int)r);
+// The four transforms: rho -> rho^ (R2C), 3 x E^ -> E4 (C2R, batch 3, output
+// stride 4), lE4 -> 3 x lE^ (R2C, batch 3, input stride 4), lrho^ -> lrho (C2R).
+int make_plans(pic_ctx *c, bool estimate_only, size_t *ws_max) {
+    long long n[3], nh[3];
+    const int rank = fft_dims(c, n, nh);
+    cufftHandle p[4] = {0, 0, 0, 0};
+    size_t ws[4] = {0, 0, 0, 0};
+    cufftResult r = CUFFT_SUCCESS;
+    int made = 0;
+    for (; made < 4 && r == CUFFT_SUCCESS; ++made) {
+        r = cufftCreate(&p[made]);
+        if (r != CUFFT_SUCCESS) break;
+        cufftSetAutoAllocation(p[made], 0);
     }
-    cufftSetAutoAllocation(a, 0);
-    cufftSetAutoAllocation(b, 0);
-    if (estimate_only) {
-        r = cufftGetSizeMany64(a, rank, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1, ws_r2c);
-        if (r == CUFFT_SUCCESS)
-            r = cufftGetSizeMany64(b, rank, n, nin, 1, c->nhalf, nout, 4, 1, CUFFT_C2R, 3, ws_c2r);
-        cufftDestroy(a);
-        cufftDestroy(b);
-        if (r != CUFFT_SUCCESS) return fail(PIC_ERR_CUFFT, "cufftGetSizeMany64 failed: %d", (int)r);
+    auto plan = [&](int q, long long *inembed, long long istride, long long idist,
+                    long long *onembed, long long ostride, long long odist, cufftType t,
+                    long long batch) {
+        if (estimate_only)
+            return cufftGetSizeMany64(p[q], rank, n, inembed, istride, idist, onembed, ostride,
+                                      odist, t, batch, &ws[q]);
+        return cufftMakePlanMany64(p[q], rank, n, inembed, istride, idist, onembed, ostride, odist,
+                                   t, batch, &ws[q]);
+    };
+    if (r == CUFFT_SUCCESS) r = plan(0, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1);
+    if (r == CUFFT_SUCCESS) r = plan(1, nh, 1, c->nhalf, n, 4, 1, CUFFT_C2R, 3);
+    if (r == CUFFT_SUCCESS) r = plan(2, n, 4, 1, nh, 1, c->nhalf, CUFFT_R2C, 3);
+    if (r == CUFFT_SUCCESS) r = plan(3, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 1);
+    if (r != CUFFT_SUCCESS || estimate_only) {
+        for (int q = 0; q < made && q < 4; ++q)
+            if (p[q]) cufftDestroy(p[q]);
+        if (r != CUFFT_SUCCESS) return fail(PIC_ERR_CUFFT, "cuFFT plan setup failed: %d", (int)r);
+        *ws_max = std::max(std::max(ws[0], ws[1]), std::max(ws[2], ws[3]));
         return PIC_OK;
     }
-    r = cufftMakePlanMany64(a, rank, n, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1, ws_r2c);
-    if (r == CUFFT_SUCCESS)
-        r = cufftMakePlanMany64(b, rank, n, nin, 1, c->nhalf, nout, 4, 1, CUFFT_C2R, 3, ws_c2r);
-    if (r != CUFFT_SUCCESS) {
-        cufftDestroy(a);
-        cufftDestroy(b);
-        return fail(PIC_ERR_CUFFT, "cufftMakePlanMany64 failed: %d", (int)r);
-    }
-    c->r2c = a;
-    c->c2r = b;
+    c->r2c = p[0];
+    c->c2r = p[1];
+    c->r2c3 = p[2];
+    c->c2r1 = p[3];
     c->plans = true;
+    *ws_max = std::max(std::max(ws[0], ws[1]), std::max(ws[2], ws[3]));
     return PIC_OK;
+}
+
+void destroy_plans(pic_ctx *c) {
+    if (!c->plans) return;
+    cufftDestroy(c->r2c);
+    cufftDestroy(c->c2r);
+    cufftDestroy(c->r2c3);
+    cufftDestroy(c->c2r1);
+    c->plans = false;
 }
 
 void compute_layout(pic_ctx *c) {
@@ -163,6 +192,7 @@ void compute_layout(pic_ctx *c) {
     L.ctrl = take(sizeof(Ctrl));
     L.sets = take(2 * 8 * L.set_stride);
     L.rho = take((size_t)c->ng * 4);
+    L.rho64 = take((size_t)c->ng * 8);
     L.rho_hat = take((size_t)c->nhalf * 8);
     L.E_hat = take((size_t)c->nhalf * 8 * 3);
     L.E4 = take((size_t)c->ng * 16);
@@ -178,6 +208,7 @@ void compute_layout(pic_ctx *c) {
     L.inv = take(capb);
     L.stage_x = take((size_t)c->staging * 24);
     L.stage_v = take((size_t)c->staging * 24);
+    L.adjE4 = take((size_t)c->ng * 16);
     L.fft = take(c->fft_reserve);
     L.total = o;
 }
@@ -195,9 +226,9 @@ int check_loaded(const pic_ctx *c) {
     return PIC_OK;
 }
 
-float qscale_of(const pic_ctx *c) {
-    if (c->np <= 0) return 0.0f;
-    return (float)(c->sp.total_charge / (double)c->np / c->dV);
+double qscale_of(const pic_ctx *c) {
+    if (c->np <= 0) return 0.0;
+    return c->sp.total_charge / (double)c->np / c->dV;
 }
 
 double mp_of(const pic_ctx *c) {
@@ -205,9 +236,10 @@ double mp_of(const pic_ctx *c) {
     return c->sp.total_charge / (double)c->np / c->sp.q_over_m;
 }
 
+// the push kernel takes 4 particles per thread and fits 3 blocks per SM
 int push_blocks_of(const pic_ctx *c) {
-    const int64_t b = (c->np + c->block - 1) / c->block;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(b, kMaxPushBlocks));
+    const int64_t b = (c->np / 4 + c->block - 1) / c->block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, std::min(kMaxPushBlocks, 152 * 3 * 2)));
 }
 
 PushConst push_const(const pic_ctx *c) {
@@ -273,15 +305,22 @@ int do_sort(pic_ctx *c) {
 }
 
 int do_deposit(pic_ctx *c) {
-    PIC_CUDA(cudaMemsetAsync(c->at<float>(c->lay.rho), 0, (size_t)c->ng * 4, c->st));
+    // the fixed-point path overwrites every node of rho (and re-zeroes the
+    // integer grid); the FP32 path accumulates into a cleared rho
+    if (!(c->prm.options & PIC_OPT_FIXED_DEPOSIT) || c->np <= 0)
+        PIC_CUDA(cudaMemsetAsync(c->at<float>(c->lay.rho), 0, (size_t)c->ng * 4, c->st));
     if (c->np > 0) {
         int r = timer_begin(c, PIC_PHASE_DEPOSIT);
         if (r) return r;
+        const bool fixed = (c->prm.options & PIC_OPT_FIXED_DEPOSIT) != 0;
         PIC_CUDA(launch_deposit(c->np, c->geom, c->ctrl(), c->at<int4>(c->lay.items),
                                 (int)c->max_items, qscale_of(c), c->at<float>(c->lay.rho),
-                                c->ctrl(), c->deposit_blocks, c->sparse_below, c->st));
-        return timer_end(c, PIC_PHASE_DEPOSIT, 1);
+                                c->at<unsigned long long>(c->lay.rho64), fixed, c->ctrl(),
+                                c->deposit_blocks, c->sparse_below, c->st));
+        c->rho_current = true;
+        return timer_end(c, PIC_PHASE_DEPOSIT, fixed ? 2 : 1);
     }
+    c->rho_current = true;
     return PIC_OK;
 }
 
@@ -303,18 +342,116 @@ int do_gather_push(pic_ctx *c, bool diag) {
                                 push_blocks_of(c), c->block, c->st));
     c->step += 1;
     c->since_sort += 1;
+    c->rho_current = false;
     return timer_end(c, PIC_PHASE_PUSH, 1);
 }
 
-int do_diag(pic_ctx *c) {
+int do_diag_field(pic_ctx *c) {
     int r = timer_begin(c, PIC_PHASE_DIAG);
     if (r) return r;
     PIC_CUDA(launch_diag_field(c->geom, c->at<float>(c->lay.rho), c->at<float4>(c->lay.E4),
                                c->at<double>(c->lay.fpart), c->st));
+    return timer_end(c, PIC_PHASE_DIAG, 1);
+}
+
+int do_diag_finalize(pic_ctx *c, int push_blocks) {
+    int r = timer_begin(c, PIC_PHASE_DIAG);
+    if (r) return r;
     PIC_CUDA(launch_diag_finalize(c->at<double>(c->lay.fpart), c->at<double>(c->lay.ppart),
-                                  push_blocks_of(c), c->dV, mp_of(c), c->prm.dt, c->ctrl(),
+                                  push_blocks, c->dV, mp_of(c), c->prm.dt, c->ctrl(),
                                   c->at<pic_diag_t>(c->lay.ring), c->prm.diag_capacity, c->st));
-    return timer_end(c, PIC_PHASE_DIAG, 2);
+    return timer_end(c, PIC_PHASE_DIAG, 1);
+}
+
+int fused_blocks_of(const pic_ctx *c) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(c->max_items, std::min(kMaxPushBlocks, 152 * 3 * 2)));
+}
+
+// gather + push + deposit of the new positions in one kernel (pic_step)
+int do_push_deposit(pic_ctx *c, bool diag) {
+    const bool fixed = (c->prm.options & PIC_OPT_FIXED_DEPOSIT) != 0;
+    if (!fixed || c->np <= 0)
+        PIC_CUDA(cudaMemsetAsync(c->at<float>(c->lay.rho), 0, (size_t)c->ng * 4, c->st));
+    int r = timer_begin(c, PIC_PHASE_PUSH);
+    if (r) return r;
+    if (c->np > 0) {
+        PIC_CUDA(launch_push_deposit(c->geom, push_const(c), diag, fixed, c->ctrl(),
+                                     c->at<int4>(c->lay.items), (int)c->max_items,
+                                     c->at<float4>(c->lay.E4), c->at<float>(c->lay.rho),
+                                     c->at<unsigned long long>(c->lay.rho64), qscale_of(c),
+                                     c->sparse_below, c->at<double>(c->lay.ppart),
+                                     fused_blocks_of(c), c->st));
+    } else {
+        // nothing to push: the plain kernel still records zero moments and the step
+        PIC_CUDA(launch_gather_push(0, c->geom, push_const(c), diag, c->ctrl(),
+                                    c->at<float4>(c->lay.E4), c->at<double>(c->lay.ppart), 1,
+                                    c->block, c->st));
+    }
+    c->step += 1;
+    c->since_sort += 1;
+    c->rho_current = true;
+    return timer_end(c, PIC_PHASE_PUSH, c->np > 0 ? (fixed ? 2 : 1) : 1);
+}
+
+// ---- adjoint buffer layout (caller-owned device memory) ---------------------
+struct AdjLayout {
+    size_t arr, ckpt, segy, segE, n_ckpt, off_segy, off_segE, total;
+};
+
+AdjLayout adj_layout(const pic_ctx *c, int n_steps, int K) {
+    AdjLayout L;
+    L.arr = align_up((size_t)std::max<int64_t>(c->cap, 1) * 4);
+    L.ckpt = 7 * L.arr;                       // cell, o[3], v[3]
+    L.segy = 4 * L.arr;                       // cell, o[3]
+    L.segE = align_up((size_t)c->ng * 16);    // E4 of one step
+    const int nseg = n_steps > 1 ? (n_steps - 1 + K - 1) / K : 0;
+    L.n_ckpt = (size_t)std::max(nseg, 1);
+    L.off_segy = L.n_ckpt * L.ckpt;
+    L.off_segE = L.off_segy + (size_t)K * L.segy;
+    L.total = L.off_segE + (size_t)K * L.segE;
+    return L;
+}
+
+int copy_arrays(pic_ctx *c, char *const dst[], char *const src[], int count) {
+    const size_t bytes = (size_t)c->np * 4;
+    if (bytes == 0) return PIC_OK;
+    for (int q = 0; q < count; ++q)
+        PIC_CUDA(cudaMemcpyAsync(dst[q], src[q], bytes, cudaMemcpyDeviceToDevice, c->st));
+    return PIC_OK;
+}
+
+void set_arrays(const ParticleSet &s, char *out[7]) {
+    out[0] = reinterpret_cast<char *>(s.cell);
+    for (int d = 0; d < 3; ++d) {
+        out[1 + d] = reinterpret_cast<char *>(s.o[d]);
+        out[4 + d] = reinterpret_cast<char *>(s.v[d]);
+    }
+}
+
+void buf_arrays(char *base, size_t arr, int count, char *out[]) {
+    for (int q = 0; q < count; ++q) out[q] = base + (size_t)q * arr;
+}
+
+int adj_save(pic_ctx *c, const AdjLayout &L, int slot) {
+    char *dst[7], *src[7];
+    buf_arrays(c->adj.buf + (size_t)slot * L.ckpt, L.arr, 7, dst);
+    set_arrays(c->hsets[c->adj.cur], src);
+    return copy_arrays(c, dst, src, 7);
+}
+
+int adj_restore(pic_ctx *c, const AdjLayout &L, int slot) {
+    char *dst[7], *src[7];
+    buf_arrays(c->adj.buf + (size_t)slot * L.ckpt, L.arr, 7, src);
+    set_arrays(c->hsets[c->adj.cur], dst);
+    return copy_arrays(c, dst, src, 7);
+}
+
+int adj_solve(pic_ctx *c) {
+    PIC_CUFFT(cufftExecR2C(c->r2c3, c->at<cufftReal>(c->lay.adjE4), c->at<cufftComplex>(c->lay.E_hat)));
+    PIC_CUDA(launch_green_adj(c->geom, c->L, c->at<float2>(c->lay.E_hat),
+                              c->at<float2>(c->lay.rho_hat), c->nhalf, c->st));
+    PIC_CUFFT(cufftExecC2R(c->c2r1, c->at<cufftComplex>(c->lay.rho_hat), c->at<cufftReal>(c->lay.rho)));
+    return PIC_OK;
 }
 
 // Reset the resettable head of the control block (everything before `cur`).
@@ -365,7 +502,9 @@ int pic_create(const pic_grid_t *grid, const pic_species_t *species, const pic_p
             return fail(PIC_ERR_ARG, "mode[%d] = %d beyond the Nyquist index", d, params->mode[d]);
     if (params->block != 0 && (params->block < 32 || params->block > 256 || params->block % 32))
         return fail(PIC_ERR_ARG, "block must be 0 or a multiple of 32 in 32..256");
-    if (params->chunk != 0 && params->chunk < 32) return fail(PIC_ERR_ARG, "chunk must be >= 32");
+    if (params->chunk != 0 && (params->chunk < 32 || params->chunk > kMaxChunk))
+        return fail(PIC_ERR_ARG, "chunk must be 0 or in 32..%d", kMaxChunk);
+    if (params->options & ~PIC_OPT_FIXED_DEPOSIT) return fail(PIC_ERR_ARG, "unknown option bits");
 
     pic_ctx *c = new (std::nothrow) pic_ctx();
     if (!c) return fail(PIC_ERR_ARG, "out of host memory");
@@ -377,7 +516,7 @@ int pic_create(const pic_grid_t *grid, const pic_species_t *species, const pic_p
     if (p.diag_capacity == 0) p.diag_capacity = 1024;
     if (p.guard == 0) p.guard = 2;
     c->block = p.block ? p.block : 256;
-    c->chunk = p.chunk ? p.chunk : 4096;
+    c->chunk = p.chunk ? p.chunk : kMaxChunk;
 
     Geom &g = c->geom;
     int64_t nt = 1;
@@ -399,10 +538,10 @@ int pic_create(const pic_grid_t *grid, const pic_species_t *species, const pic_p
     g.tvol = g.tile[0] * g.tile[1] * g.tile[2];
     c->dV = c->h[0] * c->h[1] * c->h[2];
     c->ntiles = nt;
-    c->nbins = nt * g.tvol;
+    c->nbins = nt;    // the binning key is the deposit tile
     if (c->nbins > 2147483647LL - 1) {
         delete c;
-        return fail(PIC_ERR_ARG, "too many bins for this grid and tile");
+        return fail(PIC_ERR_ARG, "too many tiles for this grid");
     }
     c->cap = species->n_particles;
     c->ng = (int64_t)grid->n[0] * grid->n[1] * grid->n[2];
@@ -424,9 +563,9 @@ int pic_create(const pic_grid_t *grid, const pic_species_t *species, const pic_p
 
     // cuFFT work area: the library's own size query when it works here,
     // never less than a conservative bound
-    size_t w1 = 0, w2 = 0;
+    size_t wmax = 0;
     size_t bound = (size_t)c->nhalf * 8 * 3 + ((size_t)4 << 20);
-    if (make_plans(c, true, &w1, &w2) == PIC_OK) bound = std::max(bound, std::max(w1, w2));
+    if (make_plans(c, true, &wmax) == PIC_OK) bound = std::max(bound, wmax);
     c->fft_reserve = bound;
     compute_layout(c);
     *out = c;
@@ -449,31 +588,27 @@ int pic_bind_workspace(pic_handle_t c, void *arena, size_t bytes, void *stream) 
     if ((uintptr_t)arena % kAlign) return fail(PIC_ERR_ARG, "arena not %zu-byte aligned", kAlign);
     if (bytes < c->lay.total)
         return fail(PIC_ERR_CAPACITY, "arena of %zu bytes < required %zu", bytes, c->lay.total);
-    if (c->plans) {
-        cufftDestroy(c->r2c);
-        cufftDestroy(c->c2r);
-        c->plans = false;
-    }
+    destroy_plans(c);
     c->bound = false;
     c->loaded = false;
+    c->adj.ready = false;
     c->arena = static_cast<char *>(arena);
     c->st = static_cast<cudaStream_t>(stream);
-    size_t w1 = 0, w2 = 0;
-    int r = make_plans(c, false, &w1, &w2);
+    size_t wmax = 0;
+    int r = make_plans(c, false, &wmax);
     if (r) return r;
-    if (std::max(w1, w2) > c->fft_reserve) {
-        cufftDestroy(c->r2c);
-        cufftDestroy(c->c2r);
-        c->plans = false;
-        return fail(PIC_ERR_CAPACITY, "cuFFT needs %zu work bytes, %zu reserved",
-                    std::max(w1, w2), c->fft_reserve);
+    if (wmax > c->fft_reserve) {
+        destroy_plans(c);
+        return fail(PIC_ERR_CAPACITY, "cuFFT needs %zu work bytes, %zu reserved", wmax,
+                    c->fft_reserve);
     }
     void *work = c->arena + c->lay.fft;
-    PIC_CUFFT(cufftSetWorkArea(c->r2c, work));
-    PIC_CUFFT(cufftSetWorkArea(c->c2r, work));
-    PIC_CUFFT(cufftSetStream(c->r2c, c->st));
-    PIC_CUFFT(cufftSetStream(c->c2r, c->st));
+    for (cufftHandle p : {c->r2c, c->c2r, c->r2c3, c->c2r1}) {
+        PIC_CUFFT(cufftSetWorkArea(p, work));
+        PIC_CUFFT(cufftSetStream(p, c->st));
+    }
 
+    PIC_CUDA(sort_prepare());
     Ctrl h;
     memset(&h, 0, sizeof(h));
     for (int s = 0; s < 2; ++s) {
@@ -486,9 +621,12 @@ int pic_bind_workspace(pic_handle_t c, void *arena, size_t bytes, void *stream) 
         }
         ps.pid = reinterpret_cast<int32_t *>(base + (size_t)7 * c->lay.set_stride);
     }
+    c->hsets[0] = h.sets[0];
+    c->hsets[1] = h.sets[1];
     PIC_CUDA(cudaMemcpyAsync(c->ctrl(), &h, sizeof(h), cudaMemcpyHostToDevice, c->st));
     PIC_CUDA(cudaMemsetAsync(c->at<char>(c->lay.E4), 0, (size_t)c->ng * 16, c->st));
     PIC_CUDA(cudaMemsetAsync(c->at<char>(c->lay.rho), 0, (size_t)c->ng * 4, c->st));
+    PIC_CUDA(cudaMemsetAsync(c->at<char>(c->lay.rho64), 0, (size_t)c->ng * 8, c->st));
     PIC_CUDA(cudaMemsetAsync(c->at<char>(c->lay.ring), 0,
                              (size_t)c->prm.diag_capacity * sizeof(pic_diag_t), c->st));
     PIC_CUDA(cudaStreamSynchronize(c->st));
@@ -503,21 +641,17 @@ int pic_set_stream(pic_handle_t c, void *stream) {
     int r = check_ready(c);
     if (r) return r;
     c->st = static_cast<cudaStream_t>(stream);
-    PIC_CUFFT(cufftSetStream(c->r2c, c->st));
-    PIC_CUFFT(cufftSetStream(c->c2r, c->st));
+    for (cufftHandle p : {c->r2c, c->c2r, c->r2c3, c->c2r1}) PIC_CUFFT(cufftSetStream(p, c->st));
     return PIC_OK;
 }
 
 void pic_destroy(pic_handle_t c) {
     if (!c) return;
+    destroy_plans(c);
     if (c->events_made)
         for (int p = 0; p < PIC_PHASE_COUNT; ++p)
             for (int s = 0; s < kTimerRing; ++s)
                 for (int e = 0; e < 2; ++e) cudaEventDestroy(c->ev[p][s][e]);
-    if (c->plans) {
-        cufftDestroy(c->r2c);
-        cufftDestroy(c->c2r);
-    }
     delete c;
 }
 
@@ -544,6 +678,7 @@ int pic_load_particles(pic_handle_t c, const double *x, const double *v, int64_t
     c->np = n;
     c->step = 0;
     c->loaded = true;
+    c->rho_current = false;
     if ((r = do_sort(c))) return r;
     if (!src_is_device) PIC_CUDA(cudaStreamSynchronize(c->st));
     return PIC_OK;
@@ -583,6 +718,7 @@ int pic_get_field(pic_handle_t c, float *rho, float *E, int dst_is_device) {
 int pic_set_rho(pic_handle_t c, const float *rho, int src_is_device) {
     int r = check_ready(c);
     if (r) return r;
+    c->rho_current = false;
     if (!rho) return fail(PIC_ERR_ARG, "null rho");
     const cudaMemcpyKind k = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     PIC_CUDA(cudaMemcpyAsync(c->at<float>(c->lay.rho), rho, (size_t)c->ng * 4, k, c->st));
@@ -625,15 +761,19 @@ int pic_step(pic_handle_t c, int n) {
     int r = check_loaded(c);
     if (r) return r;
     if (n < 0) return fail(PIC_ERR_ARG, "negative step count");
+    // each step: [re-bin] -> (deposit, only if rho is stale) -> solve ->
+    // [field diagnostics, before rho is replaced] -> fused gather + push +
+    // deposit of the new positions -> [particle diagnostics]
     for (int s = 0; s < n; ++s) {
         if (c->prm.sort_period > 0 && c->since_sort >= c->prm.sort_period) {
             if ((r = do_sort(c))) return r;
         }
-        if ((r = do_deposit(c))) return r;
+        if (!c->rho_current && (r = do_deposit(c))) return r;
         if ((r = do_solve(c))) return r;
         const bool diag = c->prm.diag_every > 0 && ((c->step + 1) % c->prm.diag_every == 0);
-        if ((r = do_gather_push(c, diag))) return r;
-        if (diag && (r = do_diag(c))) return r;
+        if (diag && (r = do_diag_field(c))) return r;
+        if ((r = do_push_deposit(c, diag))) return r;
+        if (diag && (r = do_diag_finalize(c, c->np > 0 ? fused_blocks_of(c) : 1))) return r;
     }
     return PIC_OK;
 }
@@ -669,6 +809,160 @@ int pic_device_flags(pic_handle_t c, int32_t *flags, int clear) {
     PIC_CUDA(cudaMemcpy(&f, c->ctrl(), sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (flags) *flags = f;
     if (clear) PIC_CUDA(cudaMemset(c->ctrl(), 0, sizeof(int32_t)));
+    return PIC_OK;
+}
+
+int pic_adjoint_buffer_bytes(pic_handle_t c, int n_steps, int K, size_t *bytes) {
+    if (!c || !bytes) return fail(PIC_ERR_ARG, "null argument");
+    if (n_steps < 1 || K < 1) return fail(PIC_ERR_ARG, "n_steps and checkpoint_every must be >= 1");
+    *bytes = adj_layout(c, n_steps, K).total;
+    return PIC_OK;
+}
+
+int pic_adjoint_forward(pic_handle_t c, int n_steps, int K, const double *w, void *buf,
+                        size_t bytes, double *J) {
+    int r = check_loaded(c);
+    if (r) return r;
+    if (n_steps < 1 || K < 1) return fail(PIC_ERR_ARG, "n_steps and checkpoint_every must be >= 1");
+    if (!w || !buf || !J) return fail(PIC_ERR_ARG, "null argument");
+    for (int d = 0; d < 3; ++d)
+        if (!isfinite(w[d]) || w[d] < 0.0) return fail(PIC_ERR_ARG, "weights must be finite and >= 0");
+    for (int d = 0; d < 3; ++d)
+        if (c->prm.B_ext[d] != 0.0)
+            return fail(PIC_ERR_ARG, "the adjoint of the magnetic rotation is not implemented (B_ext must be 0)");
+    if ((uintptr_t)buf % kAlign) return fail(PIC_ERR_ARG, "adjoint buffer not 256-byte aligned");
+    const AdjLayout L = adj_layout(c, n_steps, K);
+    if (bytes < L.total)
+        return fail(PIC_ERR_CAPACITY, "adjoint buffer of %zu bytes < required %zu", bytes, L.total);
+    PIC_CUDA(cudaStreamSynchronize(c->st));
+    int32_t cur = 0;
+    PIC_CUDA(cudaMemcpy(&cur, &c->ctrl()->cur, sizeof(cur), cudaMemcpyDeviceToHost));
+    PIC_CUDA(cudaMemcpy(&c->adj.step0_dev, &c->ctrl()->step, sizeof(long long), cudaMemcpyDeviceToHost));
+    c->adj.ready = false;
+    c->adj.n_steps = n_steps;
+    c->adj.K = K;
+    c->adj.nseg = n_steps > 1 ? (n_steps - 1 + K - 1) / K : 0;
+    c->adj.cur = cur;
+    c->adj.buf = static_cast<char *>(buf);
+    c->adj.step0 = c->step;
+    c->adj.since0 = c->since_sort;
+    for (int d = 0; d < 3; ++d) c->adj.w[d] = w[d];
+    if (c->adj.nseg == 0 && (r = adj_save(c, L, 0))) return r;
+    for (int s = 0; s < c->adj.nseg; ++s) {
+        if ((r = adj_save(c, L, s))) return r;
+        const int a0 = s * K, b0 = std::min(a0 + K, n_steps - 1);
+        for (int n = a0; n < b0; ++n) {
+            if ((r = do_deposit(c)) || (r = do_solve(c)) || (r = do_gather_push(c, false))) return r;
+        }
+    }
+    if ((r = do_deposit(c)) || (r = do_solve(c))) return r;
+    PIC_CUDA(launch_diag_field(c->geom, c->at<float>(c->lay.rho), c->at<float4>(c->lay.E4),
+                               c->at<double>(c->lay.fpart), c->st));
+    PIC_CUDA(launch_objective(c->at<double>(c->lay.fpart), kDiagFieldBlocks, c->dV, c->adj.w,
+                              &c->ctrl()->scalar[0], c->st));
+    PIC_CUDA(cudaMemcpyAsync(J, &c->ctrl()->scalar[0], sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    PIC_CUDA(cudaStreamSynchronize(c->st));
+    c->adj.ready = true;
+    return PIC_OK;
+}
+
+int pic_adjoint_backward(pic_handle_t c, double scale, double *gx, double *gv, int dst_is_device) {
+    int r = check_loaded(c);
+    if (r) return r;
+    if (!c->adj.ready) return fail(PIC_ERR_STATE, "no pic_adjoint_forward to reverse");
+    if (c->np > 0 && (!gx || !gv)) return fail(PIC_ERR_ARG, "null output array");
+    const AdjLayout L = adj_layout(c, c->adj.n_steps, c->adj.K);
+    const int K = c->adj.K;
+    const float qsc = (float)qscale_of(c);
+    const float c_kick = (float)(c->prm.dt * c->sp.q_over_m);
+    const float dt = (float)c->prm.dt, wz2 = (float)c->prm.wz2;
+    const ParticleSet &cs = c->hsets[c->adj.cur];
+    const float *cyo[3] = {cs.o[0], cs.o[1], cs.o[2]};
+    float4 *lE4 = c->at<float4>(c->lay.adjE4);
+    const size_t lE_bytes = (size_t)c->ng * 16;
+
+    // terminal: lE = 2 h^3 w E of the final field, then (dD/dy)^T S^T
+    PIC_CUDA(launch_adj_zero(c->np, c->ctrl(), c->st));
+    const double seed[3] = {2.0 * c->dV * c->adj.w[0], 2.0 * c->dV * c->adj.w[1],
+                            2.0 * c->dV * c->adj.w[2]};
+    PIC_CUDA(launch_adj_seed(c->ng, c->at<float4>(c->lay.E4), lE4, seed, c->st));
+    if ((r = adj_solve(c))) return r;
+    PIC_CUDA(launch_adj_rho(c->np, c->geom, c->ctrl(), cs.cell, cyo, c->at<float>(c->lay.rho), qsc,
+                            c->st));
+
+    for (int s = c->adj.nseg - 1; s >= 0; --s) {
+        if ((r = adj_restore(c, L, s))) return r;
+        const int a0 = s * K, b0 = std::min(a0 + K, c->adj.n_steps - 1);
+        // recompute the segment, keeping each step's positions and field
+        for (int n = a0; n < b0; ++n) {
+            char *dst[4], *src[7];
+            buf_arrays(c->adj.buf + L.off_segy + (size_t)(n - a0) * L.segy, L.arr, 4, dst);
+            set_arrays(cs, src);
+            if ((r = copy_arrays(c, dst, src, 4))) return r;
+            if ((r = do_deposit(c)) || (r = do_solve(c))) return r;
+            PIC_CUDA(cudaMemcpyAsync(c->adj.buf + L.off_segE + (size_t)(n - a0) * L.segE,
+                                     c->at<char>(c->lay.E4), lE_bytes, cudaMemcpyDeviceToDevice,
+                                     c->st));
+            if ((r = do_gather_push(c, false))) return r;
+        }
+        // reverse steps
+        for (int n = b0 - 1; n >= a0; --n) {
+            char *y[4];
+            buf_arrays(c->adj.buf + L.off_segy + (size_t)(n - a0) * L.segy, L.arr, 4, y);
+            const int32_t *ycell = reinterpret_cast<const int32_t *>(y[0]);
+            const float *yo[3] = {reinterpret_cast<const float *>(y[1]),
+                                  reinterpret_cast<const float *>(y[2]),
+                                  reinterpret_cast<const float *>(y[3])};
+            const float4 *En = reinterpret_cast<const float4 *>(c->adj.buf + L.off_segE +
+                                                                (size_t)(n - a0) * L.segE);
+            PIC_CUDA(cudaMemsetAsync(lE4, 0, lE_bytes, c->st));
+            PIC_CUDA(launch_adj_push(c->geom, c->ctrl(), c->at<int4>(c->lay.items),
+                                     (int)c->max_items, ycell, yo, En, lE4, c_kick, dt, wz2,
+                                     c->ctrl(), c->st));
+            if ((r = adj_solve(c))) return r;
+            PIC_CUDA(launch_adj_rho(c->np, c->geom, c->ctrl(), ycell, yo, c->at<float>(c->lay.rho),
+                                    qsc, c->st));
+        }
+    }
+
+    // gradients in load order: dJ/dx0 = ly, dJ/dv0 = lv + dt/2 ly
+    int32_t *inv = c->at<int32_t>(c->lay.inv);
+    PIC_CUDA(launch_invperm(c->np, c->ctrl(), inv, c->st));
+    if (dst_is_device) {
+        PIC_CUDA(launch_adj_unload(0, c->np, inv, c->ctrl(), 0.5 * c->prm.dt, scale, gx, gv, c->st));
+    } else {
+        double *sx = c->at<double>(c->lay.stage_x), *sv = c->at<double>(c->lay.stage_v);
+        for (int64_t o = 0; o < c->np; o += c->staging) {
+            const int64_t m = std::min<int64_t>(c->staging, c->np - o);
+            PIC_CUDA(launch_adj_unload(o, m, inv, c->ctrl(), 0.5 * c->prm.dt, scale, sx, sv, c->st));
+            PIC_CUDA(cudaMemcpyAsync(gx + 3 * o, sx, (size_t)m * 24, cudaMemcpyDeviceToHost, c->st));
+            PIC_CUDA(cudaMemcpyAsync(gv + 3 * o, sv, (size_t)m * 24, cudaMemcpyDeviceToHost, c->st));
+        }
+    }
+    // back to the state the forward pass started from
+    if ((r = adj_restore(c, L, 0))) return r;
+    PIC_CUDA(cudaMemcpyAsync(&c->ctrl()->step, &c->adj.step0_dev, sizeof(long long),
+                             cudaMemcpyHostToDevice, c->st));
+    c->step = c->adj.step0;
+    c->since_sort = c->adj.since0;
+    c->adj.ready = false;
+    c->rho_current = false;
+    PIC_CUDA(cudaStreamSynchronize(c->st));
+    return PIC_OK;
+}
+
+int pic_dot_f64(pic_handle_t c, const double *x, const double *y, int64_t n, double *out) {
+    int r = check_ready(c);
+    if (r) return r;
+    if (!out || (n > 0 && (!x || !y)) || n < 0) return fail(PIC_ERR_ARG, "bad argument");
+    if (n == 0) {
+        *out = 0.0;
+        return PIC_OK;
+    }
+    PIC_CUDA(launch_dot(n, x, y, c->at<double>(c->lay.fpart), kDiagFieldBlocks * 4,
+                        &c->ctrl()->scalar[1], c->st));
+    PIC_CUDA(cudaMemcpyAsync(out, &c->ctrl()->scalar[1], sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    PIC_CUDA(cudaStreamSynchronize(c->st));
     return PIC_OK;
 }
 

@@ -36,6 +36,7 @@ struct Ctrl {
     long long step;         // steps since the last load
     long long diag_written; // diagnostic records written since the load
     double mode[2];         // tracked Fourier coefficient of the last solve
+    double scalar[2];       // objective and dot-product results
     int32_t cur;            // which ParticleSet holds the particles
     int32_t pad0;
     ParticleSet sets[2];
@@ -77,6 +78,7 @@ struct PushConst {
 // Diagnostic partial layout: 4 doubles per block.
 constexpr int kDiagFieldBlocks = 512;
 constexpr int kMaxPushBlocks = 152 * 8;
+constexpr int kMaxChunk = 4095;   // fixed-point tile slots stay below 2^32
 
 // Set the thread-local message returned by pic_last_error(); returns `code`.
 int record_error(int code, const char *fmt, ...);
@@ -92,16 +94,26 @@ cudaError_t launch_unload(int64_t o0, int64_t m, const int32_t *inv, const Geom 
                           const double *h_d, const double *L_d, double dt, const Ctrl *ctrl,
                           double *x, double *v, cudaStream_t st);
 
+cudaError_t exclusive_scan(int32_t *data, int64_t n, int32_t *tmp, cudaStream_t st);
+cudaError_t sort_prepare();   // kernel attributes; call once per device outside capture
+cudaError_t launch_worklist(const int32_t *bin_end, int ntiles, int chunk, int32_t *tile_items,
+                            int2 *tile_range, int4 *items, int32_t *scan_tmp, Ctrl *ctrl, int flip,
+                            cudaStream_t st);
 cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t *bins,
                         int64_t nbins, int32_t *scan_tmp, int32_t *tile_items,
                         int2 *tile_range, int4 *items, cudaStream_t st);
 
 cudaError_t launch_deposit(int64_t n, const Geom &g, const Ctrl *ctrl, const int4 *items,
-                           int max_items, float qscale, float *rho, Ctrl *ctrl_w,
-                           int grid_blocks, int sparse_below, cudaStream_t st);
-cudaError_t launch_deposit_direct(int64_t n, const Geom &g, const Ctrl *ctrl, float qscale,
-                                  float *rho, cudaStream_t st);
+                           int max_items, double qscale, float *rho, unsigned long long *rho64,
+                           bool fixed, Ctrl *ctrl_w, int grid_blocks, int sparse_below,
+                           cudaStream_t st);
 
+cudaError_t launch_rho_finish(const Geom &g, unsigned long long *rho64, float *rho, double qscale,
+                              cudaStream_t st);
+cudaError_t launch_push_deposit(const Geom &g, const PushConst &pc, bool diag, bool fixed,
+                                Ctrl *ctrl, const int4 *items, int max_items, const float4 *E4,
+                                float *rho, unsigned long long *rho64, double qscale,
+                                int sparse_below, double *part, int blocks, cudaStream_t st);
 cudaError_t launch_gather_push(int64_t n, const Geom &g, const PushConst &pc, bool diag,
                                Ctrl *ctrl, const float4 *E4, double *part, int blocks,
                                int threads, cudaStream_t st);
@@ -114,5 +126,26 @@ cudaError_t launch_diag_field(const Geom &g, const float *rho, const float4 *E4,
 cudaError_t launch_diag_finalize(const double *field_part, const double *push_part,
                                  int push_blocks, double dV, double mp, double dt,
                                  Ctrl *ctrl, pic_diag_t *ring, int ring_cap, cudaStream_t st);
+
+// adjoint (k_adjoint.cu)
+cudaError_t launch_adj_seed(int64_t ng, const float4 *E4, float4 *lE4, const double *scale3,
+                            cudaStream_t st);
+cudaError_t launch_adj_push(const Geom &g, const Ctrl *ctrl, const int4 *items, int max_items,
+                            const int32_t *ycell, const float *const yo[3], const float4 *E4,
+                            float4 *lE4, float c_kick, float dt, float wz2, Ctrl *ctrl_w,
+                            cudaStream_t st);
+cudaError_t launch_green_adj(const Geom &g, const double *L_d, const float2 *lE_hat,
+                             float2 *lrho_hat, int64_t nhalf, cudaStream_t st);
+cudaError_t launch_adj_rho(int64_t n, const Geom &g, const Ctrl *ctrl, const int32_t *ycell,
+                           const float *const yo[3], const float *lrho, float qscale,
+                           cudaStream_t st);
+cudaError_t launch_adj_zero(int64_t n, const Ctrl *ctrl, cudaStream_t st);
+cudaError_t launch_adj_unload(int64_t o0, int64_t m, const int32_t *inv, const Ctrl *ctrl,
+                              double half_dt, double scale, double *gx, double *gv,
+                              cudaStream_t st);
+cudaError_t launch_objective(const double *fpart, int nb, double dV, const double *w,
+                             double *out, cudaStream_t st);
+cudaError_t launch_dot(int64_t n, const double *a, const double *b, double *part, int max_part,
+                       double *out, cudaStream_t st);
 
 }  // namespace pic

@@ -1,0 +1,102 @@
+// The per-particle gather + Boris push + drift of Section 3.1 steps 3-4
+// (Eq. momentum_eqn) and Section 3.2 of arXiv 2205.11052, shared by the
+// single-run and the batched kernels.
+//
+// E is interpolated to the particle with the CIC weights of the deposit, the
+// velocity is advanced by the Boris rotation (exact solution of
+// v1 = v0 + dt (q/m) [e + (v0 + v1)/2 x B]) and the position drifts by a full
+// step in cell units, carried into the cell index and wrapped periodically.
+#pragma once
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+template <bool EXT, bool MAG>
+__device__ __forceinline__ void push_one(const Geom &g, const PushConst &pc,
+                                         const float4 *__restrict__ E4, int32_t &c, float &fx,
+                                         float &fy, float &fz, float &vx, float &vy, float &vz,
+                                         int &bad) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    int i = cell_i(c), j = cell_j(c), k = cell_k(c);
+    if (i >= nx || j >= ny || k >= nz) {   // never produced by the kernels
+        bad |= PIC_FLAG_BAD_CELL;
+        i = j = k = 0;
+    }
+    // CIC stencil nodes (periodic)
+    const int i1 = (i + 1 == nx) ? 0 : i + 1;
+    const int j1 = (j + 1 == ny) ? 0 : j + 1;
+    const int k1 = (k + 1 == nz) ? 0 : k + 1;
+    const int nxy = nx * ny;
+    const int r00 = j * nx + k * nxy, r10 = j1 * nx + k * nxy;
+    const int r01 = j * nx + k1 * nxy, r11 = j1 * nx + k1 * nxy;
+    const float4 e000 = __ldg(E4 + r00 + i), e100 = __ldg(E4 + r00 + i1);
+    const float4 e010 = __ldg(E4 + r10 + i), e110 = __ldg(E4 + r10 + i1);
+    const float4 e001 = __ldg(E4 + r01 + i), e101 = __ldg(E4 + r01 + i1);
+    const float4 e011 = __ldg(E4 + r11 + i), e111 = __ldg(E4 + r11 + i1);
+    const float wx1 = fx, wx0 = 1.0f - fx;
+    const float wy1 = fy, wy0 = 1.0f - fy;
+    const float wz1 = fz, wz0 = 1.0f - fz;
+    const float w00 = wy0 * wz0, w10 = wy1 * wz0, w01 = wy0 * wz1, w11 = wy1 * wz1;
+    float ex = w00 * (wx0 * e000.x + wx1 * e100.x) + w10 * (wx0 * e010.x + wx1 * e110.x) +
+               w01 * (wx0 * e001.x + wx1 * e101.x) + w11 * (wx0 * e011.x + wx1 * e111.x);
+    float ey = w00 * (wx0 * e000.y + wx1 * e100.y) + w10 * (wx0 * e010.y + wx1 * e110.y) +
+               w01 * (wx0 * e001.y + wx1 * e101.y) + w11 * (wx0 * e011.y + wx1 * e111.y);
+    float ez = w00 * (wx0 * e000.z + wx1 * e100.z) + w10 * (wx0 * e010.z + wx1 * e110.z) +
+               w01 * (wx0 * e001.z + wx1 * e101.z) + w11 * (wx0 * e011.z + wx1 * e111.z);
+    if (EXT) {
+        // quadrupole about the box centre at x in [0, L): (x - c)/h = i - N/2 +
+        // 1/2 + f, wrapped into [-N/2, N/2) (a particle in [0, h/2) has its
+        // stencil base on node N-1, i.e. i + 1/2 + f lies in [N, N + 1/2))
+        float ux = (float)i - pc.half_n[0] + 0.5f + fx;
+        float uy = (float)j - pc.half_n[1] + 0.5f + fy;
+        float uz = (float)k - pc.half_n[2] + 0.5f + fz;
+        if (ux >= pc.half_n[0]) ux -= (float)nx;
+        if (uy >= pc.half_n[1]) uy -= (float)ny;
+        if (uz >= pc.half_n[2]) uz -= (float)nz;
+        ex += -0.5f * pc.wz2 * (ux * g.h[0]);
+        ey += -0.5f * pc.wz2 * (uy * g.h[1]);
+        ez += pc.wz2 * (uz * g.h[2]);
+    }
+    // Boris: half kick, rotation, half kick
+    float mx = vx + pc.qm_half_dt * ex;
+    float my = vy + pc.qm_half_dt * ey;
+    float mz = vz + pc.qm_half_dt * ez;
+    if (MAG) {
+        const float px = mx + (my * pc.t[2] - mz * pc.t[1]);
+        const float py = my + (mz * pc.t[0] - mx * pc.t[2]);
+        const float pz = mz + (mx * pc.t[1] - my * pc.t[0]);
+        mx += py * pc.s[2] - pz * pc.s[1];
+        my += pz * pc.s[0] - px * pc.s[2];
+        mz += px * pc.s[1] - py * pc.s[0];
+    }
+    vx = mx + pc.qm_half_dt * ex;
+    vy = my + pc.qm_half_dt * ey;
+    vz = mz + pc.qm_half_dt * ez;
+
+    // drift a full step in cell units, carry into the cell index, wrap
+    const float sx = fx + pc.dt_over_h[0] * vx;
+    const float sy = fy + pc.dt_over_h[1] * vy;
+    const float sz = fz + pc.dt_over_h[2] * vz;
+    float flx = floorf(sx), fly = floorf(sy), flz = floorf(sz);
+    fx = sx - flx;
+    fy = sy - fly;
+    fz = sz - flz;
+    if (fx >= 1.0f) { fx = 0.0f; flx += 1.0f; }
+    if (fy >= 1.0f) { fy = 0.0f; fly += 1.0f; }
+    if (fz >= 1.0f) { fz = 0.0f; flz += 1.0f; }
+    if (!(fabsf(flx) < 1.0e6f && fabsf(fly) < 1.0e6f && fabsf(flz) < 1.0e6f)) {
+        bad |= PIC_FLAG_NONFINITE;
+        flx = fly = flz = 0.0f;
+        fx = fy = fz = 0.0f;
+    }
+    i += (int)flx;
+    j += (int)fly;
+    k += (int)flz;
+    if ((unsigned)i >= (unsigned)nx) { i %= nx; if (i < 0) i += nx; }
+    if ((unsigned)j >= (unsigned)ny) { j %= ny; if (j < 0) j += ny; }
+    if ((unsigned)k >= (unsigned)nz) { k %= nz; if (k < 0) k += nz; }
+    c = pack_cell(i, j, k);
+}
+
+}  // namespace pic

@@ -28,12 +28,12 @@ def _d3(v):
 
 def make_structs(n, L, n_particles, dt, q_over_m=-1.0, Q=-1.0, B=(0.0, 0.0, 0.0), wz2=0.0,
                  tile=(0, 0, 0), guard=0, sort_period=0, diag_every=0, diag_capacity=0,
-                 mode=(1, 0, 0), mode_comp=0, block=0, chunk=0):
+                 mode=(1, 0, 0), mode_comp=0, block=0, chunk=0, options=0):
     grid = capi.pic_grid_t(_i3(n), _d3(L))
     species = capi.pic_species_t(float(q_over_m), float(Q), int(n_particles))
     params = capi.pic_params_t(float(dt), _d3(B), float(wz2), _i3(tile), int(guard),
                                int(sort_period), int(diag_every), int(diag_capacity),
-                               _i3(mode), int(mode_comp), int(block), int(chunk))
+                               _i3(mode), int(mode_comp), int(block), int(chunk), int(options))
     return grid, species, params
 
 
@@ -42,7 +42,7 @@ class Simulation:
 
     def __init__(self, n, L, n_particles, dt, q_over_m=-1.0, Q=-1.0, B=(0.0, 0.0, 0.0),
                  wz2=0.0, tile=(0, 0, 0), guard=0, sort_period=0, diag_every=0,
-                 diag_capacity=0, mode=(1, 0, 0), mode_comp=0, block=0, chunk=0,
+                 diag_capacity=0, mode=(1, 0, 0), mode_comp=0, block=0, chunk=0, options=0,
                  device=None, stream=None):
         import torch
 
@@ -52,7 +52,7 @@ class Simulation:
         self.dt = float(dt)
         grid, species, params = make_structs(self.n, self.L, n_particles, dt, q_over_m, Q, B, wz2,
                                              tile, guard, sort_period, diag_every, diag_capacity,
-                                             mode, mode_comp, block, chunk)
+                                             mode, mode_comp, block, chunk, options)
         self.handle = capi.pic_create(grid, species, params)
         self._closed = False
         self.sizes = capi.pic_buffer_sizes(self.handle)
@@ -148,6 +148,41 @@ class Simulation:
                             mode=complex(r.mode_re, r.mode_im), t=r.t, Px=r.Px, Py=r.Py,
                             Pz=r.Pz, K=r.K))
         return out
+
+    # ------------------------------------------------------------------ adjoint
+    def adjoint_forward(self, n_steps: int, weights=(1.0, 1.0, 1.0), checkpoint_every: int = 20):
+        """J = sum_d w_d h^3 sum_g E_d^2 of the field of the last of n_steps steps
+        from the loaded state; keeps checkpoints for adjoint_backward."""
+        import torch
+
+        nbytes = capi.pic_adjoint_buffer_bytes(self.handle, int(n_steps), int(checkpoint_every))
+        if getattr(self, "_adj_buf", None) is None or self._adj_buf.numel() < nbytes:
+            self._adj_buf = None
+            self._adj_buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        return capi.pic_adjoint_forward(self.handle, int(n_steps), int(checkpoint_every),
+                                        weights, self._adj_buf.data_ptr(), int(self._adj_buf.numel()))
+
+    def adjoint_backward(self, scale: float = 1.0, device: bool = False):
+        """(scale dJ/dx0, scale dJ/dv0) as (N, 3) float64 arrays in load order."""
+        import torch
+
+        N = self.n_particles
+        if device:
+            gx = torch.empty((N, 3), dtype=torch.float64, device=self.device)
+            gv = torch.empty((N, 3), dtype=torch.float64, device=self.device)
+            capi.pic_adjoint_backward(self.handle, float(scale), gx.data_ptr(), gv.data_ptr(), True)
+            return gx, gv
+        gx = np.empty((N, 3), dtype=np.float64)
+        gv = np.empty((N, 3), dtype=np.float64)
+        capi.pic_adjoint_backward(self.handle, float(scale), gx.ctypes.data, gv.ctypes.data, False)
+        return gx, gv
+
+    def dot(self, a, b) -> float:
+        """FP64 sum of a * b over two CUDA float64 tensors of equal size."""
+        a = a.contiguous()
+        b = b.contiguous()
+        assert a.numel() == b.numel() and a.is_cuda and b.is_cuda
+        return capi.pic_dot_f64(self.handle, a.data_ptr(), b.data_ptr(), a.numel())
 
     def flags(self, clear: bool = False) -> int:
         return capi.pic_device_flags(self.handle, clear)

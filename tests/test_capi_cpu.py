@@ -57,7 +57,8 @@ def test_create_and_sizes_without_gpu(lib):
     dict(L=(1.0, float("nan"), 1.0)), dict(dt=0.0), dict(dt=float("inf")),
     dict(n_particles=-1), dict(n_particles=2 ** 31), dict(q_over_m=0.0),
     dict(mode=(9, 0, 0)), dict(mode_comp=3), dict(block=48), dict(block=512),
-    dict(chunk=8), dict(guard=-1), dict(B=(0.0, float("nan"), 0.0)),
+    dict(chunk=8), dict(chunk=4096), dict(guard=-1), dict(B=(0.0, float("nan"), 0.0)),
+    dict(options=4),
 ])
 def test_create_rejects_bad_configs(lib, kw):
     with pytest.raises(capi.PicError) as e:
@@ -96,3 +97,22 @@ def test_library_missing_fails_loudly(tmp_path):
             capi.load_library(str(tmp_path / "nope.so"))
         finally:
             capi._lib = capi._lib_saved
+
+
+def test_batch_create_validates_and_sizes_without_gpu(lib):
+    from paper_2205_11052_gb300.sim import _d3, _i3
+
+    _, _, params = make_structs((2, 1, 1), (1.0, 1.0, 1.0), 0, 0.1)
+    good = [capi.pic_instance_t(_i3((16, 16, 16)), _d3((1.0, 1.0, 1.0)), 100, -1.0),
+            capi.pic_instance_t(_i3((24, 8, 12)), _d3((2.0, 1.0, 1.5)), 50, -2.0)]
+    b = capi.pic_batch_create(good, -1.0, params)
+    s = capi.pic_batch_buffer_sizes(b)
+    assert s.grid_nodes == 16 ** 3 + 24 * 8 * 12
+    assert s.particle_capacity == 150
+    capi.pic_batch_destroy(b)
+    bad = [capi.pic_instance_t(_i3((16, 0, 16)), _d3((1.0, 1.0, 1.0)), 100, -1.0)]
+    with pytest.raises(capi.PicError) as e:
+        capi.pic_batch_create(bad, -1.0, params)
+    assert e.value.code == capi.PIC_ERR_ARG
+    with pytest.raises(capi.PicError):
+        capi.pic_batch_create(good, 0.0, params)

@@ -1,0 +1,162 @@
+"""GPU adjoint vs the FP64 oracle: J, dJ/dx0, dJ/dv0, dJ/dalpha (needs a GPU).
+
+Tolerances: the GPU runs FP32 particles and grids, so gradients are compared
+at 1e-4 of their largest component against the oracle's discrete adjoint and
+against central differences of the oracle's objective (the spec bar
+for gradient accuracy); J itself to 1e-5.
+"""
+import numpy as np
+import pytest
+
+import pic_inputs as pi
+from oracle import pic_oracle as po
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU-only machines
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2205_11052_gb300 import capi  # noqa: E402
+from paper_2205_11052_gb300.autograd import final_field_energy  # noqa: E402
+from paper_2205_11052_gb300.build import build  # noqa: E402
+from paper_2205_11052_gb300.sim import Simulation  # noqa: E402
+
+build()
+
+FIXED = capi.PIC_OPT_FIXED_DEPOSIT
+
+
+def _small(alpha=0.2, seed=5):
+    w = pi.bump_on_tail(n=8, ppc=4, seed=seed, alpha=alpha, k=0.5)   # L = 4 pi, 2048 particles
+    w.dt = 0.1
+    return w
+
+
+def _oracle(w, n_steps, weights, wz2=0.0):
+    g = po.Grid(w.n, w.L)
+    p = po.Params(dt=w.dt, Q=w.Q, q_over_m=w.q_over_m, wz2=wz2)
+    return po.run_with_gradient(w.x, w.v, g, p, n_steps, weights)
+
+
+@pytest.mark.parametrize("options", [0, FIXED], ids=["fp32", "fixed"])
+@pytest.mark.parametrize("wz2,weights", [(0.0, (0.0, 0.0, 1.0)), (0.3, (1.0, 1.0, 1.0))])
+def test_gradient_matches_oracle_adjoint(options, wz2, weights):
+    w = _small()
+    n_steps = 6
+    sim = Simulation.from_workload(w, wz2=wz2, options=options)
+    J = sim.adjoint_forward(n_steps, weights, checkpoint_every=4)
+    gx, gv = sim.adjoint_backward()
+    Jo, gxo, gvo = _oracle(w, n_steps, weights, wz2)
+    assert J == pytest.approx(Jo, rel=1e-5)
+    assert np.max(np.abs(gx - gxo)) <= 1e-4 * np.max(np.abs(gxo))
+    assert np.max(np.abs(gv - gvo)) <= 1e-4 * np.max(np.abs(gvo))
+    # the call left the loaded state in place
+    x, v = sim.particles()
+    L = np.asarray(w.L)
+    d = x - w.x
+    d -= L * np.round(d / L)
+    assert np.max(np.abs(d)) < 1e-5 and np.max(np.abs(v - w.v)) < 1e-6
+    assert sim.counts()[1] == 0
+    sim.close()
+
+
+def test_gradient_matches_central_differences_of_the_oracle():
+    w = _small()
+    n_steps, weights = 6, (0.0, 0.0, 1.0)
+    sim = Simulation.from_workload(w, options=FIXED)
+    sim.adjoint_forward(n_steps, weights, checkpoint_every=2)
+    gx, gv = sim.adjoint_backward()
+    g = po.Grid(w.n, w.L)
+    p = po.Params(dt=w.dt, Q=w.Q)
+    rng = np.random.default_rng(3)
+    dX, dV = rng.standard_normal(w.x.shape), rng.standard_normal(w.v.shape)
+    eps = 1e-5
+    Jp = po.run_with_gradient(w.x + eps * dX, w.v + eps * dV, g, p, n_steps, weights)[0]
+    Jm = po.run_with_gradient(w.x - eps * dX, w.v - eps * dV, g, p, n_steps, weights)[0]
+    fd = (Jp - Jm) / (2 * eps)
+    ad = float(np.sum(gx * dX) + np.sum(gv * dV))
+    assert abs(ad - fd) <= 1e-4 * abs(fd)
+    sim.close()
+
+
+def test_amplitude_gradient_against_oracle_differences():
+    """dJ/dalpha = <dJ/dx0, dx0/dalpha> (FP64 dot on the GPU) vs the central
+    difference of the oracle's J over re-sampled particles (fixed uniforms)."""
+    alpha, k, eps = 0.2, 0.5, 1e-6
+    w = _small(alpha)
+    n_steps, weights = 6, (0.0, 0.0, 1.0)
+    sim = Simulation.from_workload(w, options=FIXED)
+    sim.adjoint_forward(n_steps, weights, checkpoint_every=3)
+    gx, _ = sim.adjoint_backward(device=True)
+    dxa = np.zeros_like(w.x)
+    dxa[:, 2] = po.cosine_sample_dalpha(w.x[:, 2], alpha, k)
+    ad = sim.dot(gx, torch.from_numpy(dxa).cuda())
+    wp, wm = _small(alpha + eps), _small(alpha - eps)
+    fd = (_oracle(wp, n_steps, weights)[0] - _oracle(wm, n_steps, weights)[0]) / (2 * eps)
+    assert ad == pytest.approx(fd, rel=1e-4)
+    sim.close()
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    """With the deterministic deposit the forward pass (and so J) is the same
+    bits for every checkpoint interval; the gradients agree to FP32 rounding
+    (the adjoint's own field deposit sums in FP32 in arbitrary order)."""
+    w = pi.bump_on_tail(n=16, ppc=4, seed=8, alpha=0.1, k=0.25)
+    out = []
+    for K in (1, 3, 16):
+        sim = Simulation.from_workload(w, options=FIXED)
+        J = sim.adjoint_forward(16, (0.0, 0.0, 1.0), checkpoint_every=K)
+        gx, gv = sim.adjoint_backward()
+        out.append((J, gx, gv))
+        sim.close()
+    for J, gx, gv in out[1:]:
+        assert J == out[0][0]
+        assert np.max(np.abs(gx - out[0][1])) <= 1e-5 * np.max(np.abs(out[0][1]))
+        assert np.max(np.abs(gv - out[0][2])) <= 1e-5 * np.max(np.abs(out[0][2]))
+
+
+def test_longer_run_against_oracle_adjoint():
+    """40 steps of a 16^3 bump-on-tail (16,384 particles), 5 segments."""
+    w = pi.bump_on_tail(n=16, ppc=4, seed=8, alpha=0.1, k=0.25)
+    n_steps, weights = 40, (0.0, 0.0, 1.0)
+    sim = Simulation.from_workload(w, options=FIXED)
+    J = sim.adjoint_forward(n_steps, weights, checkpoint_every=8)
+    gx, gv = sim.adjoint_backward()
+    Jo, gxo, gvo = _oracle(w, n_steps, weights)
+    assert J == pytest.approx(Jo, rel=1e-4)
+    assert np.max(np.abs(gx - gxo)) <= 1e-3 * np.max(np.abs(gxo))
+    assert np.max(np.abs(gv - gvo)) <= 1e-3 * np.max(np.abs(gvo))
+    sim.close()
+
+
+def test_autograd_function_returns_the_library_gradients():
+    w = _small()
+    sim = Simulation.from_workload(w, options=FIXED)
+    x0 = torch.from_numpy(w.x).cuda().requires_grad_(True)
+    v0 = torch.from_numpy(w.v).cuda().requires_grad_(True)
+    J = final_field_energy(x0, v0, sim, 6, (0.0, 0.0, 1.0), 2)
+    (2.0 * J).backward()
+    Jo, gxo, gvo = _oracle(w, 6, (0.0, 0.0, 1.0))
+    assert float(J.detach()) == pytest.approx(Jo, rel=1e-5)
+    assert np.max(np.abs(x0.grad.cpu().numpy() - 2 * gxo)) <= 2e-4 * np.max(np.abs(gxo))
+    assert np.max(np.abs(v0.grad.cpu().numpy() - 2 * gvo)) <= 2e-4 * np.max(np.abs(gvo))
+    sim.close()
+
+
+def test_adjoint_rejects_magnetic_fields_and_small_buffers():
+    w = _small()
+    sim = Simulation.from_workload(w, B=(0.0, 0.0, 1.0))
+    with pytest.raises(capi.PicError) as e:
+        sim.adjoint_forward(4)
+    assert e.value.code == capi.PIC_ERR_ARG
+    sim.close()
+    sim = Simulation.from_workload(w)
+    buf = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(capi.PicError) as e:
+        capi.pic_adjoint_forward(sim.handle, 4, 2, (1.0, 1.0, 1.0), buf.data_ptr(), 1024)
+    assert e.value.code == capi.PIC_ERR_CAPACITY
+    with pytest.raises(capi.PicError) as e:
+        sim.adjoint_backward()
+    assert e.value.code == capi.PIC_ERR_STATE
+    sim.close()

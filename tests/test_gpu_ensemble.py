@@ -1,0 +1,103 @@
+"""Batched ensembles vs independent oracle runs of every instance (GPU).
+
+Instances differ in grid (including non-cubic and tile-ragged ones),
+particle count, perturbation and charge; each must follow its own oracle
+trajectory to the tolerances of the single-run parity tests.
+"""
+import numpy as np
+import pytest
+
+import pic_inputs as pi
+from oracle import pic_oracle as po
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU-only machines
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2205_11052_gb300 import capi  # noqa: E402
+from paper_2205_11052_gb300.batch import Ensemble  # noqa: E402
+from paper_2205_11052_gb300.build import build  # noqa: E402
+from paper_2205_11052_gb300.sim import Simulation  # noqa: E402
+
+build()
+
+
+def _members():
+    ws = [pi.landau(n=8, ppc=4, seed=41, alpha=0.1),
+          pi.landau(n=12, ppc=3, seed=42, alpha=0.05),
+          pi.landau(n=16, ppc=2, seed=43, alpha=0.08),
+          pi.landau(n=16, ppc=5, seed=44, alpha=0.02),
+          pi.uniform_plasma(n=(10, 8, 6), ppc=3, L=(2.0, 1.5, 1.0), seed=45)]
+    return ws
+
+
+def _pos_err(x, xo, w):
+    L = np.asarray(w.L)
+    d = x - xo
+    d -= L * np.round(d / L)
+    return np.max(np.abs(d) / (L / np.asarray(w.n)))
+
+
+@pytest.mark.parametrize("options", [0, capi.PIC_OPT_FIXED_DEPOSIT], ids=["fp32", "fixed"])
+def test_every_instance_follows_its_oracle(options):
+    ws = _members()
+    ens = Ensemble([(w.n, w.L, w.x, w.v, w.Q) for w in ws], dt=0.05, diag_every=1,
+                   sort_period=2, options=options)
+    ens.step(6)
+    xs, vs = ens.particles()
+    hist = ens.diagnostics()
+    assert len(hist) == 6
+    for i, w in enumerate(ws):
+        g = po.Grid(w.n, w.L)
+        p = po.Params(dt=0.05, Q=w.Q, q_over_m=w.q_over_m)
+        xo, vo, ho = po.run(w.x, w.v, g, p, 6)
+        assert _pos_err(xs[i], xo, w) <= 1e-4, i
+        assert np.max(np.abs(vs[i] - vo)) <= 1e-4 * np.max(np.abs(vo)), i
+        for r, ro in zip(hist, ho):
+            assert r[i]["step"] == ro["step"]
+            assert r[i]["Wx"] == pytest.approx(ro["Wx"], rel=1e-4)
+            assert r[i]["K"] == pytest.approx(ro["K"], rel=1e-4)
+            assert r[i]["Q"] == pytest.approx(ro["Q"], rel=1e-6)
+    ens.close()
+
+
+def test_ensemble_equals_single_runs_of_its_members():
+    ws = _members()[:3]
+    ens = Ensemble([(w.n, w.L, w.x, w.v, w.Q) for w in ws], dt=0.05, sort_period=1,
+                   options=capi.PIC_OPT_FIXED_DEPOSIT)
+    ens.step(4)
+    xs, vs = ens.particles()
+    for i, w in enumerate(ws):
+        sim = Simulation.from_workload(w, sort_period=1, options=capi.PIC_OPT_FIXED_DEPOSIT)
+        sim.step(4)
+        x, v = sim.particles()
+        assert _pos_err(xs[i], x, w) <= 1e-5
+        assert np.max(np.abs(vs[i] - v)) <= 1e-5 * np.max(np.abs(v))
+        sim.close()
+    ens.close()
+
+
+def test_ensemble_step_replays_from_a_cuda_graph():
+    ws = _members()
+    ens = Ensemble([(w.n, w.L, w.x, w.v, w.Q) for w in ws], dt=0.05, sort_period=2,
+                   options=capi.PIC_OPT_FIXED_DEPOSIT)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    ens.set_stream(s)
+    with torch.cuda.stream(s):
+        ens.step(2)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ens.step(2)
+    for _ in range(2):
+        g.replay()
+    s.synchronize()
+    xs, vs = ens.particles()
+    for i, w in enumerate(ws):
+        xo, vo, _ = po.run(w.x, w.v, po.Grid(w.n, w.L), po.Params(dt=0.05, Q=w.Q), 6)
+        assert _pos_err(xs[i], xo, w) <= 1e-4
+        assert np.max(np.abs(vs[i] - vo)) <= 1e-4 * np.max(np.abs(vo))
+    ens.close()

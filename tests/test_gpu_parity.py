@@ -101,9 +101,10 @@ def _oracle_half_step_positions(w):
     return po.wrap(w.x + 0.5 * w.dt * w.v, _grid(w))
 
 
-def test_deposit_matches_oracle(workload):
+@pytest.mark.parametrize("options", [0, 1], ids=["fp32", "fixed"])
+def test_deposit_matches_oracle(workload, options):
     w = workload
-    sim = Simulation.from_workload(w)
+    sim = Simulation.from_workload(w, options=options)
     sim.deposit()
     rho, _ = sim.field()
     qp = w.Q / w.n_particles
@@ -116,11 +117,12 @@ def test_deposit_matches_oracle(workload):
     sim.close()
 
 
-@pytest.mark.parametrize("tile,guard,chunk", [((4, 4, 4), 1, 64), ((8, 8, 8), 2, 4096),
+@pytest.mark.parametrize("options", [0, 1], ids=["fp32", "fixed"])
+@pytest.mark.parametrize("tile,guard,chunk", [((4, 4, 4), 1, 64), ((8, 8, 8), 2, 4095),
                                               ((16, 8, 4), 3, 1000), ((5, 3, 7), 1, 33)])
-def test_deposit_is_independent_of_tiling(tile, guard, chunk):
+def test_deposit_is_independent_of_tiling(tile, guard, chunk, options):
     w = pi.landau(n=(20, 12, 14), ppc=6, seed=3, alpha=0.3)
-    sim = Simulation.from_workload(w, tile=tile, guard=guard, chunk=chunk)
+    sim = Simulation.from_workload(w, tile=tile, guard=guard, chunk=chunk, options=options)
     sim.deposit()
     rho, _ = sim.field()
     rho_o = po.deposit(_oracle_half_step_positions(w), _grid(w), w.Q / w.n_particles)
@@ -128,11 +130,12 @@ def test_deposit_is_independent_of_tiling(tile, guard, chunk):
     sim.close()
 
 
-def test_deposit_of_strays_after_many_steps_without_rebinning():
+@pytest.mark.parametrize("options", [0, 1], ids=["fp32", "fixed"])
+def test_deposit_of_strays_after_many_steps_without_rebinning(options):
     """Particles far outside their tile since the last sort still deposit exactly."""
     w = pi.landau(n=16, ppc=8, seed=4)
     w.v *= 6.0              # ~3 cells per step
-    sim = Simulation.from_workload(w, sort_period=-1, guard=1)
+    sim = Simulation.from_workload(w, sort_period=-1, guard=1, options=options)
     xo, vo = w.x.copy(), w.v.copy()
     g, p = _grid(w), _params(w)
     for _ in range(5):
@@ -142,6 +145,23 @@ def test_deposit_of_strays_after_many_steps_without_rebinning():
     rho, _ = sim.field()
     rho_o = po.deposit(po.wrap(xo + 0.5 * w.dt * vo, g), g, w.Q / w.n_particles)
     assert np.max(np.abs(rho - rho_o)) <= 1e-4 * np.max(np.abs(rho_o))
+    sim.close()
+
+
+def test_fixed_point_deposit_is_deterministic_and_conserves_charge():
+    """Integer tile sums do not depend on the order of the atomics: two
+    deposits of the same particles (re-binned in between, which changes the
+    order within tiles) give bit-identical rho."""
+    w = _penning_small()
+    sim = Simulation.from_workload(w, options=capi.PIC_OPT_FIXED_DEPOSIT)
+    sim.deposit()
+    rho1, _ = sim.field()
+    sim.sort()
+    sim.deposit()
+    rho2, _ = sim.field()
+    assert np.array_equal(rho1, rho2)
+    g = _grid(w)
+    assert abs(float(np.sum(rho1.astype(np.float64))) * g.cell_volume - w.Q) <= 1e-6 * abs(w.Q)
     sim.close()
 
 
@@ -206,11 +226,26 @@ def test_separate_calls_equal_one_step():
     sim.close()
 
 
-@pytest.mark.parametrize("sort_period", [1, 3, -1])
-def test_twenty_steps_and_diagnostics_match_oracle(sort_period):
+def test_step_after_split_calls_redeposits_the_stale_density():
+    """pic_gather_push leaves rho stale; the next pic_step deposits first."""
+    w = pi.landau(n=16, ppc=8, seed=12)
+    sim = Simulation.from_workload(w)
+    sim.deposit()
+    sim.field_solve()
+    sim.gather_push()
+    sim.step(2)
+    x, v = sim.particles()
+    xo, vo, _ = po.run(w.x, w.v, _grid(w), _params(w), 3)
+    assert _pos_err_in_cells(x, xo, w) <= 1e-4
+    assert np.max(np.abs(v - vo)) <= 1e-4 * np.max(np.abs(vo))
+    sim.close()
+
+
+@pytest.mark.parametrize("sort_period,options", [(1, 0), (3, 0), (-1, 0), (2, 1), (4, 1)])
+def test_twenty_steps_and_diagnostics_match_oracle(sort_period, options):
     """Landau damping, 16^3 grid, 8 particles per cell, dt = 0.05, 20 steps."""
     w = pi.landau(n=16, ppc=8, seed=1000, n_steps=20)
-    sim = Simulation.from_workload(w, diag_every=1, sort_period=sort_period)
+    sim = Simulation.from_workload(w, diag_every=1, sort_period=sort_period, options=options)
     sim.step(w.n_steps)
     x, v = sim.particles()
     hist = sim.diagnostics()
@@ -232,8 +267,28 @@ def test_twenty_steps_and_diagnostics_match_oracle(sort_period):
     sim.close()
 
 
-def test_penning_boris_steps_match_oracle():
+@pytest.mark.parametrize("options", [0, 1], ids=["fp32", "fixed"])
+def test_penning_boris_steps_match_oracle(options):
     w = _penning_small()
+    sim = Simulation.from_workload(w, options=options)
+    sim.step(5)
+    x, v = sim.particles()
+    xo, vo, _ = po.run(w.x, w.v, _grid(w), _params(w), 5)
+    assert _pos_err_in_cells(x, xo, w) <= 1e-4
+    assert np.max(np.abs(v - vo)) <= 1e-4 * np.max(np.abs(vo))
+    sim.close()
+
+
+@pytest.mark.parametrize("B", [(0.0, 0.0, 0.0), (0.0, 0.0, 2.0)])
+def test_quadrupole_across_the_periodic_seam(B):
+    """Particles everywhere in the box, including the half cells next to the
+    seam where the quadrupole field jumps by wz2 L: the push must take the
+    position in [0, L) (the oracle's) and not the stencil base's image."""
+    w = pi.bump_on_tail(n=8, ppc=4, seed=5, alpha=0.2, k=0.5)
+    w.dt, w.wz2, w.B = 0.1, 0.3, B
+    h = np.asarray(w.L) / np.asarray(w.n)
+    w.x[:8] = 0.25 * h           # inside [0, h/2) on every axis
+    w.v[:8] = 0.0
     sim = Simulation.from_workload(w)
     sim.step(5)
     x, v = sim.particles()
@@ -289,8 +344,9 @@ def test_reduced_axes_one_dimensional_grid():
     hist = sim.diagnostics()
     _, _, ho = po.run(w.x, w.v, _grid(w), _params(w), w.n_steps)
     for a, b in zip(hist, ho):
+        # the field decays: compare against its initial scale
         assert abs(a["mode"] - b["mode"]) <= 1e-4 * abs(ho[0]["mode"])
-        assert a["Wx"] == pytest.approx(b["Wx"], rel=1e-4)
+        assert abs(a["Wx"] - b["Wx"]) <= 1e-4 * ho[0]["Wx"]
     sim.close()
 
 

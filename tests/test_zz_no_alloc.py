@@ -3,9 +3,9 @@
 It serves callers that may not allocate device memory while running (a host
 application that owns a fixed memory budget, or a time-critical loop where
 cudaMalloc is forbidden): its scratch lives in a static device array of the
-library.  Here it is called twice in a row through the C ABI on the field of
-a real step, and each result must match the FP64 field energies and charge
-that pic_step's own diagnostics report for the same field.  The larger grid
+library.  Here it is called twice in a row through the C ABI on the density
+and field of a loaded state, and each result must match the FP64 field
+energies and charge that pic_step's own diagnostics report for that field.  The larger grid
 goes first so that partials left in the shared scratch by the first call
 would corrupt the second if a call read any slot it did not write.
 """
@@ -30,9 +30,12 @@ REL = 1e-12   # both sides are FP64 sums of the same FP32 grid data
 
 
 def _one_call(w):
+    """Deposit and solve the loaded state, reduce that field with the
+    allocation-free entry point, then take one pic_step: its diagnostic record
+    of step 0 is computed from the same rho and E."""
     sim = Simulation.from_workload(w, diag_every=1)
-    sim.step(1)
-    rec = sim.diagnostics()[-1]
+    sim.deposit()
+    sim.field_solve()
     nx, ny, nz = w.n
     ng = nx * ny * nz
     rho = torch.empty(ng, dtype=torch.float32, device="cuda")
@@ -44,6 +47,9 @@ def _one_call(w):
                                   sim.stream.cuda_stream)
     sim.stream.synchronize()
     got = out.cpu().numpy()
+    sim.step(1)
+    rec = sim.diagnostics()[-1]
+    assert rec["step"] == 0
     sim.close()
     return got, np.array([rec["Wx"], rec["Wy"], rec["Wz"], rec["Q"]])
 
