@@ -75,6 +75,24 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+# ---------------------------------------------------------------- ranks
+
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The slowest rank's figure (replicas report the job's time as the max)."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas: all ranks' units over the max time."""
+    return units_per_rank * world * steps / seconds
+
+
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -335,11 +353,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     phases, launches = capi.pic_read_timers(sim.handle)
     capi.pic_enable_timers(sim.handle, False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = N * world * args.steps / (ms * 1e-3)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = job_throughput(N, world, args.steps, ms * 1e-3)
 
     hist = sim.diagnostics()
     flags = sim.flags()
@@ -390,11 +405,8 @@ def main():
         torch.cuda.synchronize()
         barrier()
         secs = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([secs], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            secs = float(t.item())
-        e2e = {"value": N * world * args.e2e_steps / secs, "unit": UNIT,
+        secs = max_over_ranks(secs, dist, "cuda")
+        e2e = {"value": job_throughput(N, world, args.e2e_steps, secs), "unit": UNIT,
                "h2d_bytes_per_step": int(xh.numel() * 8 + vh.numel() * 8),
                "d2h_bytes_per_step": C.sizeof(capi.pic_diag_t),
                "what": "per step: pic_load_particles from pinned host FP64 (x, v), "
@@ -438,16 +450,20 @@ def main():
         dist.destroy_process_group()
 
 
-def _source_sha(rel):
+def _source_sha(rels):
+    """Hash of the kernel's source files: the traffic figure is void once they change."""
     import hashlib
 
-    if not rel:
+    if not rels:
         return None
-    p = os.path.join(ROOT, rel)
-    if not os.path.exists(p):
-        return None
-    with open(p, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for rel in ([rels] if isinstance(rels, str) else rels):
+        p = os.path.join(ROOT, rel)
+        if not os.path.exists(p):
+            return None
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 if __name__ == "__main__":

@@ -318,6 +318,8 @@ int pic_batch_create(const pic_instance_t *inst, int n_inst, double q_over_m,
             }
             D.g.nh = I.n[0] / 2 + 1;
             D.g.guard = b->prm.guard;
+            for (int d = 0; d < 3; ++d)
+                D.g.tdiv[d] = D.g.tile[d] > 1 ? (unsigned)((((uint64_t)1 << 32) + D.g.tile[d] - 1) / D.g.tile[d]) : 0u;
             D.g.tvol = D.g.tile[0] * D.g.tile[1] * D.g.tile[2];
             // push constants (as in the single-run path)
             const double dt = b->prm.dt;

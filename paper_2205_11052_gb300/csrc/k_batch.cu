@@ -101,7 +101,8 @@ __device__ __forceinline__ int b_key(int32_t c, const InstDesc &D, int &bad) {
         bad = 1;
         i = j = k = 0;
     }
-    const int ti = i / D.g.tile[0], tj = j / D.g.tile[1], tk = k / D.g.tile[2];
+    const int ti = tile_div(i, D.g.tdiv[0]), tj = tile_div(j, D.g.tdiv[1]);
+    const int tk = tile_div(k, D.g.tdiv[2]);
     return D.tile0 + ti + D.g.ntile[0] * (tj + D.g.ntile[1] * tk);
 }
 

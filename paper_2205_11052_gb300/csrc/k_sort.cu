@@ -34,8 +34,45 @@ __device__ __forceinline__ int tile_key(int32_t c, const Geom &g, int &bad) {
         bad = 1;
         i = j = k = 0;
     }
-    const int ti = i / g.tile[0], tj = j / g.tile[1], tk = k / g.tile[2];
+    // exact division by the tile size through a multiply-high (indices < 2^10)
+    const int ti = tile_div(i, g.tdiv[0]), tj = tile_div(j, g.tdiv[1]), tk = tile_div(k, g.tdiv[2]);
     return ti + g.ntile[0] * (tj + g.ntile[1] * tk);
+}
+
+// Lanes of a warp whose keys form a contiguous run (consecutive lanes, equal
+// keys; binned particles arrive in such runs) share shared-table updates:
+// the run's first lane does one update for the whole run.
+struct WarpRun {
+    int head;   // first lane of this lane's run
+    int len;    // its length
+};
+
+__device__ __forceinline__ WarpRun warp_run(int key) {
+    const int lane = threadIdx.x & 31;
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || key != prev);
+    const unsigned upto = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);
+    WarpRun r;
+    r.head = 31 - __clz(heads & upto);
+    const unsigned after = heads & ~((r.head == 31) ? 0xffffffffu : ((2u << r.head) - 1u));
+    r.len = (after ? __ffs(after) - 1 : 32) - r.head;
+    return r;
+}
+
+// slot of `key` in the shared open-addressing table (inserting it), or -1
+// when the table is full
+__device__ __forceinline__ int table_slot(int32_t *hkey, int key, int size) {
+    int h = (int)(((unsigned)key * 2654435761u) >> 24) & (size - 1);
+    for (int probes = 0; probes < size; ++probes) {
+        const int k = hkey[h];
+        if (k == key) return h;
+        if (k == -1) {
+            const int prev = atomicCAS(&hkey[h], -1, key);
+            if (prev == -1 || prev == key) return h;
+        }
+        h = (h + 1) & (size - 1);
+    }
+    return -1;
 }
 
 // Block-staged scatter.  A block takes kStage consecutive particles into
@@ -45,7 +82,7 @@ __device__ __forceinline__ int tile_key(int32_t c, const Geom &g, int &bad) {
 // with one atomic, and writes every tile's particles contiguously.  A slice
 // with more distinct tiles than the table holds (the first binning of
 // particles in arbitrary order) falls back to per-warp claims.
-constexpr int kStage = 2048;
+constexpr int kStage = 1024;
 constexpr int kHash = 256;
 
 __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl *ctrl,
@@ -87,30 +124,29 @@ __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl 
             sid[j] = __ldcs(src.pid + p);
         }
         __syncthreads();
-        // slot of each particle's tile in the table, and its rank there
-        for (int j = threadIdx.x; j < m; j += blockDim.x) {
-            const int key = tile_key(sc[j], g, bad);
-            int h = (int)(((unsigned)key * 2654435761u) >> 24) & (kHash - 1);
-            int probes = 0;
-            while (true) {
-                const int k = hkey[h];
-                if (k == key) break;
-                if (k == -1) {
-                    const int prev = atomicCAS(&hkey[h], -1, key);
-                    if (prev == -1 || prev == key) break;
-                }
-                h = (h + 1) & (kHash - 1);
-                if (++probes >= kHash) {   // table full
-                    h = -1;
-                    break;
-                }
+        // slot of each particle's tile in the table and its rank there; the
+        // first lane of each run of equal keys in a warp acts for the run
+        for (int jb = 0; jb < m; jb += blockDim.x) {
+            const int j = jb + threadIdx.x;
+            const bool act = j < m;
+            const int lane = threadIdx.x & 31;
+            const int key = act ? tile_key(sc[j], g, bad) : -1 - lane;
+            const WarpRun r = warp_run(key);
+            int h = 0, base = 0;
+            if (act && lane == r.head) {
+                h = table_slot(hkey, key, kHash);
+                if (h >= 0) base = atomicAdd(&hcnt[h], r.len);
             }
-            if (h < 0) {
-                overflow = 1;
-                slid[j] = 0xffff;
-            } else {
-                slid[j] = (uint16_t)h;
-                srank[j] = (uint16_t)atomicAdd(&hcnt[h], 1);
+            h = __shfl_sync(0xffffffffu, h, r.head);
+            base = __shfl_sync(0xffffffffu, base, r.head);
+            if (act) {
+                if (h < 0) {
+                    overflow = 1;
+                    slid[j] = 0xffff;
+                } else {
+                    slid[j] = (uint16_t)h;
+                    srank[j] = (uint16_t)(base + (lane - r.head));
+                }
             }
         }
         __syncthreads();
@@ -180,27 +216,13 @@ __global__ void __launch_bounds__(256) k_histogram_staged(int64_t n, Geom g, Ctr
         for (int jb = 0; jb < m; jb += blockDim.x) {
             const int j = jb + threadIdx.x;
             const bool act = j < m;
-            int key = 0;
-            if (act) key = tile_key(__ldcs(ps.cell + s0 + j), g, bad);
-            int h = -2;
-            if (act) {
-                h = (int)(((unsigned)key * 2654435761u) >> 24) & (kHash - 1);
-                int probes = 0;
-                while (true) {
-                    const int k = hkey[h];
-                    if (k == key) break;
-                    if (k == -1) {
-                        const int prev = atomicCAS(&hkey[h], -1, key);
-                        if (prev == -1 || prev == key) break;
-                    }
-                    h = (h + 1) & (kHash - 1);
-                    if (++probes >= kHash) {
-                        h = -1;
-                        break;
-                    }
-                }
-                if (h >= 0) atomicAdd(&hcnt[h], 1);
-                else atomicAdd(bins + key, 1);   // table full: straight to the grid
+            const int lane = threadIdx.x & 31;
+            const int key = act ? tile_key(__ldcs(ps.cell + s0 + j), g, bad) : -1 - lane;
+            const WarpRun r = warp_run(key);
+            if (act && lane == r.head) {
+                const int h = table_slot(hkey, key, kHash);
+                if (h >= 0) atomicAdd(&hcnt[h], r.len);
+                else atomicAdd(bins + key, r.len);   // table full: straight to the grid
             }
         }
         __syncthreads();
@@ -373,7 +395,7 @@ cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t
     }
     if ((e = exclusive_scan_impl(bins, nbins, scan_tmp, st)) != cudaSuccess) return e;
     if (n > 0) {
-        const int sblocks = (int)std::min<int64_t>((n + kStage - 1) / kStage, 152 * 3);
+        const int sblocks = (int)std::min<int64_t>((n + kStage - 1) / kStage, 152 * 6);
         k_scatter_staged<<<sblocks, T, kStageSmem, st>>>(n, g, ctrl, bins);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -535,6 +535,8 @@ int pic_create(const pic_grid_t *grid, const pic_species_t *species, const pic_p
     }
     g.nh = grid->n[0] / 2 + 1;
     g.guard = p.guard;
+    for (int d = 0; d < 3; ++d)
+        g.tdiv[d] = g.tile[d] > 1 ? (unsigned)((((uint64_t)1 << 32) + g.tile[d] - 1) / g.tile[d]) : 0u;
     g.tvol = g.tile[0] * g.tile[1] * g.tile[2];
     c->dV = c->h[0] * c->h[1] * c->h[2];
     c->ntiles = nt;

@@ -61,9 +61,16 @@ struct Geom {
     int ntile[3];      // tiles per axis = ceil(n / tile)
     int guard;         // guard layers around a tile
     int tvol;          // tile[0]*tile[1]*tile[2]
+    unsigned tdiv[3];  // ceil(2^32 / tile[d]), 0 for a tile of 1 (see tile_div)
     float h[3];        // cell size
     float inv_h[3];
 };
+
+// a / tile[d] for 0 <= a < 1024 by a multiply-high (exact: the rounding of the
+// reciprocal adds less than 2^-22 to a quotient whose fraction is <= 1 - 1/1024)
+__device__ __forceinline__ int tile_div(int a, unsigned tdiv) {
+    return tdiv ? (int)__umulhi((unsigned)a, tdiv) : a;
+}
 
 // Per-step push constants (FP32, precomputed on the host in FP64).
 struct PushConst {

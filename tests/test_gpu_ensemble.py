@@ -93,8 +93,8 @@ def test_ensemble_step_replays_from_a_cuda_graph():
     with torch.cuda.graph(g, stream=s):
         ens.step(2)
     for _ in range(2):
-        g.replay()
-    s.synchronize()
+        g.replay()               # on the current stream
+    torch.cuda.synchronize()
     xs, vs = ens.particles()
     for i, w in enumerate(ws):
         xo, vo, _ = po.run(w.x, w.v, po.Grid(w.n, w.L), po.Params(dt=0.05, Q=w.Q), 6)

@@ -396,8 +396,8 @@ def test_cuda_graph_replay_matches_oracle():
     with torch.cuda.graph(g, stream=s):
         sim.step(2)
     for _ in range(3):
-        g.replay()
-    s.synchronize()
+        g.replay()               # on the current stream
+    torch.cuda.synchronize()
     capi.pic_set_stream(sim.handle, torch.cuda.current_stream().cuda_stream)
     x, v = sim.particles()
     xo, vo, _ = po.run(w.x, w.v, _grid(w), _params(w), 7)
