@@ -54,8 +54,14 @@ def parse():
                     help="particles in the oracle's bounded sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--workload", default="landau", choices=["landau", "ensemble"])
     ap.add_argument("--ens-count", type=int, default=512, help="ensemble instances")
+    ap.add_argument("--record-traffic", metavar="NCU_CSV",
+                    help="write profiles/traffic.json from an ncu --csv capture of "
+                         "k_push_deposit on the 64^3 x 64 case (dram__bytes_read/write.sum), "
+                         "then exit")
     return ap.parse_args()
 
 
@@ -203,6 +209,69 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- adjoint
+
+def measure_adjoint(n_steps=200, K=20, launch=None):
+    """Cost of the discrete adjoint against the forward step on the
+    bump-on-tail workload (64^3 grid, 16 particles per cell, 200 steps).
+
+    Device time of pic_step (the forward step), and of pic_adjoint_forward /
+    pic_adjoint_backward twice: with checkpoints every K steps (the backward
+    pass recomputes each segment, then reverses it) and with the whole
+    trajectory kept in device memory (K = n_steps - 1: the backward pass is
+    the reverse sweep alone, so its cost per step is the adjoint step)."""
+    import torch
+
+    import pic_inputs as pi
+    from paper_2205_11052_gb300.sim import Simulation
+
+    launch = dict(LAUNCH if launch is None else launch)
+    w = pi.by_name("bump_on_tail_64")
+    sim = Simulation.from_workload(w, **launch)
+    st = sim.stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    sim.step(5)                              # warm-up, then back to the loaded state
+    sim.load(w.x, w.v)
+    torch.cuda.synchronize()
+    ev[0].record(st)
+    sim.step(n_steps)
+    ev[1].record(st)
+    torch.cuda.synchronize()
+    fwd_ms = ev[0].elapsed_time(ev[1]) / n_steps
+    out = {"workload": f"bump-on-tail 64^3 x 16 particles/cell ({w.n_particles:,} particles), "
+                       f"{n_steps} steps, objective W_z of the last field",
+           "forward_ms_per_step": fwd_ms}
+    for key, kk in (("checkpoints", K), ("kept_trajectory", n_steps - 1)):
+        sim.load(w.x, w.v)
+        sim.adjoint_forward(n_steps, (0.0, 0.0, 1.0), checkpoint_every=kk)     # warm-up
+        sim.adjoint_backward(device=True)
+        torch.cuda.synchronize()
+        ev[0].record(st)
+        J = sim.adjoint_forward(n_steps, (0.0, 0.0, 1.0), checkpoint_every=kk)
+        ev[1].record(st)
+        ev[2].record(st)
+        gx, gv = sim.adjoint_backward(device=True)
+        ev[3].record(st)
+        torch.cuda.synchronize()
+        af_ms = ev[0].elapsed_time(ev[1]) / n_steps
+        ab_ms = ev[2].elapsed_time(ev[3]) / n_steps
+        out[key] = {"checkpoint_every": kk,
+                    "buffer_gb": round(sim._adj_buf.numel() / 1e9, 2),
+                    "adjoint_forward_ms_per_step": af_ms,
+                    "adjoint_backward_ms_per_step": ab_ms,
+                    "backward_over_forward": ab_ms / fwd_ms,
+                    "gradient_over_forward": (af_ms + ab_ms) / fwd_ms,
+                    "J": J,
+                    "finite": bool(torch.isfinite(gx).all().item() and
+                                   torch.isfinite(gv).all().item())}
+        sim._adj_buf = None
+        torch.cuda.empty_cache()
+    # the adjoint of one step, without checkpoint recomputation
+    out["adjoint_step_over_forward"] = out["kept_trajectory"]["backward_over_forward"]
+    sim.close()
+    return out
+
+
 # ---------------------------------------------------------------- ensemble
 
 def ensemble_members(count, seed=1_000_000):
@@ -242,18 +311,33 @@ def run_ensemble(args):
     gen_s = time.perf_counter() - t0
     N = sum(w.n_particles for w in ws)
     opts = dict(sort_period=args.sort_period, options=args.options)
-    ens = Ensemble([(w.n, w.L, w.x, w.v, w.Q) for w in ws], dt=0.05, **opts)
-    ens.step(args.warmup)
+    members = [(w.n, w.L, w.x, w.v, w.Q) for w in ws]
+    tuned = None
+    if not args.no_tune:
+        from paper_2205_11052_gb300.autotune import tune_ensemble
+
+        t1 = time.perf_counter()
+        best, table = tune_ensemble(members, 0.05, space={"tile": [(8, 8, 8), (4, 4, 4)],
+                                                          "sort_period": [2, 4], "options": [1]})
+        opts = {k: tuple(v) if isinstance(v, list) else v for k, v in best.items()}
+        tuned = {"best": best, "table": table, "seconds": round(time.perf_counter() - t1, 1)}
+    ens = Ensemble(members, dt=0.05, **opts)
+    # all instances, all K steps: one CUDA graph, replayed once per timing
+    graph = ens.capture(args.steps)
+    for _ in range(max(1, args.warmup // max(1, args.steps))):
+        graph.replay()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(0)
     clocks.start()
-    e0.record(ens.stream)
-    ens.step(args.steps)
-    e1.record(ens.stream)
+    rs = torch.cuda.current_stream()
+    e0.record(rs)
+    graph.replay()
+    e1.record(rs)
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms_batch = e0.elapsed_time(e1)
+    del graph
     ens.close()
     del ens
     torch.cuda.empty_cache()
@@ -279,9 +363,12 @@ def run_ensemble(args):
         "ms_per_step": ms_batch / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"ensemble of {len(ws)} Landau instances, grids U{{16,24,32,48}}^3, "
-                               f"8-64 particles/cell, alpha U[0.01,0.1], {N:,} particles",
-                   "generation_s": round(gen_s, 1), **opts},
+                               f"8-64 particles/cell, alpha U[0.01,0.1], {N:,} particles; "
+                               f"batched steps captured in one CUDA graph",
+                   "generation_s": round(gen_s, 1),
+                   **{k: list(v) if isinstance(v, tuple) else v for k, v in opts.items()}},
         "per_instance_launches": {"value": v_single, "ms_per_step": ms_single / args.steps},
+        "autotune": tuned,
         "speedup": ms_single / ms_batch,
         "clocks": clk,
     }
@@ -295,6 +382,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.record_traffic:
+        record_traffic(args.record_traffic)
+        return
     if args.impl == "reference":
         run_reference(args, rank)
         return
@@ -422,6 +512,13 @@ def main():
                          f"{args.grid}^3 grid, 2 oracle steps ({secs:.1f} s, numpy FP64, "
                          f"single thread)"}
 
+    # ---- adjoint step cost against the forward step (bump-on-tail, 64^3)
+    adj = None
+    if rank == 0 and not args.no_adjoint:
+        sim.close()
+        torch.cuda.empty_cache()
+        adj = measure_adjoint()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -439,6 +536,7 @@ def main():
             "phases_ms": {k: round(v[0], 4) for k, v in phase_ms.items()},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "adjoint": adj,
             "gpu_launches": launches,
             "clocks": clk,
             "device_flags": flags,
@@ -448,6 +546,46 @@ def main():
     sim.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+TRAFFIC_SOURCES = ["paper_2205_11052_gb300/csrc/k_particles.cu",
+                   "paper_2205_11052_gb300/csrc/push.cuh",
+                   "paper_2205_11052_gb300/csrc/cic.cuh",
+                   "paper_2205_11052_gb300/csrc/pic_internal.cuh"]
+
+
+def record_traffic(csv_path, small_particles=64 ** 3 * 64, small_nodes=64 ** 3,
+                   full_particles=128 ** 3 * 64, full_nodes=128 ** 3):
+    """DRAM bytes of one k_push_deposit launch from an ncu CSV of the 64^3 x 64
+    case, scaled to the 128^3 x 64 launch by the particle ratio (the kernel's
+    traffic is proportional to particles and nodes, both x8), into
+    profiles/traffic.json with the hash of the kernel's sources."""
+    import csv
+
+    with open(csv_path) as f:
+        rows = [r for r in csv.reader(f)]
+    hi = next(i for i, r in enumerate(rows) if "Metric Name" in r)
+    h = rows[hi]
+    ki, mi, ui, vi = (h.index("Kernel Name"), h.index("Metric Name"), h.index("Metric Unit"),
+                      h.index("Metric Value"))
+    unit = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    per = {}
+    for r in rows[hi + 1:]:
+        if len(r) > vi and "k_push_deposit" in r[ki] and r[mi].startswith("dram__bytes_"):
+            per.setdefault(r[mi], []).append(float(r[vi].replace(",", "")) * unit[r[ui]])
+    small = sum(v[0] for v in per.values())
+    scale = full_particles / small_particles
+    assert abs(full_nodes / small_nodes - scale) < 1e-12
+    out = {"k_push_deposit": {
+        "source": TRAFFIC_SOURCES, "source_sha": _source_sha(TRAFFIC_SOURCES),
+        "bytes_per_launch_small": small,
+        "small_case": "landau 64^3 x 64 ppc (16,777,216 particles), sort period 4, fixed-point deposit",
+        "scale": scale, "bytes_per_launch_full_size": small * scale,
+        "note": "dram__bytes_read.sum + dram__bytes_write.sum of one launch, scaled by the "
+                "particle (and node) ratio to the 128^3 x 64 workload"}}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out))
 
 
 def _source_sha(rels):

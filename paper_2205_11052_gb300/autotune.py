@@ -5,8 +5,8 @@ deposit tile, guard layers, re-binning period, deposit accumulator -- on the
 caller's own particles with CUDA events (a few warm-up steps, then a few
 timed steps each) and returns the fastest.  Results are cached by the shape
 of the workload (grid, particles per cell, external fields), in memory and
-optionally in a JSON file, so an ensemble of many instances with a handful of
-grid sizes is tuned once per size.
+optionally in a JSON file.  ``tune_ensemble`` does the same for a batched
+ensemble, timing the whole ensemble per candidate.
 """
 from __future__ import annotations
 
@@ -87,3 +87,58 @@ class Autotuner:
             with open(self.cache_path, "w") as f:
                 json.dump(self.cache, f, indent=1)
         return best
+
+
+ENSEMBLE_SPACE = {
+    "tile": [(8, 8, 8), (4, 4, 4), (8, 8, 4)],
+    "sort_period": [2, 4],
+    "options": [1, 0],
+}
+
+
+def ensemble_key(members) -> str:
+    """Cache key of an ensemble: its sorted (grid, particles-per-cell bucket) mix."""
+    parts = sorted(workload_key(n, np.asarray(x).shape[0]) for n, L, x, v, Q in members)
+    return "ens|" + ";".join(f"{p}x{parts.count(p)}" for p in sorted(set(parts)))
+
+
+def tune_ensemble(members, dt, space=None, warmup=2, steps=4, cache=None, **fixed):
+    """Fastest ensemble setting among the candidates of `space` (a dict of
+    lists over tile / sort_period / options / guard), each timed on the
+    device over `steps` steps of the whole ensemble after `warmup` steps.
+    Returns (best setting, table of (setting, ms per step))."""
+    import torch
+
+    from .batch import Ensemble
+
+    space = dict(ENSEMBLE_SPACE if space is None else space)
+    key = ensemble_key(members)
+    if cache is not None and key in cache:
+        return cache[key]["best"], cache[key]["table"]
+    nmin = min(min(int(a) for a in (n if np.ndim(n) else (n, n, n))) for n, *_ in members)
+    keys = sorted(space)
+    table = []
+    for combo in itertools.product(*(space[k] for k in keys)):
+        cfg = dict(zip(keys, combo))
+        if "tile" in cfg:
+            cfg["tile"] = tuple(min(int(t), nmin) for t in cfg["tile"])
+        ens = Ensemble(members, dt=dt, **fixed, **cfg)
+        try:
+            ens.step(warmup)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(ens.stream)
+            ens.step(steps)
+            e1.record(ens.stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+        finally:
+            ens.close()
+            del ens
+            torch.cuda.empty_cache()
+        table.append(({k: list(v) if isinstance(v, tuple) else v for k, v in cfg.items()}, ms))
+    table.sort(key=lambda r: r[1])
+    best = table[0][0]
+    if cache is not None:
+        cache[key] = {"best": best, "table": table}
+    return best, table

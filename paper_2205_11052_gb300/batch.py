@@ -53,6 +53,25 @@ class Ensemble:
     def step(self, n: int = 1):
         capi.pic_batch_step(self.handle, int(n))
 
+    def capture(self, n: int = 1):
+        """Capture n steps into a CUDA graph (one launch of the whole ensemble
+        for all n steps); each ``replay()`` of the returned graph advances every
+        instance by n steps.  The ensemble moves to a private stream and takes
+        one eager step first, so that the captured launches find their state
+        initialised."""
+        import torch
+
+        s = torch.cuda.Stream(self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        self.set_stream(s)
+        with torch.cuda.stream(s):
+            self.step(1)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            self.step(n)
+        return g
+
     def set_stream(self, stream):
         self.stream = stream
         capi.pic_batch_set_stream(self.handle, stream.cuda_stream)

@@ -101,7 +101,31 @@ __device__ __forceinline__ void deposit_global(float *rho, unsigned long long *r
 // origin o; add one particle (or send it to the grid if it left the guard).
 struct Tile {
     int ox, oy, oz, S0, S01, S;
+    unsigned m0, m01;   // ceil(2^32 / S0), ceil(2^32 / S01): slot -> (a, b, c) by multiply-high
 };
+
+// slot s -> its (a, b, c) position in the tile box; exact for s * S01 < 2^32
+__host__ __device__ __forceinline__ unsigned mulhi32(unsigned a, unsigned m) {
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, m);
+#else
+    return (unsigned)(((unsigned long long)a * m) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ void tile_pos(const Tile &t, int s, int &a, int &b, int &c) {
+    c = (int)mulhi32((unsigned)s, t.m01);
+    const int r = s - c * t.S01;
+    b = (int)mulhi32((unsigned)r, t.m0);
+    a = r - b * t.S0;
+}
+
+// o + d folded into [0, n) for d within a few periods of the box
+__host__ __device__ __forceinline__ int wrap_index(int v, int n) {
+    while (v < 0) v += n;
+    while (v >= n) v -= n;
+    return v;
+}
 
 __host__ __device__ __forceinline__ Tile tile_of(const Geom &g, int tile) {
     Tile t;
@@ -115,6 +139,8 @@ __host__ __device__ __forceinline__ Tile tile_of(const Geom &g, int tile) {
     t.S0 = g.tile[0] + 2 * G + 1;
     t.S01 = t.S0 * (g.tile[1] + 2 * G + 1);
     t.S = t.S01 * (g.tile[2] + 2 * G + 1);
+    t.m0 = 0xFFFFFFFFu / (unsigned)t.S0 + 1u;
+    t.m01 = 0xFFFFFFFFu / (unsigned)t.S01 + 1u;
     return t;
 }
 
@@ -157,13 +183,11 @@ __device__ __forceinline__ void tile_flush(const uint32_t *acc, const Tile &t, c
     for (int s = threadIdx.x; s < t.S; s += blockDim.x) {
         const uint32_t raw = acc[s];
         if (raw != 0u) {
-            const int a = s % t.S0, b = (s / t.S0) % (t.S01 / t.S0), cz = s / t.S01;
-            int gi = (t.ox - G + a) % g.n[0];
-            int gj = (t.oy - G + b) % g.n[1];
-            int gk = (t.oz - G + cz) % g.n[2];
-            if (gi < 0) gi += g.n[0];
-            if (gj < 0) gj += g.n[1];
-            if (gk < 0) gk += g.n[2];
+            int a, b, cz;
+            tile_pos(t, s, a, b, cz);
+            const int gi = wrap_index(t.ox - G + a, g.n[0]);
+            const int gj = wrap_index(t.oy - G + b, g.n[1]);
+            const int gk = wrap_index(t.oz - G + cz, g.n[2]);
             const int64_t node = gi + (int64_t)g.n[0] * (gj + (int64_t)g.n[1] * gk);
             if (FIXED) atomicAdd(rho64 + node, (unsigned long long)raw);
             else atomicAdd(rho + node, __uint_as_float(raw) * qscale);

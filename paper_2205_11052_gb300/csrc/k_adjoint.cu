@@ -19,6 +19,7 @@
 // dW/dy of a CIC weight w_a(fx) w_b(fy) w_c(fz): d w_1 / dx = 1/h, d w_0 / dx = -1/h.
 #include <algorithm>
 
+#include "cic.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -36,34 +37,31 @@ __device__ __forceinline__ bool decode(int32_t c, const Geom &g, int &i, int &j,
     return true;
 }
 
-__device__ __forceinline__ void nodes8(const Geom &g, int i, int j, int k, int64_t nd[8]) {
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+// the 8 corner nodes of cell (i, j, k), corner bits a | b<<1 | c<<2 (int32:
+// grids have at most 2^30 nodes)
+__device__ __forceinline__ void corners(int i, int j, int k, int nx, int ny, int nz, int nd[8]) {
     const int i1 = (i + 1 == nx) ? 0 : i + 1;
     const int j1 = (j + 1 == ny) ? 0 : j + 1;
     const int k1 = (k + 1 == nz) ? 0 : k + 1;
-    const int64_t nxy = (int64_t)nx * ny;
-    const int64_t r00 = (int64_t)j * nx + k * nxy, r10 = (int64_t)j1 * nx + k * nxy;
-    const int64_t r01 = (int64_t)j * nx + k1 * nxy, r11 = (int64_t)j1 * nx + k1 * nxy;
+    const int r00 = (j + ny * k) * nx, r10 = (j1 + ny * k) * nx;
+    const int r01 = (j + ny * k1) * nx, r11 = (j1 + ny * k1) * nx;
     nd[0] = r00 + i; nd[1] = r00 + i1; nd[2] = r10 + i; nd[3] = r10 + i1;
     nd[4] = r01 + i; nd[5] = r01 + i1; nd[6] = r11 + i; nd[7] = r11 + i1;
 }
 
-// weights and their gradients for the 8 corners (corner bits a | b<<1 | c<<2)
-__device__ __forceinline__ void weights_and_grads(float fx, float fy, float fz, const Geom &g,
-                                                  float w[8], float dwx[8], float dwy[8],
-                                                  float dwz[8]) {
-    const float ax[2] = {1.0f - fx, fx}, ay[2] = {1.0f - fy, fy}, az[2] = {1.0f - fz, fz};
-    const float sx[2] = {-g.inv_h[0], g.inv_h[0]};
-    const float sy[2] = {-g.inv_h[1], g.inv_h[1]};
-    const float sz[2] = {-g.inv_h[2], g.inv_h[2]};
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int a = c & 1, b = (c >> 1) & 1, d = (c >> 2) & 1;
-        w[c] = ax[a] * ay[b] * az[d];
-        dwx[c] = sx[a] * ay[b] * az[d];
-        dwy[c] = ax[a] * sy[b] * az[d];
-        dwz[c] = ax[a] * ay[b] * sz[d];
-    }
+// Gradient, with respect to the in-cell offsets (fx, fy, fz), of the CIC
+// interpolation sum_abc w_abc s_abc with w_abc = ax_a ay_b az_c
+// (ax_0 = 1 - fx, ax_1 = fx): d/dfx = sum_bc ay_b az_c (s_1bc - s_0bc),
+// likewise along y and z.  Multiply by 1/h for the gradient in y.
+__device__ __forceinline__ void interp_grad(float fx, float fy, float fz, const float sc[8],
+                                            float &dx, float &dy, float &dz) {
+    const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+    dx = gy * gz * (sc[1] - sc[0]) + fy * gz * (sc[3] - sc[2]) + gy * fz * (sc[5] - sc[4]) +
+         fy * fz * (sc[7] - sc[6]);
+    dy = gx * gz * (sc[2] - sc[0]) + fx * gz * (sc[3] - sc[1]) + gx * fz * (sc[6] - sc[4]) +
+         fx * fz * (sc[7] - sc[5]);
+    dz = gx * gy * (sc[4] - sc[0]) + fx * gy * (sc[5] - sc[1]) + gx * fy * (sc[6] - sc[2]) +
+         fx * fy * (sc[7] - sc[3]);
 }
 
 __device__ __forceinline__ int tile_slot(int a, int o, int n, int T, int G) {
@@ -86,22 +84,29 @@ __global__ void k_adj_seed(int64_t ng, const float4 *__restrict__ E4, float4 *__
     }
 }
 
-// reverse push: lv <- lv + dt ly; le = c lv; ly += (dG/dy . E)^T le + Ext^T le;
-// lE += G^T le (shared-memory tile per work item, strays with global atomics)
-__global__ void __launch_bounds__(256) k_adj_push(Geom g, const Ctrl *__restrict__ ctrl,
-                                                   const int4 *__restrict__ items,
-                                                   const int32_t *__restrict__ ycell,
-                                                   const float *__restrict__ yo0,
-                                                   const float *__restrict__ yo1,
-                                                   const float *__restrict__ yo2,
-                                                   const float4 *__restrict__ E4,
-                                                   float4 *__restrict__ lE4, float c_kick,
-                                                   float dt, float wz2, Ctrl *ctrl_w) {
+// reverse push: [ly += (dD/dy)^T lrho of the following step, when given;]
+// lv <- lv + dt ly; le = c lv; ly += (dG/dy . E)^T le + Ext^T le;
+// lE += G^T le (shared-memory tile per work item, strays with global atomics;
+// global updates are one 16-byte vector atomic per node).
+//
+// The gather term is the offset gradient (interp_grad) of the CIC
+// interpolation of s_abc = le . E at the 8 corners.
+__global__ void __launch_bounds__(256, 3) k_adj_push(Geom g, const Ctrl *__restrict__ ctrl,
+                                                      const int4 *__restrict__ items,
+                                                      const int32_t *__restrict__ ycell,
+                                                      const float *__restrict__ yo0,
+                                                      const float *__restrict__ yo1,
+                                                      const float *__restrict__ yo2,
+                                                      const float4 *__restrict__ E4,
+                                                      float4 *__restrict__ lE4, float c_kick,
+                                                      float dt, float wz2, AdjRhoTerm rt,
+                                                      Ctrl *ctrl_w) {
     extern __shared__ float acc[];   // 3 * S floats: x, y, z components
     const int cur = ctrl->cur;
     const ParticleSet lam = ctrl->sets[1 - cur];   // ly in o[], lv in v[]
     const int n_items = ctrl->n_items;
     const int G = g.guard;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int S0 = g.tile[0] + 2 * G + 1, S1 = g.tile[1] + 2 * G + 1, S2 = g.tile[2] + 2 * G + 1;
     const int S01 = S0 * S1, S = S01 * S2;
     int bad = 0;
@@ -112,76 +117,85 @@ __global__ void __launch_bounds__(256) k_adj_push(Geom g, const Ctrl *__restrict
         const int ty = (tile / g.ntile[0]) % g.ntile[1];
         const int tz = tile / (g.ntile[0] * g.ntile[1]);
         const int ox = tx * g.tile[0], oy = ty * g.tile[1], oz = tz * g.tile[2];
-        for (int s = threadIdx.x; s < 3 * S; s += blockDim.x) acc[s] = 0.0f;
+        const cic::Tile tb = cic::tile_of(g, tile);
+        for (int q = threadIdx.x; q < 3 * S; q += blockDim.x) acc[q] = 0.0f;
         __syncthreads();
         for (int p = item.y + threadIdx.x; p < item.z; p += blockDim.x) {
             int i, j, k;
             if (!decode(ycell[p], g, i, j, k)) bad = 1;
-            float w[8], dwx[8], dwy[8], dwz[8];
-            weights_and_grads(yo0[p], yo1[p], yo2[p], g, w, dwx, dwy, dwz);
-            int64_t nd[8];
-            nodes8(g, i, j, k, nd);
-            float ly[3] = {lam.o[0][p], lam.o[1][p], lam.o[2][p]};
-            float lv[3] = {lam.v[0][p], lam.v[1][p], lam.v[2][p]};
+            float ly0 = lam.o[0][p], ly1 = lam.o[1][p], ly2 = lam.o[2][p];
+            if (rt.cell) {
+                // the deposit term (dD/dy)^T lrho of the step after this one
+                int ri, rj, rk;
+                decode(rt.cell[p], g, ri, rj, rk);
+                int rn[8];
+                corners(ri, rj, rk, nx, ny, nz, rn);
+                float rs[8];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) lv[d] += dt * ly[d];
-            const float le[3] = {c_kick * lv[0], c_kick * lv[1], c_kick * lv[2]};
-            float tx_ = 0.f, ty_ = 0.f, tz_ = 0.f;
+                for (int cc = 0; cc < 8; ++cc) rs[cc] = __ldg(rt.lrho + rn[cc]);
+                float rx, ry, rz;
+                interp_grad(rt.o[0][p], rt.o[1][p], rt.o[2][p], rs, rx, ry, rz);
+                ly0 += rt.sx * rx;
+                ly1 += rt.sy * ry;
+                ly2 += rt.sz * rz;
+            }
+            const float fx = yo0[p], fy = yo1[p], fz = yo2[p];
+            const float lv0 = lam.v[0][p] + dt * ly0;
+            const float lv1 = lam.v[1][p] + dt * ly1;
+            const float lv2 = lam.v[2][p] + dt * ly2;
+            const float le0 = c_kick * lv0, le1 = c_kick * lv1, le2 = c_kick * lv2;
+            int nd[8];
+            corners(i, j, k, nx, ny, nz, nd);
+            float sc[8];
 #pragma unroll
             for (int cc = 0; cc < 8; ++cc) {
                 const float4 e = __ldg(E4 + nd[cc]);
-                const float s = le[0] * e.x + le[1] * e.y + le[2] * e.z;
-                tx_ += dwx[cc] * s;
-                ty_ += dwy[cc] * s;
-                tz_ += dwz[cc] * s;
+                sc[cc] = le0 * e.x + le1 * e.y + le2 * e.z;
             }
-            ly[0] += tx_ - 0.5f * wz2 * le[0];
-            ly[1] += ty_ - 0.5f * wz2 * le[1];
-            ly[2] += tz_ + wz2 * le[2];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                lam.o[d][p] = ly[d];
-                lam.v[d][p] = lv[d];
-            }
+            float dx, dy, dz;
+            interp_grad(fx, fy, fz, sc, dx, dy, dz);
+            ly0 += g.inv_h[0] * dx - 0.5f * wz2 * le0;
+            ly1 += g.inv_h[1] * dy - 0.5f * wz2 * le1;
+            ly2 += g.inv_h[2] * dz + wz2 * le2;
+            lam.o[0][p] = ly0;
+            lam.o[1][p] = ly1;
+            lam.o[2][p] = ly2;
+            lam.v[0][p] = lv0;
+            lam.v[1][p] = lv1;
+            lam.v[2][p] = lv2;
             // G^T le
-            const int si = tile_slot(i, ox, g.n[0], g.tile[0], G);
-            const int sj = tile_slot(j, oy, g.n[1], g.tile[1], G);
-            const int sk = tile_slot(k, oz, g.n[2], g.tile[2], G);
+            const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+            const float w[8] = {gx * gy * gz, fx * gy * gz, gx * fy * gz, fx * fy * gz,
+                                gx * gy * fz, fx * gy * fz, gx * fy * fz, fx * fy * fz};
+            const int si = tile_slot(i, ox, nx, g.tile[0], G);
+            const int sj = tile_slot(j, oy, ny, g.tile[1], G);
+            const int sk = tile_slot(k, oz, nz, g.tile[2], G);
             if (si >= 0 && sj >= 0 && sk >= 0) {
                 const int s = si + S0 * sj + S01 * sk;
                 const int off[8] = {0, 1, S0, S0 + 1, S01, S01 + 1, S01 + S0, S01 + S0 + 1};
 #pragma unroll
                 for (int cc = 0; cc < 8; ++cc) {
-                    atomicAdd(acc + s + off[cc], w[cc] * le[0]);
-                    atomicAdd(acc + S + s + off[cc], w[cc] * le[1]);
-                    atomicAdd(acc + 2 * S + s + off[cc], w[cc] * le[2]);
+                    atomicAdd(acc + s + off[cc], w[cc] * le0);
+                    atomicAdd(acc + S + s + off[cc], w[cc] * le1);
+                    atomicAdd(acc + 2 * S + s + off[cc], w[cc] * le2);
                 }
             } else {
 #pragma unroll
-                for (int cc = 0; cc < 8; ++cc) {
-                    float *dst = reinterpret_cast<float *>(lE4 + nd[cc]);
-                    atomicAdd(dst + 0, w[cc] * le[0]);
-                    atomicAdd(dst + 1, w[cc] * le[1]);
-                    atomicAdd(dst + 2, w[cc] * le[2]);
-                }
+                for (int cc = 0; cc < 8; ++cc)
+                    atomicAdd(lE4 + nd[cc], make_float4(w[cc] * le0, w[cc] * le1, w[cc] * le2, 0.0f));
             }
         }
         __syncthreads();
-        for (int s = threadIdx.x; s < S; s += blockDim.x) {
-            const float ax = acc[s], ay = acc[S + s], az = acc[2 * S + s];
+        for (int q = threadIdx.x; q < S; q += blockDim.x) {
+            const float ax = acc[q], ay = acc[S + q], az = acc[2 * S + q];
             if (ax != 0.0f || ay != 0.0f || az != 0.0f) {
-                const int a = s % S0, b = (s / S0) % S1, cz = s / S01;
-                int gi = (ox - G + a) % g.n[0];
-                int gj = (oy - G + b) % g.n[1];
-                int gk = (oz - G + cz) % g.n[2];
-                if (gi < 0) gi += g.n[0];
-                if (gj < 0) gj += g.n[1];
-                if (gk < 0) gk += g.n[2];
-                float *dst = reinterpret_cast<float *>(
-                    lE4 + gi + (int64_t)g.n[0] * (gj + (int64_t)g.n[1] * gk));
-                atomicAdd(dst + 0, ax);
-                atomicAdd(dst + 1, ay);
-                atomicAdd(dst + 2, az);
+                int a, b, cz;
+                cic::tile_pos(tb, q, a, b, cz);
+                const int gi = cic::wrap_index(ox - G + a, nx);
+                const int gj = cic::wrap_index(oy - G + b, ny);
+                const int gk = cic::wrap_index(oz - G + cz, nz);
+                atomicAdd(lE4 + gi + (int64_t)nx * (gj + (int64_t)ny * gk),
+                          make_float4(ax, ay, az, 0.0f));
             }
         }
         __syncthreads();
@@ -224,25 +238,22 @@ __global__ void k_adj_rho(int64_t n, Geom g, const Ctrl *__restrict__ ctrl,
                           const float *__restrict__ yo1, const float *__restrict__ yo2,
                           const float *__restrict__ lrho, float qscale) {
     const ParticleSet lam = ctrl->sets[1 - ctrl->cur];
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const float sx = qscale * g.inv_h[0], sy = qscale * g.inv_h[1], sz = qscale * g.inv_h[2];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
         int i, j, k;
         decode(ycell[p], g, i, j, k);
-        float w[8], dwx[8], dwy[8], dwz[8];
-        weights_and_grads(yo0[p], yo1[p], yo2[p], g, w, dwx, dwy, dwz);
-        int64_t nd[8];
-        nodes8(g, i, j, k, nd);
-        float tx = 0.f, ty = 0.f, tz = 0.f;
+        int nd[8];
+        corners(i, j, k, nx, ny, nz, nd);
+        float sc[8];
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc) {
-            const float r = __ldg(lrho + nd[cc]);
-            tx += dwx[cc] * r;
-            ty += dwy[cc] * r;
-            tz += dwz[cc] * r;
-        }
-        lam.o[0][p] += qscale * tx;
-        lam.o[1][p] += qscale * ty;
-        lam.o[2][p] += qscale * tz;
+        for (int cc = 0; cc < 8; ++cc) sc[cc] = __ldg(lrho + nd[cc]);
+        float dx, dy, dz;
+        interp_grad(yo0[p], yo1[p], yo2[p], sc, dx, dy, dz);
+        lam.o[0][p] += sx * dx;
+        lam.o[1][p] += sy * dy;
+        lam.o[2][p] += sz * dz;
     }
 }
 
@@ -272,6 +283,23 @@ __global__ void k_adj_unload(int64_t o0, int64_t m, const int32_t *__restrict__ 
         const double ly = lam.o[d][p], lv = lam.v[d][p];
         gx[3 * q + d] = scale * ly;
         gv[3 * q + d] = scale * (lv + half_dt * ly);
+    }
+}
+
+// The forward sweep re-bins the particles every few steps, and the
+// multipliers of a step are in that step's particle order.  Moving them back
+// across a re-binning is a permutation: with pos[pid] the slot of particle
+// pid in the later order, slot i of the earlier order (particle
+// pid_prev[i]) takes the multipliers from slot pos[pid_prev[i]].
+__global__ void k_adj_reorder(int64_t n, const int32_t *__restrict__ pos,
+                              const int32_t *__restrict__ pid_prev, ReorderArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t j = pos[pid_prev[i]];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        a.out_o[d][i] = a.in_o[d][j];
+        a.out_v[d][i] = a.in_v[d][j];
     }
 }
 
@@ -333,8 +361,8 @@ cudaError_t launch_adj_seed(int64_t ng, const float4 *E4, float4 *lE4, const dou
 
 cudaError_t launch_adj_push(const Geom &g, const Ctrl *ctrl, const int4 *items, int max_items,
                             const int32_t *ycell, const float *const yo[3], const float4 *E4,
-                            float4 *lE4, float c_kick, float dt, float wz2, Ctrl *ctrl_w,
-                            cudaStream_t st) {
+                            float4 *lE4, float c_kick, float dt, float wz2, const AdjRhoTerm &rt,
+                            Ctrl *ctrl_w, cudaStream_t st) {
     const int S = (g.tile[0] + 2 * g.guard + 1) * (g.tile[1] + 2 * g.guard + 1) *
                   (g.tile[2] + 2 * g.guard + 1);
     const size_t smem = sizeof(float) * 3 * (size_t)S;
@@ -345,7 +373,7 @@ cudaError_t launch_adj_push(const Geom &g, const Ctrl *ctrl, const int4 *items, 
     }
     const int blocks = std::max(1, std::min(152 * 4, max_items));
     k_adj_push<<<blocks, 256, smem, st>>>(g, ctrl, items, ycell, yo[0], yo[1], yo[2], E4, lE4,
-                                          c_kick, dt, wz2, ctrl_w);
+                                          c_kick, dt, wz2, rt, ctrl_w);
     return cudaGetLastError();
 }
 
@@ -372,6 +400,21 @@ cudaError_t launch_adj_zero(int64_t n, const Ctrl *ctrl, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int b = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
     k_adj_zero<<<b, 256, 0, st>>>(n, ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_reorder(int64_t n, const int32_t *pos, const int32_t *pid_prev,
+                               const float *const in_o[3], const float *const in_v[3],
+                               float *const out_o[3], float *const out_v[3], cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    ReorderArgs a;
+    for (int d = 0; d < 3; ++d) {
+        a.in_o[d] = in_o[d];
+        a.in_v[d] = in_v[d];
+        a.out_o[d] = out_o[d];
+        a.out_v[d] = out_v[d];
+    }
+    k_adj_reorder<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, pos, pid_prev, a);
     return cudaGetLastError();
 }
 

@@ -125,6 +125,24 @@ __global__ void k_diag_finalize(const double *__restrict__ fpart, int fblocks,
 
 }  // namespace
 
+// The push kernels read E through 256-bit loads of x-adjacent node pairs:
+// E8[2q] = E at node q, E8[2q + 1] = E at its +x neighbour (periodic).
+__global__ void k_pair_E(int nx, int64_t ng, const float4 *__restrict__ E4, float4 *__restrict__ E8) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= ng) return;
+    const int64_t row = q / nx;
+    const int i = (int)(q - row * nx);
+    const int64_t q1 = (i + 1 == nx) ? row * nx : q + 1;
+    E8[2 * q] = E4[q];
+    E8[2 * q + 1] = E4[q1];
+}
+
+cudaError_t launch_pair_E(const Geom &g, const float4 *E4, float4 *E8, cudaStream_t st) {
+    const int64_t ng = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    k_pair_E<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(g.n[0], ng, E4, E8);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_green(const Geom &g, const double *L_d, const float2 *rho_hat, float2 *E_hat,
                          int64_t nhalf, const int *mode_idx, int mode_comp, int mode_conj,
                          Ctrl *ctrl, cudaStream_t st) {

@@ -104,7 +104,7 @@ __global__ void k_unload(int64_t o0, int64_t m, const int32_t *__restrict__ inv,
 // ---------------------------------------------------------------------------
 template <bool DIAG, bool EXT, bool MAG>
 __global__ void __launch_bounds__(256, 3) k_gather_push(int64_t n, Geom g, PushConst pc, Ctrl *ctrl,
-                                                      const float4 *__restrict__ E4,
+                                                      const float4 *__restrict__ E8,
                                                       double *__restrict__ part) {
     const ParticleSet ps = ctrl->sets[ctrl->cur];
     float a_vx = 0.f, a_vy = 0.f, a_vz = 0.f, a_v2 = 0.f;
@@ -119,10 +119,10 @@ __global__ void __launch_bounds__(256, 3) k_gather_push(int64_t n, Geom g, PushC
         float4 ux = __ldcs(reinterpret_cast<const float4 *>(ps.v[0]) + q);
         float4 uy = __ldcs(reinterpret_cast<const float4 *>(ps.v[1]) + q);
         float4 uz = __ldcs(reinterpret_cast<const float4 *>(ps.v[2]) + q);
-        push_one<EXT, MAG>(g, pc, E4, c.x, ox.x, oy.x, oz.x, ux.x, uy.x, uz.x, bad);
-        push_one<EXT, MAG>(g, pc, E4, c.y, ox.y, oy.y, oz.y, ux.y, uy.y, uz.y, bad);
-        push_one<EXT, MAG>(g, pc, E4, c.z, ox.z, oy.z, oz.z, ux.z, uy.z, uz.z, bad);
-        push_one<EXT, MAG>(g, pc, E4, c.w, ox.w, oy.w, oz.w, ux.w, uy.w, uz.w, bad);
+        push_one_pairs<EXT, MAG>(g, pc, E8, c.x, ox.x, oy.x, oz.x, ux.x, uy.x, uz.x, bad);
+        push_one_pairs<EXT, MAG>(g, pc, E8, c.y, ox.y, oy.y, oz.y, ux.y, uy.y, uz.y, bad);
+        push_one_pairs<EXT, MAG>(g, pc, E8, c.z, ox.z, oy.z, oz.z, ux.z, uy.z, uz.z, bad);
+        push_one_pairs<EXT, MAG>(g, pc, E8, c.w, ox.w, oy.w, oz.w, ux.w, uy.w, uz.w, bad);
         __stcs(reinterpret_cast<int4 *>(ps.cell) + q, c);
         __stcs(reinterpret_cast<float4 *>(ps.o[0]) + q, ox);
         __stcs(reinterpret_cast<float4 *>(ps.o[1]) + q, oy);
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256, 3) k_gather_push(int64_t n, Geom g, PushC
         int32_t c = ps.cell[p];
         float fx = ps.o[0][p], fy = ps.o[1][p], fz = ps.o[2][p];
         float vx = ps.v[0][p], vy = ps.v[1][p], vz = ps.v[2][p];
-        push_one<EXT, MAG>(g, pc, E4, c, fx, fy, fz, vx, vy, vz, bad);
+        push_one_pairs<EXT, MAG>(g, pc, E8, c, fx, fy, fz, vx, vy, vz, bad);
         ps.cell[p] = c;
         ps.o[0][p] = fx;
         ps.o[1][p] = fy;
@@ -193,13 +193,13 @@ __global__ void __launch_bounds__(256, 3) k_gather_push(int64_t n, Geom g, PushC
 // bytes per particle) instead of being read again by a separate deposit.
 // ---------------------------------------------------------------------------
 template <bool DIAG, bool EXT, bool MAG, bool FIXED>
-__device__ __forceinline__ void pd_one(const Geom &g, const PushConst &pc, const float4 *E4,
+__device__ __forceinline__ void pd_one(const Geom &g, const PushConst &pc, const float4 *E8,
                                        bool sparse, uint32_t *acc, const cic::Tile &t, float *rho,
                                        unsigned long long *rho64, float qscale, int32_t &c,
                                        float &fx, float &fy, float &fz, float &vx, float &vy,
                                        float &vz, int &bad, unsigned long long &strays,
                                        float (&a)[4]) {
-    push_one<EXT, MAG>(g, pc, E4, c, fx, fy, fz, vx, vy, vz, bad);
+    push_one_pairs<EXT, MAG>(g, pc, E8, c, fx, fy, fz, vx, vy, vz, bad);
     const int i = cell_i(c), j = cell_j(c), k = cell_k(c);
     if (sparse) {
         float w[8];
@@ -217,9 +217,9 @@ __device__ __forceinline__ void pd_one(const Geom &g, const PushConst &pc, const
 }
 
 template <bool DIAG, bool EXT, bool MAG, bool FIXED>
-__global__ void __launch_bounds__(256, 3) k_push_deposit(Geom g, PushConst pc, Ctrl *ctrl,
+__global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g, PushConst pc, Ctrl *ctrl,
                                                           const int4 *__restrict__ items,
-                                                          const float4 *__restrict__ E4,
+                                                          const float4 *__restrict__ E8,
                                                           float *rho, unsigned long long *rho64,
                                                           float qscale, int sparse_below,
                                                           double *__restrict__ part) {
@@ -237,53 +237,20 @@ __global__ void __launch_bounds__(256, 3) k_push_deposit(Geom g, PushConst pc, C
             for (int s = threadIdx.x; s < t.S; s += blockDim.x) acc[s] = 0u;
             __syncthreads();
         }
-        // 16-byte groups of 4 over the aligned interior [q0*4, q1*4) of the
-        // item, single particles for its unaligned head and tail
-        const int q0 = (item.y + 3) >> 2, q1 = item.z >> 2;
-        for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-            int4 c = __ldcs(reinterpret_cast<const int4 *>(ps.cell) + q);
-            float4 ox = __ldcs(reinterpret_cast<const float4 *>(ps.o[0]) + q);
-            float4 oy = __ldcs(reinterpret_cast<const float4 *>(ps.o[1]) + q);
-            float4 oz = __ldcs(reinterpret_cast<const float4 *>(ps.o[2]) + q);
-            float4 ux = __ldcs(reinterpret_cast<const float4 *>(ps.v[0]) + q);
-            float4 uy = __ldcs(reinterpret_cast<const float4 *>(ps.v[1]) + q);
-            float4 uz = __ldcs(reinterpret_cast<const float4 *>(ps.v[2]) + q);
-            pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E4, sparse, acc, t, rho, rho64, qscale, c.x, ox.x,
-                                          oy.x, oz.x, ux.x, uy.x, uz.x, bad, strays, a);
-            pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E4, sparse, acc, t, rho, rho64, qscale, c.y, ox.y,
-                                          oy.y, oz.y, ux.y, uy.y, uz.y, bad, strays, a);
-            pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E4, sparse, acc, t, rho, rho64, qscale, c.z, ox.z,
-                                          oy.z, oz.z, ux.z, uy.z, uz.z, bad, strays, a);
-            pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E4, sparse, acc, t, rho, rho64, qscale, c.w, ox.w,
-                                          oy.w, oz.w, ux.w, uy.w, uz.w, bad, strays, a);
-            __stcs(reinterpret_cast<int4 *>(ps.cell) + q, c);
-            __stcs(reinterpret_cast<float4 *>(ps.o[0]) + q, ox);
-            __stcs(reinterpret_cast<float4 *>(ps.o[1]) + q, oy);
-            __stcs(reinterpret_cast<float4 *>(ps.o[2]) + q, oz);
-            __stcs(reinterpret_cast<float4 *>(ps.v[0]) + q, ux);
-            __stcs(reinterpret_cast<float4 *>(ps.v[1]) + q, uy);
-            __stcs(reinterpret_cast<float4 *>(ps.v[2]) + q, uz);
-        }
-        // head [item.y, 4 q0) and tail [4 q1, item.z); when the item lies
-        // inside one group (q0 > q1) the head covers all of it
-        const int head_end = min(4 * q0, item.z);
-        const int tail_beg = max(4 * q1, head_end);
-        const int nh = head_end - item.y, nt = item.z - tail_beg;
-        if ((int)threadIdx.x < nh + nt) {
-            const int p = (int)threadIdx.x < nh ? item.y + (int)threadIdx.x
-                                                : tail_beg + ((int)threadIdx.x - nh);
-            int32_t c = ps.cell[p];
-            float fx = ps.o[0][p], fy = ps.o[1][p], fz = ps.o[2][p];
-            float vx = ps.v[0][p], vy = ps.v[1][p], vz = ps.v[2][p];
-            pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E4, sparse, acc, t, rho, rho64, qscale, c, fx, fy,
+        // one particle per thread and iteration (coalesced 4-byte streams)
+        for (int p = item.y + threadIdx.x; p < item.z; p += blockDim.x) {
+            int32_t c = __ldcs(ps.cell + p);
+            float fx = __ldcs(ps.o[0] + p), fy = __ldcs(ps.o[1] + p), fz = __ldcs(ps.o[2] + p);
+            float vx = __ldcs(ps.v[0] + p), vy = __ldcs(ps.v[1] + p), vz = __ldcs(ps.v[2] + p);
+            pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E8, sparse, acc, t, rho, rho64, qscale, c, fx, fy,
                                           fz, vx, vy, vz, bad, strays, a);
-            ps.cell[p] = c;
-            ps.o[0][p] = fx;
-            ps.o[1][p] = fy;
-            ps.o[2][p] = fz;
-            ps.v[0][p] = vx;
-            ps.v[1][p] = vy;
-            ps.v[2][p] = vz;
+            __stcs(ps.cell + p, c);
+            __stcs(ps.o[0] + p, fx);
+            __stcs(ps.o[1] + p, fy);
+            __stcs(ps.o[2] + p, fz);
+            __stcs(ps.v[0] + p, vx);
+            __stcs(ps.v[1] + p, vy);
+            __stcs(ps.v[2] + p, vz);
         }
         if (!sparse) {
             __syncthreads();
@@ -324,6 +291,46 @@ cudaError_t launch_load(const double *x, const double *v, int64_t m, int64_t bas
     return cudaGetLastError();
 }
 
+// Device-to-device copy of up to 8 arrays in one launch (16-byte vectors; the
+// byte tail of each array by the first threads).  Copies inside the arena run
+// on the SMs at HBM speed rather than through a copy engine.
+__global__ void __launch_bounds__(256) k_copy(CopyList cl) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int a = 0; a < cl.count; ++a) {
+        const int64_t n16 = cl.bytes[a] >> 4;
+        const uint4 *src = reinterpret_cast<const uint4 *>(cl.src[a]);
+        uint4 *dst = reinterpret_cast<uint4 *>(cl.dst[a]);
+        for (int64_t q = t0; q < n16; q += stride) dst[q] = src[q];
+        const int64_t rem = cl.bytes[a] & 15;
+        if (t0 < rem) cl.dst[a][(n16 << 4) + t0] = cl.src[a][(n16 << 4) + t0];
+    }
+}
+
+cudaError_t launch_copy(const CopyList &cl, cudaStream_t st) {
+    int64_t total = 0;
+    for (int a = 0; a < cl.count; ++a) {
+        if ((reinterpret_cast<uintptr_t>(cl.dst[a]) | reinterpret_cast<uintptr_t>(cl.src[a])) & 15)
+            return cudaErrorMisalignedAddress;
+        total += cl.bytes[a] >> 4;
+    }
+    if (total == 0 && cl.count == 0) return cudaSuccess;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 8));
+    k_copy<<<blocks, 256, 0, st>>>(cl);
+    return cudaGetLastError();
+}
+
+__global__ void k_pid_positions(int64_t n, const int32_t *__restrict__ pid, int32_t *pos) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) pos[pid[p]] = (int32_t)p;
+}
+
+cudaError_t launch_pid_positions(int64_t n, const int32_t *pid, int32_t *pos, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_pid_positions<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, pid, pos);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_invperm(int64_t n, Ctrl *ctrl, int32_t *inv, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int T = 256;
@@ -342,11 +349,11 @@ cudaError_t launch_unload(int64_t o0, int64_t m, const int32_t *inv, const Geom 
 }
 
 cudaError_t launch_gather_push(int64_t n, const Geom &g, const PushConst &pc, bool diag,
-                               Ctrl *ctrl, const float4 *E4, double *part, int blocks,
+                               Ctrl *ctrl, const float4 *E8, double *part, int blocks,
                                int threads, cudaStream_t st) {
     const bool ext = pc.wz2 != 0.0f;
     const bool mag = pc.t[0] != 0.0f || pc.t[1] != 0.0f || pc.t[2] != 0.0f;
-#define PIC_GP(D, X, M) k_gather_push<D, X, M><<<blocks, threads, 0, st>>>(n, g, pc, ctrl, E4, part)
+#define PIC_GP(D, X, M) k_gather_push<D, X, M><<<blocks, threads, 0, st>>>(n, g, pc, ctrl, E8, part)
     if (diag) {
         if (ext) { if (mag) PIC_GP(true, true, true); else PIC_GP(true, true, false); }
         else     { if (mag) PIC_GP(true, false, true); else PIC_GP(true, false, false); }
@@ -362,26 +369,46 @@ cudaError_t launch_gather_push(int64_t n, const Geom &g, const PushConst &pc, bo
 
 namespace pic {
 
+size_t push_deposit_smem(const Geom &g) {
+    const cic::Tile t0 = cic::tile_of(g, 0);
+    return sizeof(uint32_t) * (size_t)t0.S;   // the deposit tile
+}
+
+// Allow the fused kernel's shared memory (call outside any stream capture)
+cudaError_t push_deposit_prepare(const Geom &g) {
+    const size_t smem = push_deposit_smem(g);
+    if (smem <= 48 * 1024) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+#define PIC_PDA(D, X, M, F)                                                                   \
+    if ((e = cudaFuncSetAttribute(k_push_deposit<D, X, M, F>,                                 \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != \
+        cudaSuccess)                                                                          \
+        return e
+    PIC_PDA(false, false, false, false); PIC_PDA(false, false, false, true);
+    PIC_PDA(false, false, true, false);  PIC_PDA(false, false, true, true);
+    PIC_PDA(false, true, false, false);  PIC_PDA(false, true, false, true);
+    PIC_PDA(false, true, true, false);   PIC_PDA(false, true, true, true);
+    PIC_PDA(true, false, false, false);  PIC_PDA(true, false, false, true);
+    PIC_PDA(true, false, true, false);   PIC_PDA(true, false, true, true);
+    PIC_PDA(true, true, false, false);   PIC_PDA(true, true, false, true);
+    PIC_PDA(true, true, true, false);    PIC_PDA(true, true, true, true);
+#undef PIC_PDA
+    return cudaSuccess;
+}
+
 cudaError_t launch_push_deposit(const Geom &g, const PushConst &pc, bool diag, bool fixed,
-                                Ctrl *ctrl, const int4 *items, int max_items, const float4 *E4,
+                                Ctrl *ctrl, const int4 *items, int max_items, const float4 *E8,
                                 float *rho, unsigned long long *rho64, double qscale,
                                 int sparse_below, double *part, int blocks, cudaStream_t st) {
     const bool ext = pc.wz2 != 0.0f;
     const bool mag = pc.t[0] != 0.0f || pc.t[1] != 0.0f || pc.t[2] != 0.0f;
-    const cic::Tile t0 = cic::tile_of(g, 0);
-    const size_t smem = sizeof(uint32_t) * (size_t)t0.S;
+    const size_t smem = push_deposit_smem(g);
     const int nb = std::max(1, std::min(blocks, max_items));
     const float qs = (float)qscale;
     cudaError_t e = cudaSuccess;
 #define PIC_PD(D, X, M, F)                                                                      \
-    do {                                                                                        \
-        auto kern = k_push_deposit<D, X, M, F>;                                                 \
-        if (smem > 48 * 1024 &&                                                                 \
-            (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
-                                      (int)smem)) != cudaSuccess)                               \
-            return e;                                                                           \
-        kern<<<nb, 256, smem, st>>>(g, pc, ctrl, items, E4, rho, rho64, qs, sparse_below, part); \
-    } while (0)
+    k_push_deposit<D, X, M, F><<<nb, 256, smem, st>>>(g, pc, ctrl, items, E8, rho, rho64, qs,   \
+                                                      sparse_below, part)
 #define PIC_PD_F(D, X, M) \
     do { if (fixed) PIC_PD(D, X, M, true); else PIC_PD(D, X, M, false); } while (0)
     if (diag) {

@@ -48,7 +48,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Byte offsets of every device buffer inside the caller's arena.
 struct Layout {
-    size_t ctrl, sets, rho, rho64, rho_hat, E_hat, E4, bins, scan_tmp, tile_items, tile_range,
+    size_t ctrl, sets, rho, rho64, rho_hat, E_hat, E4, E8, bins, scan_tmp, tile_items, tile_range,
         items, fpart, ppart, ring, inv, stage_x, stage_v, adjE4, fft, total;
     size_t set_stride;   // bytes of one per-particle array
 };
@@ -85,11 +85,10 @@ struct pic_ctx {
     // state of the last pic_adjoint_forward
     struct {
         bool ready;
-        int n_steps, K, nseg, cur;
+        int n_steps, K, nseg, cur, cur_end;
         double w[3];
         char *buf;
         int64_t step0;
-        int since0;
         long long step0_dev;
     } adj;
     // phase timers: a ring of event pairs per phase, drained when it wraps
@@ -196,6 +195,7 @@ void compute_layout(pic_ctx *c) {
     L.rho_hat = take((size_t)c->nhalf * 8);
     L.E_hat = take((size_t)c->nhalf * 8 * 3);
     L.E4 = take((size_t)c->ng * 16);
+    L.E8 = take((size_t)c->ng * 32);
     L.bins = take((size_t)(c->nbins + 1) * 4);
     const int64_t scan_n = std::max(c->nbins, c->ntiles);
     L.scan_tmp = take((size_t)((scan_n + 4095) / 4096 + 2) * 4);
@@ -331,14 +331,15 @@ int do_solve(pic_ctx *c) {
     PIC_CUDA(launch_green(c->geom, c->L, c->at<float2>(c->lay.rho_hat), c->at<float2>(c->lay.E_hat),
                           c->nhalf, c->mode_idx, c->prm.mode_comp, c->mode_conj, c->ctrl(), c->st));
     PIC_CUFFT(cufftExecC2R(c->c2r, c->at<cufftComplex>(c->lay.E_hat), c->at<cufftReal>(c->lay.E4)));
-    return timer_end(c, PIC_PHASE_SOLVE, 1);
+    PIC_CUDA(launch_pair_E(c->geom, c->at<float4>(c->lay.E4), c->at<float4>(c->lay.E8), c->st));
+    return timer_end(c, PIC_PHASE_SOLVE, 2);
 }
 
 int do_gather_push(pic_ctx *c, bool diag) {
     int r = timer_begin(c, PIC_PHASE_PUSH);
     if (r) return r;
     PIC_CUDA(launch_gather_push(c->np, c->geom, push_const(c), diag, c->ctrl(),
-                                c->at<float4>(c->lay.E4), c->at<double>(c->lay.ppart),
+                                c->at<float4>(c->lay.E8), c->at<double>(c->lay.ppart),
                                 push_blocks_of(c), c->block, c->st));
     c->step += 1;
     c->since_sort += 1;
@@ -364,7 +365,8 @@ int do_diag_finalize(pic_ctx *c, int push_blocks) {
 }
 
 int fused_blocks_of(const pic_ctx *c) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(c->max_items, std::min(kMaxPushBlocks, 152 * 3 * 2)));
+    return (int)std::max<int64_t>(
+        1, std::min<int64_t>(c->max_items, std::min(kMaxPushBlocks, 152 * PIC_PD_MIN_BLOCKS * 2)));
 }
 
 // gather + push + deposit of the new positions in one kernel (pic_step)
@@ -377,14 +379,14 @@ int do_push_deposit(pic_ctx *c, bool diag) {
     if (c->np > 0) {
         PIC_CUDA(launch_push_deposit(c->geom, push_const(c), diag, fixed, c->ctrl(),
                                      c->at<int4>(c->lay.items), (int)c->max_items,
-                                     c->at<float4>(c->lay.E4), c->at<float>(c->lay.rho),
+                                     c->at<float4>(c->lay.E8), c->at<float>(c->lay.rho),
                                      c->at<unsigned long long>(c->lay.rho64), qscale_of(c),
                                      c->sparse_below, c->at<double>(c->lay.ppart),
                                      fused_blocks_of(c), c->st));
     } else {
         // nothing to push: the plain kernel still records zero moments and the step
         PIC_CUDA(launch_gather_push(0, c->geom, push_const(c), diag, c->ctrl(),
-                                    c->at<float4>(c->lay.E4), c->at<double>(c->lay.ppart), 1,
+                                    c->at<float4>(c->lay.E8), c->at<double>(c->lay.ppart), 1,
                                     c->block, c->st));
     }
     c->step += 1;
@@ -394,56 +396,207 @@ int do_push_deposit(pic_ctx *c, bool diag) {
 }
 
 // ---- adjoint buffer layout (caller-owned device memory) ---------------------
+// The forward sweep re-bins the particles at the start of every segment of K
+// steps (a checkpoint) and every R steps inside it (R = the re-binning period),
+// so the tiled kernels always see tile-ordered particles.  Each re-binning
+// starts a new particle order; an "order record" keeps its pid array and work
+// items.  Buffer:
+//   checkpoints [n_ckpt]: cell, o[3], v[3], pid (order record 0), items, n_items
+//   per-step store [K]  : cell, o[3] and E4 of each step of the segment being
+//                         reversed
+//   order records [nrec - 1]: pid, items, n_items of records 1.. of that segment
+//   multiplier backup   : ly[3], lv[3] while a segment is recomputed/permuted
 struct AdjLayout {
-    size_t arr, ckpt, segy, segE, n_ckpt, off_segy, off_segE, total;
+    size_t arr, items, ckpt, segy, segE, rec, n_ckpt, off_items, off_nitems;
+    size_t off_segy, off_segE, off_rec, off_lam, total;
+    int R, nrec;
 };
 
 AdjLayout adj_layout(const pic_ctx *c, int n_steps, int K) {
     AdjLayout L;
     L.arr = align_up((size_t)std::max<int64_t>(c->cap, 1) * 4);
-    L.ckpt = 7 * L.arr;                       // cell, o[3], v[3]
+    L.items = align_up((size_t)c->max_items * 16);
+    L.off_items = 8 * L.arr;
+    L.off_nitems = L.off_items + L.items;
+    L.ckpt = L.off_nitems + kAlign;
     L.segy = 4 * L.arr;                       // cell, o[3]
     L.segE = align_up((size_t)c->ng * 16);    // E4 of one step
+    L.rec = L.arr + L.items + kAlign;         // pid, items, n_items
+    L.R = std::max(1, std::min(c->prm.sort_period > 0 ? c->prm.sort_period : K, K));
+    L.nrec = (K + L.R - 1) / L.R;
     const int nseg = n_steps > 1 ? (n_steps - 1 + K - 1) / K : 0;
     L.n_ckpt = (size_t)std::max(nseg, 1);
     L.off_segy = L.n_ckpt * L.ckpt;
     L.off_segE = L.off_segy + (size_t)K * L.segy;
-    L.total = L.off_segE + (size_t)K * L.segE;
+    L.off_rec = L.off_segE + (size_t)K * L.segE;
+    L.off_lam = L.off_rec + (size_t)(L.nrec - 1) * L.rec;
+    L.total = L.off_lam + 6 * L.arr;
     return L;
 }
 
+// `count` (<= 8) particle arrays of np 4-byte entries, in one copy kernel
 int copy_arrays(pic_ctx *c, char *const dst[], char *const src[], int count) {
     const size_t bytes = (size_t)c->np * 4;
     if (bytes == 0) return PIC_OK;
-    for (int q = 0; q < count; ++q)
-        PIC_CUDA(cudaMemcpyAsync(dst[q], src[q], bytes, cudaMemcpyDeviceToDevice, c->st));
+    CopyList cl{};
+    cl.count = count;
+    for (int q = 0; q < count; ++q) {
+        cl.dst[q] = dst[q];
+        cl.src[q] = src[q];
+        cl.bytes[q] = (int64_t)bytes;
+    }
+    PIC_CUDA(launch_copy(cl, c->st));
     return PIC_OK;
 }
 
-void set_arrays(const ParticleSet &s, char *out[7]) {
+int copy_bytes(pic_ctx *c, void *dst, const void *src, size_t bytes) {
+    if (bytes == 0) return PIC_OK;
+    PIC_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->st));
+    return PIC_OK;
+}
+
+void set_arrays(const ParticleSet &s, char *out[8]) {
     out[0] = reinterpret_cast<char *>(s.cell);
     for (int d = 0; d < 3; ++d) {
         out[1 + d] = reinterpret_cast<char *>(s.o[d]);
         out[4 + d] = reinterpret_cast<char *>(s.v[d]);
     }
+    out[7] = reinterpret_cast<char *>(s.pid);
 }
 
 void buf_arrays(char *base, size_t arr, int count, char *out[]) {
     for (int q = 0; q < count; ++q) out[q] = base + (size_t)q * arr;
 }
 
-int adj_save(pic_ctx *c, const AdjLayout &L, int slot) {
-    char *dst[7], *src[7];
-    buf_arrays(c->adj.buf + (size_t)slot * L.ckpt, L.arr, 7, dst);
-    set_arrays(c->hsets[c->adj.cur], src);
-    return copy_arrays(c, dst, src, 7);
+// order record r of the current segment (r = 0: the segment's checkpoint)
+struct OrderRec {
+    char *pid, *items, *nitems;
+};
+OrderRec order_rec(const pic_ctx *c, const AdjLayout &L, int seg, int r) {
+    OrderRec o;
+    if (r == 0) {
+        char *base = c->adj.buf + (size_t)seg * L.ckpt;
+        o.pid = base + 7 * L.arr;
+        o.items = base + L.off_items;
+        o.nitems = base + L.off_nitems;
+    } else {
+        char *base = c->adj.buf + L.off_rec + (size_t)(r - 1) * L.rec;
+        o.pid = base;
+        o.items = base + L.arr;
+        o.nitems = base + L.arr + L.items;
+    }
+    return o;
 }
 
-int adj_restore(pic_ctx *c, const AdjLayout &L, int slot) {
-    char *dst[7], *src[7];
-    buf_arrays(c->adj.buf + (size_t)slot * L.ckpt, L.arr, 7, src);
-    set_arrays(c->hsets[c->adj.cur], dst);
-    return copy_arrays(c, dst, src, 7);
+// current set's pid and work items -> order record
+int adj_record(pic_ctx *c, const AdjLayout &L, int seg, int rec, int cur) {
+    const OrderRec o = order_rec(c, L, seg, rec);
+    int r;
+    if ((r = copy_bytes(c, o.pid, c->hsets[cur].pid, (size_t)c->np * 4)) ||
+        (r = copy_bytes(c, o.items, c->at<char>(c->lay.items), (size_t)c->max_items * 16)) ||
+        (r = copy_bytes(c, o.nitems, &c->ctrl()->n_items, sizeof(int))))
+        return r;
+    return PIC_OK;
+}
+
+// work items of an order record -> the live work items
+int adj_use_items(pic_ctx *c, const AdjLayout &L, int seg, int rec) {
+    const OrderRec o = order_rec(c, L, seg, rec);
+    int r;
+    if ((r = copy_bytes(c, c->at<char>(c->lay.items), o.items, (size_t)c->max_items * 16)) ||
+        (r = copy_bytes(c, &c->ctrl()->n_items, o.nitems, sizeof(int))))
+        return r;
+    return PIC_OK;
+}
+
+// checkpoint `seg` <-> the current particle set (with order record 0)
+int adj_save(pic_ctx *c, const AdjLayout &L, int seg, int cur) {
+    char *dst[8], *src[8];
+    buf_arrays(c->adj.buf + (size_t)seg * L.ckpt, L.arr, 7, dst);
+    set_arrays(c->hsets[cur], src);
+    int r = copy_arrays(c, dst, src, 7);
+    return r ? r : adj_record(c, L, seg, 0, cur);
+}
+
+int adj_restore(pic_ctx *c, const AdjLayout &L, int seg, int cur) {
+    char *dst[8], *src[8];
+    buf_arrays(c->adj.buf + (size_t)seg * L.ckpt, L.arr, 8, src);
+    set_arrays(c->hsets[cur], dst);
+    int r = copy_arrays(c, dst, src, 8);
+    return r ? r : adj_use_items(c, L, seg, 0);
+}
+
+// positions (cell, o) and field of step `slot` of the segment being reversed
+int adj_keep_y(pic_ctx *c, const AdjLayout &L, int slot, int cur) {
+    char *dst[4], *src[8];
+    buf_arrays(c->adj.buf + L.off_segy + (size_t)slot * L.segy, L.arr, 4, dst);
+    set_arrays(c->hsets[cur], src);
+    return copy_arrays(c, dst, src, 4);
+}
+
+int adj_keep_E(pic_ctx *c, const AdjLayout &L, int slot) {
+    CopyList cl{};
+    cl.count = 1;
+    cl.dst[0] = c->adj.buf + L.off_segE + (size_t)slot * L.segE;
+    cl.src[0] = c->at<char>(c->lay.E4);
+    cl.bytes[0] = c->ng * 16;
+    PIC_CUDA(launch_copy(cl, c->st));
+    return PIC_OK;
+}
+
+// Re-bin; *cur follows the particles (the sort moves a non-empty store to the
+// other set, which is also where the multipliers live: back them up first
+// when they are live).
+int adj_rebin(pic_ctx *c, int *cur) {
+    int r = do_sort(c);
+    if (r) return r;
+    if (c->np > 0) *cur = 1 - *cur;
+    return PIC_OK;
+}
+
+// multipliers (ly, lv: o[], v[] of the set that is not current) <-> backup
+int adj_lam_backup(pic_ctx *c, const AdjLayout &L, int cur, bool to_backup) {
+    const ParticleSet &ls = c->hsets[1 - cur];
+    char *lam[6] = {reinterpret_cast<char *>(ls.o[0]), reinterpret_cast<char *>(ls.o[1]),
+                    reinterpret_cast<char *>(ls.o[2]), reinterpret_cast<char *>(ls.v[0]),
+                    reinterpret_cast<char *>(ls.v[1]), reinterpret_cast<char *>(ls.v[2])};
+    char *bk[6];
+    buf_arrays(c->adj.buf + L.off_lam, L.arr, 6, bk);
+    return to_backup ? copy_arrays(c, bk, lam, 6) : copy_arrays(c, lam, bk, 6);
+}
+
+// Multipliers held in the backup in the order given by pid_later -> the live
+// multiplier arrays in the order given by pid_earlier (same particles).
+int adj_permute_from_backup(pic_ctx *c, const AdjLayout &L, int cur, const int32_t *pid_later,
+                            const int32_t *pid_earlier) {
+    if (c->np <= 0) return PIC_OK;
+    int32_t *pos = c->at<int32_t>(c->lay.inv);
+    const ParticleSet &ls = c->hsets[1 - cur];
+    char *bk[6];
+    buf_arrays(c->adj.buf + L.off_lam, L.arr, 6, bk);
+    const float *in_o[3] = {reinterpret_cast<float *>(bk[0]), reinterpret_cast<float *>(bk[1]),
+                            reinterpret_cast<float *>(bk[2])};
+    const float *in_v[3] = {reinterpret_cast<float *>(bk[3]), reinterpret_cast<float *>(bk[4]),
+                            reinterpret_cast<float *>(bk[5])};
+    float *out_o[3] = {ls.o[0], ls.o[1], ls.o[2]};
+    float *out_v[3] = {ls.v[0], ls.v[1], ls.v[2]};
+    PIC_CUDA(launch_pid_positions(c->np, pid_later, pos, c->st));
+    PIC_CUDA(launch_adj_reorder(c->np, pos, pid_earlier, in_o, in_v, out_o, out_v, c->st));
+    return PIC_OK;
+}
+
+// One forward step of a sweep that keeps its trajectory: re-bin when an order
+// starts here (recording it), keep y_n, solve, keep E_n, push + deposit.
+int adj_keep_step(pic_ctx *c, const AdjLayout &L, int seg, int a0, int n, int *cur) {
+    int r;
+    if (n > a0 && (n - a0) % L.R == 0) {
+        if ((r = adj_rebin(c, cur)) || (r = adj_record(c, L, seg, (n - a0) / L.R, *cur)))
+            return r;
+    }
+    if ((r = adj_keep_y(c, L, n - a0, *cur))) return r;
+    if (!c->rho_current && (r = do_deposit(c))) return r;
+    if ((r = do_solve(c)) || (r = adj_keep_E(c, L, n - a0))) return r;
+    return do_push_deposit(c, false);
 }
 
 int adj_solve(pic_ctx *c) {
@@ -541,6 +694,11 @@ int pic_create(const pic_grid_t *grid, const pic_species_t *species, const pic_p
     c->dV = c->h[0] * c->h[1] * c->h[2];
     c->ntiles = nt;
     c->nbins = nt;    // the binning key is the deposit tile
+    if (push_deposit_smem(g) > kMaxSmemPerBlock) {
+        delete c;
+        return fail(PIC_ERR_ARG, "deposit tile plus guard too large for shared memory "
+                                 "(%zu bytes > %d)", push_deposit_smem(g), kMaxSmemPerBlock);
+    }
     if (c->nbins > 2147483647LL - 1) {
         delete c;
         return fail(PIC_ERR_ARG, "too many tiles for this grid");
@@ -611,6 +769,7 @@ int pic_bind_workspace(pic_handle_t c, void *arena, size_t bytes, void *stream) 
     }
 
     PIC_CUDA(sort_prepare());
+    PIC_CUDA(push_deposit_prepare(c->geom));
     Ctrl h;
     memset(&h, 0, sizeof(h));
     for (int s = 0; s < 2; ++s) {
@@ -847,17 +1006,30 @@ int pic_adjoint_forward(pic_handle_t c, int n_steps, int K, const double *w, voi
     c->adj.cur = cur;
     c->adj.buf = static_cast<char *>(buf);
     c->adj.step0 = c->step;
-    c->adj.since0 = c->since_sort;
     for (int d = 0; d < 3; ++d) c->adj.w[d] = w[d];
-    if (c->adj.nseg == 0 && (r = adj_save(c, L, 0))) return r;
-    for (int s = 0; s < c->adj.nseg; ++s) {
-        if ((r = adj_save(c, L, s))) return r;
+    // checkpoint s holds the state at step s K, re-binned so that the
+    // segment's tiled kernels (forward and reverse) see tile-ordered particles
+    // The last segment's positions, fields and orders are kept as they are
+    // computed, so the reverse sweep starts without recomputing it (with
+    // K >= n_steps - 1 nothing is recomputed at all).
+    const int nck = (int)L.n_ckpt;
+    for (int s = 0; s < nck; ++s) {
+        if ((r = adj_rebin(c, &cur)) || (r = adj_save(c, L, s, cur))) return r;
         const int a0 = s * K, b0 = std::min(a0 + K, n_steps - 1);
+        const bool keep = s == c->adj.nseg - 1;
         for (int n = a0; n < b0; ++n) {
-            if ((r = do_deposit(c)) || (r = do_solve(c)) || (r = do_gather_push(c, false))) return r;
+            if (keep) {
+                if ((r = adj_keep_step(c, L, s, a0, n, &cur))) return r;
+                continue;
+            }
+            if (n > a0 && (n - a0) % L.R == 0 && (r = adj_rebin(c, &cur))) return r;
+            if (!c->rho_current && (r = do_deposit(c))) return r;
+            if ((r = do_solve(c)) || (r = do_push_deposit(c, false))) return r;
         }
     }
-    if ((r = do_deposit(c)) || (r = do_solve(c))) return r;
+    c->adj.cur_end = cur;
+    if (!c->rho_current && (r = do_deposit(c))) return r;
+    if ((r = do_solve(c))) return r;
     PIC_CUDA(launch_diag_field(c->geom, c->at<float>(c->lay.rho), c->at<float4>(c->lay.E4),
                                c->at<double>(c->lay.fpart), c->st));
     PIC_CUDA(launch_objective(c->at<double>(c->lay.fpart), kDiagFieldBlocks, c->dV, c->adj.w,
@@ -875,39 +1047,47 @@ int pic_adjoint_backward(pic_handle_t c, double scale, double *gx, double *gv, i
     if (c->np > 0 && (!gx || !gv)) return fail(PIC_ERR_ARG, "null output array");
     const AdjLayout L = adj_layout(c, c->adj.n_steps, c->adj.K);
     const int K = c->adj.K;
+    int cur = c->adj.cur_end;
     const float qsc = (float)qscale_of(c);
     const float c_kick = (float)(c->prm.dt * c->sp.q_over_m);
     const float dt = (float)c->prm.dt, wz2 = (float)c->prm.wz2;
-    const ParticleSet &cs = c->hsets[c->adj.cur];
-    const float *cyo[3] = {cs.o[0], cs.o[1], cs.o[2]};
     float4 *lE4 = c->at<float4>(c->lay.adjE4);
     const size_t lE_bytes = (size_t)c->ng * 16;
+    float *lrho = c->at<float>(c->lay.rho);
 
     // terminal: lE = 2 h^3 w E of the final field, then (dD/dy)^T S^T
-    PIC_CUDA(launch_adj_zero(c->np, c->ctrl(), c->st));
-    const double seed[3] = {2.0 * c->dV * c->adj.w[0], 2.0 * c->dV * c->adj.w[1],
-                            2.0 * c->dV * c->adj.w[2]};
-    PIC_CUDA(launch_adj_seed(c->ng, c->at<float4>(c->lay.E4), lE4, seed, c->st));
-    if ((r = adj_solve(c))) return r;
-    PIC_CUDA(launch_adj_rho(c->np, c->geom, c->ctrl(), cs.cell, cyo, c->at<float>(c->lay.rho), qsc,
-                            c->st));
+    {
+        const ParticleSet &cs = c->hsets[cur];
+        const float *cyo[3] = {cs.o[0], cs.o[1], cs.o[2]};
+        PIC_CUDA(launch_adj_zero(c->np, c->ctrl(), c->st));
+        const double seed[3] = {2.0 * c->dV * c->adj.w[0], 2.0 * c->dV * c->adj.w[1],
+                                2.0 * c->dV * c->adj.w[2]};
+        PIC_CUDA(launch_adj_seed(c->ng, c->at<float4>(c->lay.E4), lE4, seed, c->st));
+        if ((r = adj_solve(c))) return r;
+        PIC_CUDA(launch_adj_rho(c->np, c->geom, c->ctrl(), cs.cell, cyo, lrho, qsc, c->st));
+    }
 
     for (int s = c->adj.nseg - 1; s >= 0; --s) {
-        if ((r = adj_restore(c, L, s))) return r;
         const int a0 = s * K, b0 = std::min(a0 + K, c->adj.n_steps - 1);
-        // recompute the segment, keeping each step's positions and field
-        for (int n = a0; n < b0; ++n) {
-            char *dst[4], *src[7];
-            buf_arrays(c->adj.buf + L.off_segy + (size_t)(n - a0) * L.segy, L.arr, 4, dst);
-            set_arrays(cs, src);
-            if ((r = copy_arrays(c, dst, src, 4))) return r;
-            if ((r = do_deposit(c)) || (r = do_solve(c))) return r;
-            PIC_CUDA(cudaMemcpyAsync(c->adj.buf + L.off_segE + (size_t)(n - a0) * L.segE,
-                                     c->at<char>(c->lay.E4), lE_bytes, cudaMemcpyDeviceToDevice,
-                                     c->st));
-            if ((r = do_gather_push(c, false))) return r;
+        if (s != c->adj.nseg - 1) {
+            // recompute the segment from its checkpoint, keeping each step's
+            // positions, field and particle order (the last segment was kept
+            // by the forward sweep); the multipliers, in checkpoint s + 1's
+            // order, wait in the backup while the re-binning uses their arrays
+            if ((r = adj_lam_backup(c, L, cur, true))) return r;
+            if ((r = adj_restore(c, L, s, cur))) return r;
+            c->rho_current = false;
+            for (int n = a0; n < b0; ++n)
+                if ((r = adj_keep_step(c, L, s, a0, n, &cur))) return r;
+            const int32_t *pid_next =
+                reinterpret_cast<const int32_t *>(order_rec(c, L, s + 1, 0).pid);
+            if ((r = adj_permute_from_backup(c, L, cur, pid_next, c->hsets[cur].pid))) return r;
         }
-        // reverse steps
+        // reverse steps.  The deposit term of step n is applied by the reverse
+        // push of step n - 1 (rt), or on its own where an order starts.
+        int rec = (b0 - 1 - a0) / L.R;
+        if (b0 > a0 && (r = adj_use_items(c, L, s, rec))) return r;
+        AdjRhoTerm rt{};
         for (int n = b0 - 1; n >= a0; --n) {
             char *y[4];
             buf_arrays(c->adj.buf + L.off_segy + (size_t)(n - a0) * L.segy, L.arr, 4, y);
@@ -919,13 +1099,36 @@ int pic_adjoint_backward(pic_handle_t c, double scale, double *gx, double *gv, i
                                                                 (size_t)(n - a0) * L.segE);
             PIC_CUDA(cudaMemsetAsync(lE4, 0, lE_bytes, c->st));
             PIC_CUDA(launch_adj_push(c->geom, c->ctrl(), c->at<int4>(c->lay.items),
-                                     (int)c->max_items, ycell, yo, En, lE4, c_kick, dt, wz2,
+                                     (int)c->max_items, ycell, yo, En, lE4, c_kick, dt, wz2, rt,
                                      c->ctrl(), c->st));
             if ((r = adj_solve(c))) return r;
-            PIC_CUDA(launch_adj_rho(c->np, c->geom, c->ctrl(), ycell, yo, c->at<float>(c->lay.rho),
-                                    qsc, c->st));
+            rt.cell = ycell;
+            for (int d = 0; d < 3; ++d) rt.o[d] = yo[d];
+            rt.lrho = lrho;
+            rt.sx = qsc * (float)c->inv_h[0];
+            rt.sy = qsc * (float)c->inv_h[1];
+            rt.sz = qsc * (float)c->inv_h[2];
+            if (rec > 0 && n == a0 + rec * L.R) {
+                // order `rec` began at this step: finish the step in it, then
+                // move the multipliers to the order before the re-binning
+                PIC_CUDA(launch_adj_rho(c->np, c->geom, c->ctrl(), rt.cell, rt.o, lrho, qsc, c->st));
+                rt = AdjRhoTerm{};
+                if ((r = adj_lam_backup(c, L, cur, true))) return r;
+                const int32_t *pid_l = reinterpret_cast<const int32_t *>(order_rec(c, L, s, rec).pid);
+                const int32_t *pid_e =
+                    reinterpret_cast<const int32_t *>(order_rec(c, L, s, rec - 1).pid);
+                if ((r = adj_permute_from_backup(c, L, cur, pid_l, pid_e))) return r;
+                --rec;
+                if ((r = adj_use_items(c, L, s, rec))) return r;
+            }
         }
+        if (rt.cell)
+            PIC_CUDA(launch_adj_rho(c->np, c->geom, c->ctrl(), rt.cell, rt.o, lrho, qsc, c->st));
     }
+
+    // The multipliers are now in the order of checkpoint 0: restore it (the
+    // state the forward sweep started from, re-binned, with its work items).
+    if ((r = adj_restore(c, L, 0, cur))) return r;
 
     // gradients in load order: dJ/dx0 = ly, dJ/dv0 = lv + dt/2 ly
     int32_t *inv = c->at<int32_t>(c->lay.inv);
@@ -941,12 +1144,11 @@ int pic_adjoint_backward(pic_handle_t c, double scale, double *gx, double *gv, i
             PIC_CUDA(cudaMemcpyAsync(gv + 3 * o, sv, (size_t)m * 24, cudaMemcpyDeviceToHost, c->st));
         }
     }
-    // back to the state the forward pass started from
-    if ((r = adj_restore(c, L, 0))) return r;
     PIC_CUDA(cudaMemcpyAsync(&c->ctrl()->step, &c->adj.step0_dev, sizeof(long long),
                              cudaMemcpyHostToDevice, c->st));
     c->step = c->adj.step0;
-    c->since_sort = c->adj.since0;
+    c->since_sort = 0;
+    c->adj.cur_end = cur;
     c->adj.ready = false;
     c->rho_current = false;
     PIC_CUDA(cudaStreamSynchronize(c->st));

@@ -85,6 +85,11 @@ struct PushConst {
 // Diagnostic partial layout: 4 doubles per block.
 constexpr int kDiagFieldBlocks = 512;
 constexpr int kMaxPushBlocks = 152 * 8;
+constexpr int kMaxSmemPerBlock = 227 * 1024;   // opt-in shared memory per block
+// resident blocks per SM the fused push + deposit kernel is compiled for
+#ifndef PIC_PD_MIN_BLOCKS
+#define PIC_PD_MIN_BLOCKS 4
+#endif
 constexpr int kMaxChunk = 4095;   // fixed-point tile slots stay below 2^32
 
 // Set the thread-local message returned by pic_last_error(); returns `code`.
@@ -117,13 +122,20 @@ cudaError_t launch_deposit(int64_t n, const Geom &g, const Ctrl *ctrl, const int
 
 cudaError_t launch_rho_finish(const Geom &g, unsigned long long *rho64, float *rho, double qscale,
                               cudaStream_t st);
+// dynamic shared memory of the fused push + deposit kernel for geometry g,
+// and the one-time attribute setting it needs above 48 KiB
+size_t push_deposit_smem(const Geom &g);
+cudaError_t push_deposit_prepare(const Geom &g);
+// E8: the x-paired field (launch_pair_E), 2 float4 per node
 cudaError_t launch_push_deposit(const Geom &g, const PushConst &pc, bool diag, bool fixed,
-                                Ctrl *ctrl, const int4 *items, int max_items, const float4 *E4,
+                                Ctrl *ctrl, const int4 *items, int max_items, const float4 *E8,
                                 float *rho, unsigned long long *rho64, double qscale,
                                 int sparse_below, double *part, int blocks, cudaStream_t st);
 cudaError_t launch_gather_push(int64_t n, const Geom &g, const PushConst &pc, bool diag,
-                               Ctrl *ctrl, const float4 *E4, double *part, int blocks,
+                               Ctrl *ctrl, const float4 *E8, double *part, int blocks,
                                int threads, cudaStream_t st);
+// E8[2q] = E4[q], E8[2q + 1] = E4[q + x (periodic)]
+cudaError_t launch_pair_E(const Geom &g, const float4 *E4, float4 *E8, cudaStream_t st);
 
 cudaError_t launch_green(const Geom &g, const double *L_d, const float2 *rho_hat,
                          float2 *E_hat, int64_t nhalf, const int *mode_idx, int mode_comp,
@@ -137,16 +149,45 @@ cudaError_t launch_diag_finalize(const double *field_part, const double *push_pa
 // adjoint (k_adjoint.cu)
 cudaError_t launch_adj_seed(int64_t ng, const float4 *E4, float4 *lE4, const double *scale3,
                             cudaStream_t st);
+// up to 8 device-to-device copies in one launch (pointers 16-byte aligned)
+struct CopyList {
+    int count;
+    char *dst[8];
+    const char *src[8];
+    int64_t bytes[8];
+};
+cudaError_t launch_copy(const CopyList &cl, cudaStream_t st);
+
+// The deposit term of the adjoint of one step, (dD/dy)^T lrho evaluated at
+// that step's positions (cell, o) and scaled by q/h_d, folded into the
+// reverse push of the step before it (cell == nullptr: no such term).
+struct AdjRhoTerm {
+    const int32_t *cell;
+    const float *o[3];
+    const float *lrho;
+    float sx, sy, sz;
+};
 cudaError_t launch_adj_push(const Geom &g, const Ctrl *ctrl, const int4 *items, int max_items,
                             const int32_t *ycell, const float *const yo[3], const float4 *E4,
-                            float4 *lE4, float c_kick, float dt, float wz2, Ctrl *ctrl_w,
-                            cudaStream_t st);
+                            float4 *lE4, float c_kick, float dt, float wz2, const AdjRhoTerm &rt,
+                            Ctrl *ctrl_w, cudaStream_t st);
 cudaError_t launch_green_adj(const Geom &g, const double *L_d, const float2 *lE_hat,
                              float2 *lrho_hat, int64_t nhalf, cudaStream_t st);
 cudaError_t launch_adj_rho(int64_t n, const Geom &g, const Ctrl *ctrl, const int32_t *ycell,
                            const float *const yo[3], const float *lrho, float qscale,
                            cudaStream_t st);
 cudaError_t launch_adj_zero(int64_t n, const Ctrl *ctrl, cudaStream_t st);
+struct ReorderArgs {
+    const float *in_o[3];
+    const float *in_v[3];
+    float *out_o[3];
+    float *out_v[3];
+};
+cudaError_t launch_adj_reorder(int64_t n, const int32_t *pos, const int32_t *pid_prev,
+                               const float *const in_o[3], const float *const in_v[3],
+                               float *const out_o[3], float *const out_v[3], cudaStream_t st);
+// pos[pid[j]] = j for j < n (the inverse of a particle order)
+cudaError_t launch_pid_positions(int64_t n, const int32_t *pid, int32_t *pos, cudaStream_t st);
 cudaError_t launch_adj_unload(int64_t o0, int64_t m, const int32_t *inv, const Ctrl *ctrl,
                               double half_dt, double scale, double *gx, double *gv,
                               cudaStream_t st);

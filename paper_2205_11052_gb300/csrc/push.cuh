@@ -12,38 +12,79 @@
 
 namespace pic {
 
-template <bool EXT, bool MAG>
-__device__ __forceinline__ void push_one(const Geom &g, const PushConst &pc,
-                                         const float4 *__restrict__ E4, int32_t &c, float &fx,
-                                         float &fy, float &fz, float &vx, float &vy, float &vz,
-                                         int &bad) {
+// CIC interpolation of the eight corner values (corner bits a | b<<1 | c<<2)
+__device__ __forceinline__ void interp_E(const float4 e[8], float fx, float fy, float fz,
+                                        float &ex, float &ey, float &ez) {
+    const float wx1 = fx, wx0 = 1.0f - fx;
+    const float wy1 = fy, wy0 = 1.0f - fy;
+    const float wz1 = fz, wz0 = 1.0f - fz;
+    const float w00 = wy0 * wz0, w10 = wy1 * wz0, w01 = wy0 * wz1, w11 = wy1 * wz1;
+    ex = w00 * (wx0 * e[0].x + wx1 * e[1].x) + w10 * (wx0 * e[2].x + wx1 * e[3].x) +
+         w01 * (wx0 * e[4].x + wx1 * e[5].x) + w11 * (wx0 * e[6].x + wx1 * e[7].x);
+    ey = w00 * (wx0 * e[0].y + wx1 * e[1].y) + w10 * (wx0 * e[2].y + wx1 * e[3].y) +
+         w01 * (wx0 * e[4].y + wx1 * e[5].y) + w11 * (wx0 * e[6].y + wx1 * e[7].y);
+    ez = w00 * (wx0 * e[0].z + wx1 * e[1].z) + w10 * (wx0 * e[2].z + wx1 * e[3].z) +
+         w01 * (wx0 * e[4].z + wx1 * e[5].z) + w11 * (wx0 * e[6].z + wx1 * e[7].z);
+}
+
+// E at the particle from the grid in global memory (periodic stencil)
+__device__ __forceinline__ void gather_E_global(const Geom &g, const float4 *__restrict__ E4, int i,
+                                                int j, int k, float fx, float fy, float fz,
+                                                float &ex, float &ey, float &ez) {
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    int i = cell_i(c), j = cell_j(c), k = cell_k(c);
-    if (i >= nx || j >= ny || k >= nz) {   // never produced by the kernels
-        bad |= PIC_FLAG_BAD_CELL;
-        i = j = k = 0;
-    }
-    // CIC stencil nodes (periodic)
     const int i1 = (i + 1 == nx) ? 0 : i + 1;
     const int j1 = (j + 1 == ny) ? 0 : j + 1;
     const int k1 = (k + 1 == nz) ? 0 : k + 1;
     const int nxy = nx * ny;
     const int r00 = j * nx + k * nxy, r10 = j1 * nx + k * nxy;
     const int r01 = j * nx + k1 * nxy, r11 = j1 * nx + k1 * nxy;
-    const float4 e000 = __ldg(E4 + r00 + i), e100 = __ldg(E4 + r00 + i1);
-    const float4 e010 = __ldg(E4 + r10 + i), e110 = __ldg(E4 + r10 + i1);
-    const float4 e001 = __ldg(E4 + r01 + i), e101 = __ldg(E4 + r01 + i1);
-    const float4 e011 = __ldg(E4 + r11 + i), e111 = __ldg(E4 + r11 + i1);
-    const float wx1 = fx, wx0 = 1.0f - fx;
-    const float wy1 = fy, wy0 = 1.0f - fy;
-    const float wz1 = fz, wz0 = 1.0f - fz;
-    const float w00 = wy0 * wz0, w10 = wy1 * wz0, w01 = wy0 * wz1, w11 = wy1 * wz1;
-    float ex = w00 * (wx0 * e000.x + wx1 * e100.x) + w10 * (wx0 * e010.x + wx1 * e110.x) +
-               w01 * (wx0 * e001.x + wx1 * e101.x) + w11 * (wx0 * e011.x + wx1 * e111.x);
-    float ey = w00 * (wx0 * e000.y + wx1 * e100.y) + w10 * (wx0 * e010.y + wx1 * e110.y) +
-               w01 * (wx0 * e001.y + wx1 * e101.y) + w11 * (wx0 * e011.y + wx1 * e111.y);
-    float ez = w00 * (wx0 * e000.z + wx1 * e100.z) + w10 * (wx0 * e010.z + wx1 * e110.z) +
-               w01 * (wx0 * e001.z + wx1 * e101.z) + w11 * (wx0 * e011.z + wx1 * e111.z);
+    float4 e[8];
+    e[0] = __ldg(E4 + r00 + i);
+    e[1] = __ldg(E4 + r00 + i1);
+    e[2] = __ldg(E4 + r10 + i);
+    e[3] = __ldg(E4 + r10 + i1);
+    e[4] = __ldg(E4 + r01 + i);
+    e[5] = __ldg(E4 + r01 + i1);
+    e[6] = __ldg(E4 + r11 + i);
+    e[7] = __ldg(E4 + r11 + i1);
+    interp_E(e, fx, fy, fz, ex, ey, ez);
+}
+
+// E8 holds, per node q, E at q and at its +x neighbour (periodic): 32 bytes,
+// so each of the four (y, z) corner rows of the stencil is one aligned
+// 256-bit read-only load
+__device__ __forceinline__ void ld_pair(const float4 *p, float4 &a, float4 &b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
+__device__ __forceinline__ void gather_E_pairs(const Geom &g, const float4 *__restrict__ E8, int i,
+                                               int j, int k, float fx, float fy, float fz,
+                                               float &ex, float &ey, float &ez) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int j1 = (j + 1 == ny) ? 0 : j + 1;
+    const int k1 = (k + 1 == nz) ? 0 : k + 1;
+    const int nxy = nx * ny;
+    const int r00 = j * nx + k * nxy + i, r10 = j1 * nx + k * nxy + i;
+    const int r01 = j * nx + k1 * nxy + i, r11 = j1 * nx + k1 * nxy + i;
+    float4 e[8];
+    ld_pair(E8 + 2 * r00, e[0], e[1]);
+    ld_pair(E8 + 2 * r10, e[2], e[3]);
+    ld_pair(E8 + 2 * r01, e[4], e[5]);
+    ld_pair(E8 + 2 * r11, e[6], e[7]);
+    interp_E(e, fx, fy, fz, ex, ey, ez);
+}
+
+// Boris kick with the interpolated field (plus the external quadrupole), then
+// a full drift in cell units carried into the cell index and wrapped; (i, j, k)
+// is the particle's stencil base before the step
+template <bool EXT, bool MAG>
+__device__ __forceinline__ void kick_drift(const Geom &g, const PushConst &pc, float ex, float ey,
+                                           float ez, int i, int j, int k, int32_t &c, float &fx,
+                                           float &fy, float &fz, float &vx, float &vy, float &vz,
+                                           int &bad) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     if (EXT) {
         // quadrupole about the box centre at x in [0, L): (x - c)/h = i - N/2 +
         // 1/2 + f, wrapped into [-N/2, N/2) (a particle in [0, h/2) has its
@@ -97,6 +138,44 @@ __device__ __forceinline__ void push_one(const Geom &g, const PushConst &pc,
     if ((unsigned)j >= (unsigned)ny) { j %= ny; if (j < 0) j += ny; }
     if ((unsigned)k >= (unsigned)nz) { k %= nz; if (k < 0) k += nz; }
     c = pack_cell(i, j, k);
+}
+
+// stencil base of a packed cell (flagged and clamped to 0 if out of range)
+__device__ __forceinline__ void decode_base(const Geom &g, int32_t c, int &i, int &j, int &k,
+                                            int &bad) {
+    i = cell_i(c);
+    j = cell_j(c);
+    k = cell_k(c);
+    if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) {   // never produced by the kernels
+        bad |= PIC_FLAG_BAD_CELL;
+        i = j = k = 0;
+    }
+}
+
+// gather from the grid in global memory + kick + drift
+template <bool EXT, bool MAG>
+__device__ __forceinline__ void push_one(const Geom &g, const PushConst &pc,
+                                         const float4 *__restrict__ E4, int32_t &c, float &fx,
+                                         float &fy, float &fz, float &vx, float &vy, float &vz,
+                                         int &bad) {
+    int i, j, k;
+    decode_base(g, c, i, j, k, bad);
+    float ex, ey, ez;
+    gather_E_global(g, E4, i, j, k, fx, fy, fz, ex, ey, ez);
+    kick_drift<EXT, MAG>(g, pc, ex, ey, ez, i, j, k, c, fx, fy, fz, vx, vy, vz, bad);
+}
+
+// gather from the x-paired grid + kick + drift
+template <bool EXT, bool MAG>
+__device__ __forceinline__ void push_one_pairs(const Geom &g, const PushConst &pc,
+                                               const float4 *__restrict__ E8, int32_t &c,
+                                               float &fx, float &fy, float &fz, float &vx,
+                                               float &vy, float &vz, int &bad) {
+    int i, j, k;
+    decode_base(g, c, i, j, k, bad);
+    float ex, ey, ez;
+    gather_E_pairs(g, E8, i, j, k, fx, fy, fz, ex, ey, ez);
+    kick_drift<EXT, MAG>(g, pc, ex, ey, ez, i, j, k, c, fx, fy, fz, vx, vy, vz, bad);
 }
 
 }  // namespace pic

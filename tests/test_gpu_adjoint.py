@@ -2,8 +2,8 @@
 
 Tolerances: the GPU runs FP32 particles and grids, so gradients are compared
 at 1e-4 of their largest component against the oracle's discrete adjoint and
-against central differences of the oracle's objective (the spec bar
-for gradient accuracy); J itself to 1e-5.
+against central differences of the oracle's objective (the accuracy the GPU
+gradient is held to); J itself to 1e-5.
 """
 import numpy as np
 import pytest

@@ -101,3 +101,21 @@ def test_ensemble_step_replays_from_a_cuda_graph():
         assert _pos_err(xs[i], xo, w) <= 1e-4
         assert np.max(np.abs(vs[i] - vo)) <= 1e-4 * np.max(np.abs(vo))
     ens.close()
+
+
+def test_autotuner_picks_the_fastest_measured_setting():
+    from paper_2205_11052_gb300.autotune import Autotuner, tune_ensemble
+
+    ws = _members()
+    members = [(w.n, w.L, w.x, w.v, w.Q) for w in ws]
+    cache = {}
+    best, table = tune_ensemble(members, 0.05, space={"tile": [(8, 8, 8), (4, 4, 4)],
+                                                      "sort_period": [2], "options": [1]},
+                                warmup=1, steps=2, cache=cache)
+    assert len(table) == 2 and best == table[0][0]
+    assert table[0][1] <= table[1][1] and all(ms > 0 for _, ms in table)
+    assert tune_ensemble(members, 0.05, cache=cache)[0] == best      # served from the cache
+    tuner = Autotuner(space={"tile": [(8, 8, 8), (4, 4, 4)], "sort_period": [2], "options": [1]},
+                      warmup=1, steps=2)
+    cfg = tuner.tune(ws[0])
+    assert cfg in [r["cfg"] for r in next(iter(tuner.cache.values()))["table"]]

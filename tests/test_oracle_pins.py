@@ -257,6 +257,26 @@ def test_landau_damping_rate_and_frequency():
     assert abs(hist[-1]["Px"]) < 1e-9 * abs(w.Q)
 
 
+def test_bump_on_tail_growth_rate_on_a_quiet_lattice():
+    """Bump-on-tail (Section 4.2 family): electrons 0.9 N(0,1) + 0.1 N(4, 0.3^2),
+    seeded at k = 0.3 with alpha = 1e-3 on a quiet 1D lattice (32 cells,
+    64 x 512 particles).  The most strongly growing root fitted on t in
+    [5, 20] matches the two-Maxwellian dispersion root 0.92925 + 0.21093i."""
+    from tests.fits import fastest_root
+
+    w = pi.bump_on_tail_quiet(n=(32, 1, 1), L=2.0 * math.pi / 0.3, axis=0, m=1, alpha=1e-3,
+                              ms=64, mv=512)
+    grid = po.Grid(w.n, w.L)
+    p = po.Params(dt=w.dt, Q=w.Q, q_over_m=w.q_over_m)
+    _, _, hist = po.run(w.x, w.v, grid, p, 400)
+    t = np.array([d["t_field"] for d in hist])
+    c = np.array([d["mode"] for d in hist])
+    gamma, omega = fastest_root(t, c, 5.0, 20.0)
+    root = dispersion.root(0.3, 0.93 + 0.21j, species=((0.9, 0.0, 1.0), (0.1, 4.0, 0.3)))
+    assert gamma == pytest.approx(root.imag, rel=0.02)
+    assert omega == pytest.approx(root.real, rel=0.005)
+
+
 def test_diagnostics_field_energy_of_a_known_field():
     grid = po.Grid((8, 8, 8), (2.0, 2.0, 2.0))
     E = np.zeros((3,) + grid.shape)
