@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "cic.cuh"
+#include "push.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -37,6 +38,12 @@ __device__ __forceinline__ bool decode(int32_t c, const Geom &g, int &i, int &j,
     return true;
 }
 
+// warp-reduced maximum of a non-negative float, merged into *dst (float bits)
+__device__ __forceinline__ void max_to(unsigned int *dst, float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v > 0.0f) atomicMax(dst, __float_as_uint(v));
+}
+
 // the 8 corner nodes of cell (i, j, k), corner bits a | b<<1 | c<<2 (int32:
 // grids have at most 2^30 nodes)
 __device__ __forceinline__ void corners(int i, int j, int k, int nx, int ny, int nz, int nd[8]) {
@@ -47,6 +54,18 @@ __device__ __forceinline__ void corners(int i, int j, int k, int nx, int ny, int
     const int r01 = (j + ny * k1) * nx, r11 = (j1 + ny * k1) * nx;
     nd[0] = r00 + i; nd[1] = r00 + i1; nd[2] = r10 + i; nd[3] = r10 + i1;
     nd[4] = r01 + i; nd[5] = r01 + i1; nd[6] = r11 + i; nd[7] = r11 + i1;
+}
+
+// the 8 corner values of an x-paired scalar grid (v2[q] = (v[q], v[q + x])):
+// four aligned 8-byte loads, corner bits a | b<<1 | c<<2
+__device__ __forceinline__ void corners_from_pairs(const float2 *__restrict__ v2, int i, int j,
+                                                   int k, int nx, int ny, int nz, float sc[8]) {
+    const int j1 = (j + 1 == ny) ? 0 : j + 1;
+    const int k1 = (k + 1 == nz) ? 0 : k + 1;
+    const float2 a = __ldg(v2 + (j + ny * k) * nx + i), b = __ldg(v2 + (j1 + ny * k) * nx + i);
+    const float2 c = __ldg(v2 + (j + ny * k1) * nx + i), d = __ldg(v2 + (j1 + ny * k1) * nx + i);
+    sc[0] = a.x; sc[1] = a.y; sc[2] = b.x; sc[3] = b.y;
+    sc[4] = c.x; sc[5] = c.y; sc[6] = d.x; sc[7] = d.y;
 }
 
 // Gradient, with respect to the in-cell offsets (fx, fy, fz), of the CIC
@@ -91,18 +110,41 @@ __global__ void k_adj_seed(int64_t ng, const float4 *__restrict__ E4, float4 *__
 //
 // The gather term is the offset gradient (interp_grad) of the CIC
 // interpolation of s_abc = le . E at the 8 corners.
-__global__ void __launch_bounds__(256, 3) k_adj_push(Geom g, const Ctrl *__restrict__ ctrl,
+__global__ void __launch_bounds__(256, PIC_ADJ_MIN_BLOCKS) k_adj_push(Geom g, const Ctrl *__restrict__ ctrl,
                                                       const int4 *__restrict__ items,
                                                       const int32_t *__restrict__ ycell,
                                                       const float *__restrict__ yo0,
                                                       const float *__restrict__ yo1,
                                                       const float *__restrict__ yo2,
-                                                      const float4 *__restrict__ E4,
+                                                      const float4 *__restrict__ E8,
                                                       float4 *__restrict__ lE4, float c_kick,
                                                       float dt, float wz2, AdjRhoTerm rt,
-                                                      Ctrl *ctrl_w) {
-    extern __shared__ float acc[];   // 3 * S floats: x, y, z components
+                                                      AdjBound ab, Ctrl *ctrl_w) {
+    // 3 * S integer accumulators (x, y, z components) in units of 1 / qs
+    extern __shared__ int acc[];
     const int cur = ctrl->cur;
+    // |le| <= c (|lv| + dt (|ly| + kb |lrho|)) with the maxima left by the
+    // kernels that wrote lv, ly and lrho (read slot: the other parity); a node
+    // of an item gets at most 4095 contributions w |le| <= |le|, so
+    // qs = 2^(30 - e) with 4096 |le|max < 2^e keeps every sum below 2^30
+    const int rd = ab.par ^ 1;
+    const float m_ly = __uint_as_float(ctrl->adj_ly[rd]);
+    const float m_lv = __uint_as_float(ctrl->adj_lv[rd]);
+    const float m_rho = rt.cell ? __uint_as_float(ctrl->adj_lrho[rd]) : 0.0f;
+    const float m_le = ab.c_abs * (m_lv + ab.dt * (m_ly + ab.kb * m_rho));
+    float qs = 1073741824.0f;   // 2^30 when every |le| is 0
+    int nonfinite = 0;
+    if (!(m_le <= 3.0e38f)) {
+        nonfinite = 1;
+        qs = 1.0f;
+    } else if (m_le > 0.0f) {
+        int e;
+        frexpf(4096.0f * m_le, &e);
+        qs = ldexpf(1.0f, max(-120, min(120, 30 - e)));
+    }
+    const float inv_qs = 1.0f / qs;   // exact: a power of two
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl_w->adj_lrho[ab.par] = 0u;   // for this step's solve
+    float mly = 0.0f, mlv = 0.0f;
     const ParticleSet lam = ctrl->sets[1 - cur];   // ly in o[], lv in v[]
     const int n_items = ctrl->n_items;
     const int G = g.guard;
@@ -118,7 +160,7 @@ __global__ void __launch_bounds__(256, 3) k_adj_push(Geom g, const Ctrl *__restr
         const int tz = tile / (g.ntile[0] * g.ntile[1]);
         const int ox = tx * g.tile[0], oy = ty * g.tile[1], oz = tz * g.tile[2];
         const cic::Tile tb = cic::tile_of(g, tile);
-        for (int q = threadIdx.x; q < 3 * S; q += blockDim.x) acc[q] = 0.0f;
+        for (int q = threadIdx.x; q < 3 * S; q += blockDim.x) acc[q] = 0;
         __syncthreads();
         for (int p = item.y + threadIdx.x; p < item.z; p += blockDim.x) {
             int i, j, k;
@@ -128,11 +170,8 @@ __global__ void __launch_bounds__(256, 3) k_adj_push(Geom g, const Ctrl *__restr
                 // the deposit term (dD/dy)^T lrho of the step after this one
                 int ri, rj, rk;
                 decode(rt.cell[p], g, ri, rj, rk);
-                int rn[8];
-                corners(ri, rj, rk, nx, ny, nz, rn);
                 float rs[8];
-#pragma unroll
-                for (int cc = 0; cc < 8; ++cc) rs[cc] = __ldg(rt.lrho + rn[cc]);
+                corners_from_pairs(rt.lrho2, ri, rj, rk, nx, ny, nz, rs);
                 float rx, ry, rz;
                 interp_grad(rt.o[0][p], rt.o[1][p], rt.o[2][p], rs, rx, ry, rz);
                 ly0 += rt.sx * rx;
@@ -148,9 +187,11 @@ __global__ void __launch_bounds__(256, 3) k_adj_push(Geom g, const Ctrl *__restr
             corners(i, j, k, nx, ny, nz, nd);
             float sc[8];
 #pragma unroll
-            for (int cc = 0; cc < 8; ++cc) {
-                const float4 e = __ldg(E4 + nd[cc]);
-                sc[cc] = le0 * e.x + le1 * e.y + le2 * e.z;
+            for (int r = 0; r < 4; ++r) {
+                float4 e0, e1;
+                ld_pair(E8 + 2 * nd[2 * r], e0, e1);
+                sc[2 * r] = le0 * e0.x + le1 * e0.y + le2 * e0.z;
+                sc[2 * r + 1] = le0 * e1.x + le1 * e1.y + le2 * e1.z;
             }
             float dx, dy, dz;
             interp_grad(fx, fy, fz, sc, dx, dy, dz);
@@ -163,6 +204,8 @@ __global__ void __launch_bounds__(256, 3) k_adj_push(Geom g, const Ctrl *__restr
             lam.v[0][p] = lv0;
             lam.v[1][p] = lv1;
             lam.v[2][p] = lv2;
+            mly = fmaxf(mly, fmaxf(fabsf(ly0), fmaxf(fabsf(ly1), fabsf(ly2))));
+            mlv = fmaxf(mlv, fmaxf(fabsf(lv0), fmaxf(fabsf(lv1), fabsf(lv2))));
             // G^T le
             const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
             const float w[8] = {gx * gy * gz, fx * gy * gz, gx * fy * gz, fx * fy * gz,
@@ -173,11 +216,12 @@ __global__ void __launch_bounds__(256, 3) k_adj_push(Geom g, const Ctrl *__restr
             if (si >= 0 && sj >= 0 && sk >= 0) {
                 const int s = si + S0 * sj + S01 * sk;
                 const int off[8] = {0, 1, S0, S0 + 1, S01, S01 + 1, S01 + S0, S01 + S0 + 1};
+                const float q0 = qs * le0, q1 = qs * le1, q2 = qs * le2;
 #pragma unroll
                 for (int cc = 0; cc < 8; ++cc) {
-                    atomicAdd(acc + s + off[cc], w[cc] * le0);
-                    atomicAdd(acc + S + s + off[cc], w[cc] * le1);
-                    atomicAdd(acc + 2 * S + s + off[cc], w[cc] * le2);
+                    atomicAdd(acc + s + off[cc], __float2int_rn(w[cc] * q0));
+                    atomicAdd(acc + S + s + off[cc], __float2int_rn(w[cc] * q1));
+                    atomicAdd(acc + 2 * S + s + off[cc], __float2int_rn(w[cc] * q2));
                 }
             } else {
 #pragma unroll
@@ -187,8 +231,9 @@ __global__ void __launch_bounds__(256, 3) k_adj_push(Geom g, const Ctrl *__restr
         }
         __syncthreads();
         for (int q = threadIdx.x; q < S; q += blockDim.x) {
-            const float ax = acc[q], ay = acc[S + q], az = acc[2 * S + q];
-            if (ax != 0.0f || ay != 0.0f || az != 0.0f) {
+            const int ix = acc[q], iy = acc[S + q], iz = acc[2 * S + q];
+            if (ix != 0 || iy != 0 || iz != 0) {
+                const float ax = (float)ix * inv_qs, ay = (float)iy * inv_qs, az = (float)iz * inv_qs;
                 int a, b, cz;
                 cic::tile_pos(tb, q, a, b, cz);
                 const int gi = cic::wrap_index(ox - G + a, nx);
@@ -200,7 +245,10 @@ __global__ void __launch_bounds__(256, 3) k_adj_push(Geom g, const Ctrl *__restr
         }
         __syncthreads();
     }
+    max_to(&ctrl_w->adj_ly[ab.par], mly);
+    max_to(&ctrl_w->adj_lv[ab.par], mlv);
     if (bad) atomicOr(&ctrl_w->flags, PIC_FLAG_BAD_CELL);
+    if (nonfinite) atomicOr(&ctrl_w->flags, PIC_FLAG_NONFINITE);
 }
 
 // lrho^ = sum_d (+i g_d / |k|^2) lE^_d / N_g   (S^T, with the C2R 1/N_g folded in)
@@ -233,28 +281,41 @@ __global__ void k_green_adj(int nx, int ny, int nz, int nh, double tpx, double t
 }
 
 // ly += (q_p / h^3) sum_corner grad W lrho  ((dD/dy)^T lrho)
-__global__ void k_adj_rho(int64_t n, Geom g, const Ctrl *__restrict__ ctrl,
-                          const int32_t *__restrict__ ycell, const float *__restrict__ yo0,
-                          const float *__restrict__ yo1, const float *__restrict__ yo2,
-                          const float *__restrict__ lrho, float qscale) {
+// (with `out` given, the updated multipliers go there instead of in place:
+// ly + term to out.o, lv copied to out.v)
+__global__ void k_adj_rho(int64_t n, Geom g, Ctrl *ctrl, const int32_t *__restrict__ ycell,
+                          const float *__restrict__ yo0, const float *__restrict__ yo1,
+                          const float *__restrict__ yo2, const float2 *__restrict__ lrho2,
+                          float qscale, LamOut out, int par) {
     const ParticleSet lam = ctrl->sets[1 - ctrl->cur];
+    float mly = 0.0f;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const float sx = qscale * g.inv_h[0], sy = qscale * g.inv_h[1], sz = qscale * g.inv_h[2];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
         int i, j, k;
         decode(ycell[p], g, i, j, k);
-        int nd[8];
-        corners(i, j, k, nx, ny, nz, nd);
         float sc[8];
-#pragma unroll
-        for (int cc = 0; cc < 8; ++cc) sc[cc] = __ldg(lrho + nd[cc]);
+        corners_from_pairs(lrho2, i, j, k, nx, ny, nz, sc);
         float dx, dy, dz;
         interp_grad(yo0[p], yo1[p], yo2[p], sc, dx, dy, dz);
-        lam.o[0][p] += sx * dx;
-        lam.o[1][p] += sy * dy;
-        lam.o[2][p] += sz * dz;
+        const float ly0 = lam.o[0][p] + sx * dx, ly1 = lam.o[1][p] + sy * dy;
+        const float ly2 = lam.o[2][p] + sz * dz;
+        if (out.o[0]) {
+            out.o[0][p] = ly0;
+            out.o[1][p] = ly1;
+            out.o[2][p] = ly2;
+            out.v[0][p] = lam.v[0][p];
+            out.v[1][p] = lam.v[1][p];
+            out.v[2][p] = lam.v[2][p];
+        } else {
+            lam.o[0][p] = ly0;
+            lam.o[1][p] = ly1;
+            lam.o[2][p] = ly2;
+        }
+        mly = fmaxf(mly, fmaxf(fabsf(ly0), fmaxf(fabsf(ly1), fabsf(ly2))));
     }
+    max_to(&ctrl->adj_ly[par], mly);
 }
 
 __global__ void k_adj_zero(int64_t n, const Ctrl *__restrict__ ctrl) {
@@ -360,20 +421,20 @@ cudaError_t launch_adj_seed(int64_t ng, const float4 *E4, float4 *lE4, const dou
 }
 
 cudaError_t launch_adj_push(const Geom &g, const Ctrl *ctrl, const int4 *items, int max_items,
-                            const int32_t *ycell, const float *const yo[3], const float4 *E4,
+                            const int32_t *ycell, const float *const yo[3], const float4 *E8,
                             float4 *lE4, float c_kick, float dt, float wz2, const AdjRhoTerm &rt,
-                            Ctrl *ctrl_w, cudaStream_t st) {
+                            const AdjBound &ab, Ctrl *ctrl_w, cudaStream_t st) {
     const int S = (g.tile[0] + 2 * g.guard + 1) * (g.tile[1] + 2 * g.guard + 1) *
                   (g.tile[2] + 2 * g.guard + 1);
-    const size_t smem = sizeof(float) * 3 * (size_t)S;
+    const size_t smem = sizeof(int) * 3 * (size_t)S;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_adj_push, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const int blocks = std::max(1, std::min(152 * 4, max_items));
-    k_adj_push<<<blocks, 256, smem, st>>>(g, ctrl, items, ycell, yo[0], yo[1], yo[2], E4, lE4,
-                                          c_kick, dt, wz2, rt, ctrl_w);
+    const int blocks = std::max(1, std::min(152 * PIC_ADJ_MIN_BLOCKS * 2, max_items));
+    k_adj_push<<<blocks, 256, smem, st>>>(g, ctrl, items, ycell, yo[0], yo[1], yo[2], E8, lE4,
+                                          c_kick, dt, wz2, rt, ab, ctrl_w);
     return cudaGetLastError();
 }
 
@@ -387,12 +448,47 @@ cudaError_t launch_green_adj(const Geom &g, const double *L_d, const float2 *lE_
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_rho(int64_t n, const Geom &g, const Ctrl *ctrl, const int32_t *ycell,
-                           const float *const yo[3], const float *lrho, float qscale,
-                           cudaStream_t st) {
+// lrho2[q] = (lrho[q], lrho[q + x]) (periodic): the x-paired copy read by
+// the deposit-term gathers; also clears lE for the next reverse push (its
+// transform has been taken by now)
+//
+// Bound bookkeeping for step m (par = m & 1): the maximum |lrho| goes to
+// adj_lrho[par]; adj_ly / adj_lv[par ^ 1], last read by the reverse push of
+// step m, are cleared for the push of step m - 1 to fill.
+__global__ void k_adj_pair_rho(int nx, int64_t ng, const float *__restrict__ lrho,
+                               float2 *__restrict__ lrho2, float4 *__restrict__ lE4, Ctrl *ctrl,
+                               int par) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q == 0) {
+        ctrl->adj_ly[par ^ 1] = 0u;
+        ctrl->adj_lv[par ^ 1] = 0u;
+    }
+    float m = 0.0f;
+    if (q < ng) {
+        const int64_t row = q / nx;
+        const int i = (int)(q - row * nx);
+        const float a = lrho[q];
+        lrho2[q] = make_float2(a, lrho[(i + 1 == nx) ? row * nx : q + 1]);
+        lE4[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        m = fabsf(a);
+    }
+    max_to(&ctrl->adj_lrho[par], m);
+}
+
+cudaError_t launch_adj_pair_rho(const Geom &g, const float *lrho, float2 *lrho2, float4 *lE4,
+                                Ctrl *ctrl, int par, cudaStream_t st) {
+    const int64_t ng = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    k_adj_pair_rho<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(g.n[0], ng, lrho, lrho2, lE4,
+                                                                 ctrl, par);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_rho(int64_t n, const Geom &g, Ctrl *ctrl, const int32_t *ycell,
+                           const float *const yo[3], const float2 *lrho2, float qscale,
+                           const LamOut &out, int par, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int b = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
-    k_adj_rho<<<b, 256, 0, st>>>(n, g, ctrl, ycell, yo[0], yo[1], yo[2], lrho, qscale);
+    k_adj_rho<<<b, 256, 0, st>>>(n, g, ctrl, ycell, yo[0], yo[1], yo[2], lrho2, qscale, out, par);
     return cudaGetLastError();
 }
 

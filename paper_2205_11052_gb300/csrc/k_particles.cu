@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g,
                                                           const float4 *__restrict__ E8,
                                                           float *rho, unsigned long long *rho64,
                                                           float qscale, int sparse_below,
-                                                          double *__restrict__ part) {
+                                                          double *__restrict__ part,
+                                                          SaveY save) {
     extern __shared__ uint32_t acc[];
     const ParticleSet ps = ctrl->sets[ctrl->cur];
     const int n_items = ctrl->n_items;
@@ -242,6 +243,12 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g,
             int32_t c = __ldcs(ps.cell + p);
             float fx = __ldcs(ps.o[0] + p), fy = __ldcs(ps.o[1] + p), fz = __ldcs(ps.o[2] + p);
             float vx = __ldcs(ps.v[0] + p), vy = __ldcs(ps.v[1] + p), vz = __ldcs(ps.v[2] + p);
+            if (save.cell) {
+                __stcs(save.cell + p, c);
+                __stcs(save.o[0] + p, fx);
+                __stcs(save.o[1] + p, fy);
+                __stcs(save.o[2] + p, fz);
+            }
             pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E8, sparse, acc, t, rho, rho64, qscale, c, fx, fy,
                                           fz, vx, vy, vz, bad, strays, a);
             __stcs(ps.cell + p, c);
@@ -399,7 +406,8 @@ cudaError_t push_deposit_prepare(const Geom &g) {
 cudaError_t launch_push_deposit(const Geom &g, const PushConst &pc, bool diag, bool fixed,
                                 Ctrl *ctrl, const int4 *items, int max_items, const float4 *E8,
                                 float *rho, unsigned long long *rho64, double qscale,
-                                int sparse_below, double *part, int blocks, cudaStream_t st) {
+                                int sparse_below, double *part, int blocks, const SaveY &save,
+                                cudaStream_t st) {
     const bool ext = pc.wz2 != 0.0f;
     const bool mag = pc.t[0] != 0.0f || pc.t[1] != 0.0f || pc.t[2] != 0.0f;
     const size_t smem = push_deposit_smem(g);
@@ -408,7 +416,7 @@ cudaError_t launch_push_deposit(const Geom &g, const PushConst &pc, bool diag, b
     cudaError_t e = cudaSuccess;
 #define PIC_PD(D, X, M, F)                                                                      \
     k_push_deposit<D, X, M, F><<<nb, 256, smem, st>>>(g, pc, ctrl, items, E8, rho, rho64, qs,   \
-                                                      sparse_below, part)
+                                                      sparse_below, part, save)
 #define PIC_PD_F(D, X, M) \
     do { if (fixed) PIC_PD(D, X, M, true); else PIC_PD(D, X, M, false); } while (0)
     if (diag) {

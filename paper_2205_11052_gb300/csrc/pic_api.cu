@@ -48,7 +48,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Byte offsets of every device buffer inside the caller's arena.
 struct Layout {
-    size_t ctrl, sets, rho, rho64, rho_hat, E_hat, E4, E8, bins, scan_tmp, tile_items, tile_range,
+    size_t ctrl, sets, rho, rho64, rho_hat, E_hat, E4, E8, lrho2, bins, scan_tmp, tile_items, tile_range,
         items, fpart, ppart, ring, inv, stage_x, stage_v, adjE4, fft, total;
     size_t set_stride;   // bytes of one per-particle array
 };
@@ -209,6 +209,7 @@ void compute_layout(pic_ctx *c) {
     L.stage_x = take((size_t)c->staging * 24);
     L.stage_v = take((size_t)c->staging * 24);
     L.adjE4 = take((size_t)c->ng * 16);
+    L.lrho2 = take((size_t)c->ng * 8);
     L.fft = take(c->fft_reserve);
     L.total = o;
 }
@@ -370,7 +371,7 @@ int fused_blocks_of(const pic_ctx *c) {
 }
 
 // gather + push + deposit of the new positions in one kernel (pic_step)
-int do_push_deposit(pic_ctx *c, bool diag) {
+int do_push_deposit(pic_ctx *c, bool diag, const SaveY &save = SaveY{}) {
     const bool fixed = (c->prm.options & PIC_OPT_FIXED_DEPOSIT) != 0;
     if (!fixed || c->np <= 0)
         PIC_CUDA(cudaMemsetAsync(c->at<float>(c->lay.rho), 0, (size_t)c->ng * 4, c->st));
@@ -382,7 +383,7 @@ int do_push_deposit(pic_ctx *c, bool diag) {
                                      c->at<float4>(c->lay.E8), c->at<float>(c->lay.rho),
                                      c->at<unsigned long long>(c->lay.rho64), qscale_of(c),
                                      c->sparse_below, c->at<double>(c->lay.ppart),
-                                     fused_blocks_of(c), c->st));
+                                     fused_blocks_of(c), save, c->st));
     } else {
         // nothing to push: the plain kernel still records zero moments and the step
         PIC_CUDA(launch_gather_push(0, c->geom, push_const(c), diag, c->ctrl(),
@@ -420,7 +421,7 @@ AdjLayout adj_layout(const pic_ctx *c, int n_steps, int K) {
     L.off_nitems = L.off_items + L.items;
     L.ckpt = L.off_nitems + kAlign;
     L.segy = 4 * L.arr;                       // cell, o[3]
-    L.segE = align_up((size_t)c->ng * 16);    // E4 of one step
+    L.segE = align_up((size_t)c->ng * 32);    // x-paired E of one step
     L.rec = L.arr + L.items + kAlign;         // pid, items, n_items
     L.R = std::max(1, std::min(c->prm.sort_period > 0 ? c->prm.sort_period : K, K));
     L.nrec = (K + L.R - 1) / L.R;
@@ -526,20 +527,13 @@ int adj_restore(pic_ctx *c, const AdjLayout &L, int seg, int cur) {
     return r ? r : adj_use_items(c, L, seg, 0);
 }
 
-// positions (cell, o) and field of step `slot` of the segment being reversed
-int adj_keep_y(pic_ctx *c, const AdjLayout &L, int slot, int cur) {
-    char *dst[4], *src[8];
-    buf_arrays(c->adj.buf + L.off_segy + (size_t)slot * L.segy, L.arr, 4, dst);
-    set_arrays(c->hsets[cur], src);
-    return copy_arrays(c, dst, src, 4);
-}
-
+// field (x-paired) of step `slot` of the segment being reversed
 int adj_keep_E(pic_ctx *c, const AdjLayout &L, int slot) {
     CopyList cl{};
     cl.count = 1;
     cl.dst[0] = c->adj.buf + L.off_segE + (size_t)slot * L.segE;
-    cl.src[0] = c->at<char>(c->lay.E4);
-    cl.bytes[0] = c->ng * 16;
+    cl.src[0] = c->at<char>(c->lay.E8);
+    cl.bytes[0] = c->ng * 32;
     PIC_CUDA(launch_copy(cl, c->st));
     return PIC_OK;
 }
@@ -565,6 +559,17 @@ int adj_lam_backup(pic_ctx *c, const AdjLayout &L, int cur, bool to_backup) {
     return to_backup ? copy_arrays(c, bk, lam, 6) : copy_arrays(c, lam, bk, 6);
 }
 
+LamOut adj_backup_out(pic_ctx *c, const AdjLayout &L) {
+    char *bk[6];
+    buf_arrays(c->adj.buf + L.off_lam, L.arr, 6, bk);
+    LamOut o;
+    for (int d = 0; d < 3; ++d) {
+        o.o[d] = reinterpret_cast<float *>(bk[d]);
+        o.v[d] = reinterpret_cast<float *>(bk[3 + d]);
+    }
+    return o;
+}
+
 // Multipliers held in the backup in the order given by pid_later -> the live
 // multiplier arrays in the order given by pid_earlier (same particles).
 int adj_permute_from_backup(pic_ctx *c, const AdjLayout &L, int cur, const int32_t *pid_later,
@@ -586,24 +591,33 @@ int adj_permute_from_backup(pic_ctx *c, const AdjLayout &L, int cur, const int32
 }
 
 // One forward step of a sweep that keeps its trajectory: re-bin when an order
-// starts here (recording it), keep y_n, solve, keep E_n, push + deposit.
+// starts here (recording it), solve, keep E_n, push + deposit keeping y_n.
 int adj_keep_step(pic_ctx *c, const AdjLayout &L, int seg, int a0, int n, int *cur) {
     int r;
     if (n > a0 && (n - a0) % L.R == 0) {
         if ((r = adj_rebin(c, cur)) || (r = adj_record(c, L, seg, (n - a0) / L.R, *cur)))
             return r;
     }
-    if ((r = adj_keep_y(c, L, n - a0, *cur))) return r;
     if (!c->rho_current && (r = do_deposit(c))) return r;
     if ((r = do_solve(c)) || (r = adj_keep_E(c, L, n - a0))) return r;
-    return do_push_deposit(c, false);
+    if (c->np == 0) return do_push_deposit(c, false);
+    // y_n is written by the push that reads it
+    char *y[4];
+    buf_arrays(c->adj.buf + L.off_segy + (size_t)(n - a0) * L.segy, L.arr, 4, y);
+    SaveY save;
+    save.cell = reinterpret_cast<int32_t *>(y[0]);
+    for (int d = 0; d < 3; ++d) save.o[d] = reinterpret_cast<float *>(y[1 + d]);
+    return do_push_deposit(c, false, save);
 }
 
-int adj_solve(pic_ctx *c) {
+// the adjoint field solve of step m (par = m & 1: its bound bookkeeping slot)
+int adj_solve(pic_ctx *c, int par) {
     PIC_CUFFT(cufftExecR2C(c->r2c3, c->at<cufftReal>(c->lay.adjE4), c->at<cufftComplex>(c->lay.E_hat)));
     PIC_CUDA(launch_green_adj(c->geom, c->L, c->at<float2>(c->lay.E_hat),
                               c->at<float2>(c->lay.rho_hat), c->nhalf, c->st));
     PIC_CUFFT(cufftExecC2R(c->c2r1, c->at<cufftComplex>(c->lay.rho_hat), c->at<cufftReal>(c->lay.rho)));
+    PIC_CUDA(launch_adj_pair_rho(c->geom, c->at<float>(c->lay.rho), c->at<float2>(c->lay.lrho2),
+                                 c->at<float4>(c->lay.adjE4), c->ctrl(), par, c->st));
     return PIC_OK;
 }
 
@@ -1051,11 +1065,13 @@ int pic_adjoint_backward(pic_handle_t c, double scale, double *gx, double *gv, i
     const float qsc = (float)qscale_of(c);
     const float c_kick = (float)(c->prm.dt * c->sp.q_over_m);
     const float dt = (float)c->prm.dt, wz2 = (float)c->prm.wz2;
+    const float kb = 2.0f * fabsf(qsc) *
+                     (float)std::max(c->inv_h[0], std::max(c->inv_h[1], c->inv_h[2]));
     float4 *lE4 = c->at<float4>(c->lay.adjE4);
-    const size_t lE_bytes = (size_t)c->ng * 16;
-    float *lrho = c->at<float>(c->lay.rho);
+    const float2 *lrho2 = c->at<float2>(c->lay.lrho2);
 
     // terminal: lE = 2 h^3 w E of the final field, then (dD/dy)^T S^T
+    PIC_CUDA(cudaMemsetAsync(c->ctrl()->adj_ly, 0, sizeof(c->ctrl()->adj_ly) * 3, c->st));
     {
         const ParticleSet &cs = c->hsets[cur];
         const float *cyo[3] = {cs.o[0], cs.o[1], cs.o[2]};
@@ -1063,10 +1079,13 @@ int pic_adjoint_backward(pic_handle_t c, double scale, double *gx, double *gv, i
         const double seed[3] = {2.0 * c->dV * c->adj.w[0], 2.0 * c->dV * c->adj.w[1],
                                 2.0 * c->dV * c->adj.w[2]};
         PIC_CUDA(launch_adj_seed(c->ng, c->at<float4>(c->lay.E4), lE4, seed, c->st));
-        if ((r = adj_solve(c))) return r;
-        PIC_CUDA(launch_adj_rho(c->np, c->geom, c->ctrl(), cs.cell, cyo, lrho, qsc, c->st));
+        const int last = c->adj.n_steps - 1;   // the step whose field J measures
+        if ((r = adj_solve(c, last & 1))) return r;
+        PIC_CUDA(launch_adj_rho(c->np, c->geom, c->ctrl(), cs.cell, cyo, lrho2, qsc, LamOut{},
+                                last & 1, c->st));
     }
 
+    bool backup_ready = false;   // the multipliers already sit in the backup
     for (int s = c->adj.nseg - 1; s >= 0; --s) {
         const int a0 = s * K, b0 = std::min(a0 + K, c->adj.n_steps - 1);
         if (s != c->adj.nseg - 1) {
@@ -1074,7 +1093,8 @@ int pic_adjoint_backward(pic_handle_t c, double scale, double *gx, double *gv, i
             // positions, field and particle order (the last segment was kept
             // by the forward sweep); the multipliers, in checkpoint s + 1's
             // order, wait in the backup while the re-binning uses their arrays
-            if ((r = adj_lam_backup(c, L, cur, true))) return r;
+            if (!backup_ready && (r = adj_lam_backup(c, L, cur, true))) return r;
+            backup_ready = false;
             if ((r = adj_restore(c, L, s, cur))) return r;
             c->rho_current = false;
             for (int n = a0; n < b0; ++n)
@@ -1097,23 +1117,22 @@ int pic_adjoint_backward(pic_handle_t c, double scale, double *gx, double *gv, i
                                   reinterpret_cast<const float *>(y[3])};
             const float4 *En = reinterpret_cast<const float4 *>(c->adj.buf + L.off_segE +
                                                                 (size_t)(n - a0) * L.segE);
-            PIC_CUDA(cudaMemsetAsync(lE4, 0, lE_bytes, c->st));
             PIC_CUDA(launch_adj_push(c->geom, c->ctrl(), c->at<int4>(c->lay.items),
                                      (int)c->max_items, ycell, yo, En, lE4, c_kick, dt, wz2, rt,
-                                     c->ctrl(), c->st));
-            if ((r = adj_solve(c))) return r;
+                                     AdjBound{n & 1, fabsf(c_kick), dt, kb}, c->ctrl(), c->st));
+            if ((r = adj_solve(c, n & 1))) return r;
             rt.cell = ycell;
             for (int d = 0; d < 3; ++d) rt.o[d] = yo[d];
-            rt.lrho = lrho;
+            rt.lrho2 = lrho2;
             rt.sx = qsc * (float)c->inv_h[0];
             rt.sy = qsc * (float)c->inv_h[1];
             rt.sz = qsc * (float)c->inv_h[2];
             if (rec > 0 && n == a0 + rec * L.R) {
                 // order `rec` began at this step: finish the step in it, then
                 // move the multipliers to the order before the re-binning
-                PIC_CUDA(launch_adj_rho(c->np, c->geom, c->ctrl(), rt.cell, rt.o, lrho, qsc, c->st));
+                PIC_CUDA(launch_adj_rho(c->np, c->geom, c->ctrl(), rt.cell, rt.o, lrho2, qsc,
+                                        adj_backup_out(c, L), n & 1, c->st));
                 rt = AdjRhoTerm{};
-                if ((r = adj_lam_backup(c, L, cur, true))) return r;
                 const int32_t *pid_l = reinterpret_cast<const int32_t *>(order_rec(c, L, s, rec).pid);
                 const int32_t *pid_e =
                     reinterpret_cast<const int32_t *>(order_rec(c, L, s, rec - 1).pid);
@@ -1122,8 +1141,14 @@ int pic_adjoint_backward(pic_handle_t c, double scale, double *gx, double *gv, i
                 if ((r = adj_use_items(c, L, s, rec))) return r;
             }
         }
-        if (rt.cell)
-            PIC_CUDA(launch_adj_rho(c->np, c->geom, c->ctrl(), rt.cell, rt.o, lrho, qsc, c->st));
+        if (rt.cell) {
+            // the segment's first step; before another segment is recomputed
+            // the multipliers go to the backup anyway, so write them there
+            const bool to_backup = s > 0 && c->np > 0;
+            PIC_CUDA(launch_adj_rho(c->np, c->geom, c->ctrl(), rt.cell, rt.o, lrho2, qsc,
+                                    to_backup ? adj_backup_out(c, L) : LamOut{}, a0 & 1, c->st));
+            backup_ready = to_backup;
+        }
     }
 
     // The multipliers are now in the order of checkpoint 0: restore it (the

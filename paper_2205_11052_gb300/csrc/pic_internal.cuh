@@ -37,6 +37,10 @@ struct Ctrl {
     long long diag_written; // diagnostic records written since the load
     double mode[2];         // tracked Fourier coefficient of the last solve
     double scalar[2];       // objective and dot-product results
+    // adjoint sweep: bit patterns of non-negative float maxima (atomicMax on
+    // the bits orders them), double-buffered by step parity: |ly|, |lv| of
+    // the multipliers and |lrho| of the last adjoint solve
+    unsigned int adj_ly[2], adj_lv[2], adj_lrho[2];
     int32_t cur;            // which ParticleSet holds the particles
     int32_t pad0;
     ParticleSet sets[2];
@@ -90,6 +94,10 @@ constexpr int kMaxSmemPerBlock = 227 * 1024;   // opt-in shared memory per block
 #ifndef PIC_PD_MIN_BLOCKS
 #define PIC_PD_MIN_BLOCKS 4
 #endif
+// resident blocks per SM the reverse push is compiled for
+#ifndef PIC_ADJ_MIN_BLOCKS
+#define PIC_ADJ_MIN_BLOCKS 4
+#endif
 constexpr int kMaxChunk = 4095;   // fixed-point tile slots stay below 2^32
 
 // Set the thread-local message returned by pic_last_error(); returns `code`.
@@ -126,11 +134,18 @@ cudaError_t launch_rho_finish(const Geom &g, unsigned long long *rho64, float *r
 // and the one-time attribute setting it needs above 48 KiB
 size_t push_deposit_smem(const Geom &g);
 cudaError_t push_deposit_prepare(const Geom &g);
+// Optional copy of the positions a push starts from (cell, o[3]), written by
+// the fused kernel as it reads them (the adjoint keeps each step's y).
+struct SaveY {
+    int32_t *cell;
+    float *o[3];
+};
 // E8: the x-paired field (launch_pair_E), 2 float4 per node
 cudaError_t launch_push_deposit(const Geom &g, const PushConst &pc, bool diag, bool fixed,
                                 Ctrl *ctrl, const int4 *items, int max_items, const float4 *E8,
                                 float *rho, unsigned long long *rho64, double qscale,
-                                int sparse_below, double *part, int blocks, cudaStream_t st);
+                                int sparse_below, double *part, int blocks, const SaveY &save,
+                                cudaStream_t st);
 cudaError_t launch_gather_push(int64_t n, const Geom &g, const PushConst &pc, bool diag,
                                Ctrl *ctrl, const float4 *E8, double *part, int blocks,
                                int threads, cudaStream_t st);
@@ -161,21 +176,36 @@ cudaError_t launch_copy(const CopyList &cl, cudaStream_t st);
 // The deposit term of the adjoint of one step, (dD/dy)^T lrho evaluated at
 // that step's positions (cell, o) and scaled by q/h_d, folded into the
 // reverse push of the step before it (cell == nullptr: no such term).
+// Scale of the integer accumulation of G^T le in the reverse push of step n:
+// the step's parity and the constants of the bound on |le| (c = dt q/m,
+// kb = 2 max_d |q / h_d| bounds the deposit term per unit |lrho|).
+struct AdjBound {
+    int par;
+    float c_abs, dt, kb;
+};
 struct AdjRhoTerm {
     const int32_t *cell;
     const float *o[3];
-    const float *lrho;
+    const float2 *lrho2;   // x-paired lrho (launch_pair_scalar)
     float sx, sy, sz;
 };
 cudaError_t launch_adj_push(const Geom &g, const Ctrl *ctrl, const int4 *items, int max_items,
-                            const int32_t *ycell, const float *const yo[3], const float4 *E4,
+                            const int32_t *ycell, const float *const yo[3], const float4 *E8,
                             float4 *lE4, float c_kick, float dt, float wz2, const AdjRhoTerm &rt,
-                            Ctrl *ctrl_w, cudaStream_t st);
+                            const AdjBound &ab, Ctrl *ctrl_w, cudaStream_t st);
 cudaError_t launch_green_adj(const Geom &g, const double *L_d, const float2 *lE_hat,
                              float2 *lrho_hat, int64_t nhalf, cudaStream_t st);
-cudaError_t launch_adj_rho(int64_t n, const Geom &g, const Ctrl *ctrl, const int32_t *ycell,
-                           const float *const yo[3], const float *lrho, float qscale,
-                           cudaStream_t st);
+// where k_adj_rho writes the updated multipliers (o[0] == nullptr: in place)
+struct LamOut {
+    float *o[3];
+    float *v[3];
+};
+cudaError_t launch_adj_rho(int64_t n, const Geom &g, Ctrl *ctrl, const int32_t *ycell,
+                           const float *const yo[3], const float2 *lrho2, float qscale,
+                           const LamOut &out, int par, cudaStream_t st);
+// lrho2[q] = (lrho[q], lrho[q + x (periodic)]); lE4 cleared
+cudaError_t launch_adj_pair_rho(const Geom &g, const float *lrho, float2 *lrho2, float4 *lE4,
+                                Ctrl *ctrl, int par, cudaStream_t st);
 cudaError_t launch_adj_zero(int64_t n, const Ctrl *ctrl, cudaStream_t st);
 struct ReorderArgs {
     const float *in_o[3];

@@ -160,3 +160,31 @@ def test_adjoint_rejects_magnetic_fields_and_small_buffers():
         sim.adjoint_backward()
     assert e.value.code == capi.PIC_ERR_STATE
     sim.close()
+
+
+def test_directional_derivative_with_the_benchmark_settings():
+    """The bump-on-tail velocity mixture and seed wave (k = 0.1, alpha = 0.05)
+    on a 16^3 grid with 16 particles per cell (65,536 particles), 40 steps,
+    the benchmark's launch settings (re-binning every 4 steps, fixed-point
+    deposit), checkpoints every 20 steps: <dJ/d(x0, v0), delta> against the
+    central difference of the oracle's J along delta."""
+    import bench
+
+    w = pi.bump_on_tail(n=16, ppc=16, seed=11)
+    n_steps, weights = 40, (0.0, 0.0, 1.0)
+    sim = Simulation.from_workload(w, **bench.LAUNCH)
+    J = sim.adjoint_forward(n_steps, weights, checkpoint_every=20)
+    gx, gv = sim.adjoint_backward()
+    sim.close()
+    rng = np.random.default_rng(5)
+    dX, dV = rng.standard_normal(w.x.shape), rng.standard_normal(w.v.shape)
+    g = po.Grid(w.n, w.L)
+    p = po.Params(dt=w.dt, Q=w.Q)
+    eps = 1e-6
+    Jp = po.run_with_gradient(w.x + eps * dX, w.v + eps * dV, g, p, n_steps, weights)[0]
+    Jm = po.run_with_gradient(w.x - eps * dX, w.v - eps * dV, g, p, n_steps, weights)[0]
+    fd = (Jp - Jm) / (2 * eps)
+    ad = float(np.sum(gx * dX) + np.sum(gv * dV))
+    J0 = po.run_with_gradient(w.x, w.v, g, p, n_steps, weights)[0]
+    assert J == pytest.approx(J0, rel=1e-4)
+    assert ad == pytest.approx(fd, rel=1e-3)
