@@ -56,7 +56,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--workload", default="landau", choices=["landau", "ensemble"])
+    ap.add_argument("--workload", default="landau", choices=["landau", "ensemble", "adjoint"],
+                    help="landau: the benchmark step; ensemble: batched instances vs per-instance "
+                         "launches; adjoint: only the adjoint cost measurement")
+    ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--ens-count", type=int, default=512, help="ensemble instances")
     ap.add_argument("--record-traffic", metavar="NCU_CSV",
                     help="write profiles/traffic.json from an ncu --csv capture of "
@@ -390,6 +393,12 @@ def main():
         return
     if args.workload == "ensemble":
         run_ensemble(args)
+        return
+    if args.workload == "adjoint":
+        from paper_2205_11052_gb300.build import build
+
+        build()
+        print(json.dumps(measure_adjoint(n_steps=args.adjoint_steps)), flush=True)
         return
 
     import numpy as np

@@ -82,8 +82,12 @@ __device__ __forceinline__ int table_slot(int32_t *hkey, int key, int size) {
 // with one atomic, and writes every tile's particles contiguously.  A slice
 // with more distinct tiles than the table holds (the first binning of
 // particles in arbitrary order) falls back to per-warp claims.
-constexpr int kStage = 1024;
+#ifndef PIC_SORT_STAGE
+#define PIC_SORT_STAGE 512
+#endif
+constexpr int kStage = PIC_SORT_STAGE;
 constexpr int kHash = 256;
+constexpr int kPerThread = kStage / 256;   // the staged kernels run 256 threads per block
 
 __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl *ctrl,
                                                          int32_t *bins) {
@@ -112,16 +116,21 @@ __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl 
             hcnt[h] = 0;
         }
         if (threadIdx.x == 0) overflow = 0;
-        for (int j = threadIdx.x; j < m; j += blockDim.x) {
-            const int64_t p = s0 + j;
-            sc[j] = __ldcs(src.cell + p);
-            so[j] = __ldcs(src.o[0] + p);
-            so[kStage + j] = __ldcs(src.o[1] + p);
-            so[2 * kStage + j] = __ldcs(src.o[2] + p);
-            sv[j] = __ldcs(src.v[0] + p);
-            sv[kStage + j] = __ldcs(src.v[1] + p);
-            sv[2 * kStage + j] = __ldcs(src.v[2] + p);
-            sid[j] = __ldcs(src.pid + p);
+        // all of the slice's loads in flight at once (kStage / 256 per thread)
+#pragma unroll
+        for (int u = 0; u < kPerThread; ++u) {
+            const int j = u * 256 + threadIdx.x;
+            if (j < m) {
+                const int64_t p = s0 + j;
+                sc[j] = __ldcs(src.cell + p);
+                so[j] = __ldcs(src.o[0] + p);
+                so[kStage + j] = __ldcs(src.o[1] + p);
+                so[2 * kStage + j] = __ldcs(src.o[2] + p);
+                sv[j] = __ldcs(src.v[0] + p);
+                sv[kStage + j] = __ldcs(src.v[1] + p);
+                sv[2 * kStage + j] = __ldcs(src.v[2] + p);
+                sid[j] = __ldcs(src.pid + p);
+            }
         }
         __syncthreads();
         // slot of each particle's tile in the table and its rank there; the
@@ -178,16 +187,20 @@ __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl 
             for (int h = threadIdx.x; h < kHash; h += blockDim.x)
                 if (hcnt[h] > 0) hbase[h] = atomicAdd(bins + hkey[h], hcnt[h]);
             __syncthreads();
-            for (int j = threadIdx.x; j < m; j += blockDim.x) {
-                const int q = hbase[slid[j]] + srank[j];
-                dst.cell[q] = sc[j];
-                dst.o[0][q] = so[j];
-                dst.o[1][q] = so[kStage + j];
-                dst.o[2][q] = so[2 * kStage + j];
-                dst.v[0][q] = sv[j];
-                dst.v[1][q] = sv[kStage + j];
-                dst.v[2][q] = sv[2 * kStage + j];
-                dst.pid[q] = sid[j];
+#pragma unroll
+            for (int u = 0; u < kPerThread; ++u) {
+                const int j = u * 256 + threadIdx.x;
+                if (j < m) {
+                    const int q = hbase[slid[j]] + srank[j];
+                    dst.cell[q] = sc[j];
+                    dst.o[0][q] = so[j];
+                    dst.o[1][q] = so[kStage + j];
+                    dst.o[2][q] = so[2 * kStage + j];
+                    dst.v[0][q] = sv[j];
+                    dst.v[1][q] = sv[kStage + j];
+                    dst.v[2][q] = sv[2 * kStage + j];
+                    dst.pid[q] = sid[j];
+                }
             }
         }
         __syncthreads();
@@ -213,11 +226,19 @@ __global__ void __launch_bounds__(256) k_histogram_staged(int64_t n, Geom g, Ctr
             hcnt[h] = 0;
         }
         __syncthreads();
-        for (int jb = 0; jb < m; jb += blockDim.x) {
-            const int j = jb + threadIdx.x;
+        // the slice's cells first (kStage / 256 loads in flight per thread)
+        int32_t cv[kPerThread];
+#pragma unroll
+        for (int u = 0; u < kPerThread; ++u) {
+            const int j = u * 256 + threadIdx.x;
+            cv[u] = j < m ? __ldcs(ps.cell + s0 + j) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kPerThread; ++u) {
+            const int j = u * 256 + threadIdx.x;
             const bool act = j < m;
             const int lane = threadIdx.x & 31;
-            const int key = act ? tile_key(__ldcs(ps.cell + s0 + j), g, bad) : -1 - lane;
+            const int key = act ? tile_key(cv[u], g, bad) : -1 - lane;
             const WarpRun r = warp_run(key);
             if (act && lane == r.head) {
                 const int h = table_slot(hkey, key, kHash);
@@ -395,7 +416,9 @@ cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t
     }
     if ((e = exclusive_scan_impl(bins, nbins, scan_tmp, st)) != cudaSuccess) return e;
     if (n > 0) {
-        const int sblocks = (int)std::min<int64_t>((n + kStage - 1) / kStage, 152 * 6);
+        // resident blocks per SM as the staging buffer allows (228 KB per SM)
+        const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (228 * 1024) / (kStageSmem + 1024)));
+        const int sblocks = (int)std::min<int64_t>((n + kStage - 1) / kStage, 152 * per_sm);
         k_scatter_staged<<<sblocks, T, kStageSmem, st>>>(n, g, ctrl, bins);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
