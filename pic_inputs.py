@@ -395,16 +395,16 @@ def landau_lattice_1d(nx=32, mx=256, mv=128, alpha=0.05, k=0.5, dt=0.05, n_steps
 
 
 def _mixture_quantiles(u: np.ndarray, eps: float, v_beam: float, sigma_beam: float,
-                       sigma_bulk: float) -> np.ndarray:
-    """Inverse CDF of (1 - eps) N(0, sigma_bulk^2) + eps N(v_beam, sigma_beam^2) at u,
+                       sigma_bulk: float, u_bulk: float = 0.0) -> np.ndarray:
+    """Inverse CDF of (1 - eps) N(u_bulk, sigma_bulk^2) + eps N(v_beam, sigma_beam^2) at u,
     by bisection (monotone CDF; 80 halvings reach double precision)."""
     from scipy.special import ndtr
 
-    lo = np.full(u.shape, -12.0 * sigma_bulk + min(0.0, v_beam))
-    hi = np.full(u.shape, 12.0 * max(sigma_bulk, sigma_beam) + max(0.0, v_beam))
+    lo = np.full(u.shape, min(u_bulk - 12.0 * sigma_bulk, v_beam - 12.0 * sigma_beam))
+    hi = np.full(u.shape, max(u_bulk + 12.0 * sigma_bulk, v_beam + 12.0 * sigma_beam))
     for _ in range(80):
         mid = 0.5 * (lo + hi)
-        F = (1.0 - eps) * ndtr(mid / sigma_bulk) + eps * ndtr((mid - v_beam) / sigma_beam)
+        F = (1.0 - eps) * ndtr((mid - u_bulk) / sigma_bulk) + eps * ndtr((mid - v_beam) / sigma_beam)
         below = F < u
         lo = np.where(below, mid, lo)
         hi = np.where(below, hi, mid)
@@ -413,13 +413,14 @@ def _mixture_quantiles(u: np.ndarray, eps: float, v_beam: float, sigma_beam: flo
 
 def bump_on_tail_quiet(n=(64, 64, 64), L=20.0 * math.pi, axis=2, m=3, alpha=1e-3, ms=4096,
                        mv=1024, eps=0.1, v_beam=4.0, sigma_beam=0.3, sigma_bulk=1.0, seed=1006,
-                       dt=0.05, n_steps=300) -> Workload:
+                       dt=0.05, n_steps=300, u_bulk=0.0) -> Workload:
     """Bump-on-tail start that is quiet along one axis, for growth-rate checks.
 
     Along `axis`: ms stratified inverse-transform samples of the density
     1 + alpha cos(k s), k = 2 pi m / L, paired with every one of mv stratified
-    samples of the velocity mixture (1 - eps) N(0, sigma_bulk^2) +
-    eps N(v_beam, sigma_beam^2): ms * mv particles.  The Fourier modes
+    samples of the velocity mixture (1 - eps) N(u_bulk, sigma_bulk^2) +
+    eps N(v_beam, sigma_beam^2): ms * mv particles (u_bulk = -v_beam, eps = 1/2
+    and equal spreads give the symmetric two-stream case).  The Fourier modes
     (0, 0, j) (for axis 2) of the charge then carry no sampling noise, so the
     seeded mode m grows from its seed alone.  The transverse positions are
     uniform and the transverse velocities N(0, sigma_bulk^2), both seeded
@@ -431,7 +432,7 @@ def bump_on_tail_quiet(n=(64, 64, 64), L=20.0 * math.pi, axis=2, m=3, alpha=1e-3
     us = (np.arange(ms, dtype=np.float64) + 0.5) / ms
     s = sample_cosine_density(us, L, alpha, k)
     uv = (np.arange(mv, dtype=np.float64) + 0.5) / mv
-    vs = _mixture_quantiles(uv, eps, v_beam, sigma_beam, sigma_bulk)
+    vs = _mixture_quantiles(uv, eps, v_beam, sigma_beam, sigma_bulk, u_bulk)
     S, V = np.meshgrid(s, vs, indexing="ij")
     N = ms * mv
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -444,5 +445,5 @@ def bump_on_tail_quiet(n=(64, 64, 64), L=20.0 * math.pi, axis=2, m=3, alpha=1e-3
     return Workload(name=f"bump_on_tail_quiet_{nn[0]}x{nn[1]}x{nn[2]}_m{m}", n=nn, L=Ls,
                     x=_wrap(x, Ls), v=v, q_over_m=-1.0, Q=-(L ** 3), dt=dt, n_steps=n_steps,
                     mode=tuple(mode), mode_comp=axis,
-                    meta=dict(alpha=alpha, k=k, m=m, eps=eps, v_beam=v_beam,
+                    meta=dict(alpha=alpha, k=k, m=m, eps=eps, v_beam=v_beam, u_bulk=u_bulk,
                               sigma_beam=sigma_beam, ms=ms, mv=mv, seed=seed))

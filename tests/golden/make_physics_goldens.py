@@ -18,6 +18,15 @@ seeded generators of pic_inputs.py; nothing here calls the CUDA path.
       lattice with the resolution of the 64^3 benchmark grid (64 cells,
       256 x 512 particles, 400 steps).  About a minute.
 
+  two_stream_quiet_1d_history.json
+      The symmetric two-stream instability (Section 4.2, Eq. twostream_f:
+      beams at v_z = -pi/2 and +pi/2, spread 0.1, k = 0.5) seeded with
+      alpha = 1e-3 on a quiet 1D lattice (32 cells, 64 x 512 particles,
+      400 steps).
+  strong_landau_16_history.json
+      Strong Landau damping (Section 4.1 with alpha = 0.5; Section 5.3) on a
+      16^3 grid with 16 particles per cell (65,536 particles), 200 steps.
+
     python tests/golden/make_physics_goldens.py [name ...]
 """
 import json
@@ -68,10 +77,32 @@ def bump_on_tail_quiet_1d():
                                  ms=256, mv=512)
 
 
+def two_stream_quiet_1d():
+    """The input of two_stream_quiet_1d_history.json (also run by the GPU test)."""
+    return pi.bump_on_tail_quiet(n=(32, 1, 1), L=4.0 * math.pi, axis=0, m=1, alpha=1e-3, ms=64,
+                                 mv=512, eps=0.5, v_beam=0.5 * math.pi, sigma_beam=0.1,
+                                 sigma_bulk=0.1, u_bulk=-0.5 * math.pi)
+
+
+def two_stream_quiet():
+    w = two_stream_quiet_1d()
+    return {"workload": "pic_inputs.bump_on_tail_quiet(n=(32,1,1), L=4 pi, axis=0, m=1, alpha=1e-3, "
+                        "ms=64, mv=512, eps=0.5, v_beam=pi/2, sigma_beam=0.1, sigma_bulk=0.1, "
+                        "u_bulk=-pi/2)", "n_steps": 400, **_run(w, 400)}
+
+
+def strong_landau_16():
+    w = pi.landau(n=16, ppc=16, alpha=0.5, seed=1007)
+    return {"workload": "pic_inputs.landau(n=16, ppc=16, alpha=0.5, seed=1007)", "n_steps": 200,
+            **_run(w, 200)}
+
+
 TABLE = {
     "landau_32x32x32_ppc64_history.json": landau_32,
     "landau_lattice_1d_history.json": landau_lattice,
     "bump_on_tail_quiet_1d_history.json": bump_on_tail_quiet,
+    "two_stream_quiet_1d_history.json": two_stream_quiet,
+    "strong_landau_16_history.json": strong_landau_16,
 }
 
 if __name__ == "__main__":

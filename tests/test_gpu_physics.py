@@ -23,6 +23,16 @@
   benchmark's own bump-on-tail input (alpha = 0.05 at k = 0.1) saturates the
   beam mode at once, so there only its two Langmuir roots (1.08464 and
   -0.98988) are checked.
+* Two-stream instability (Section 4.2, Eq. twostream_f: beams at -pi/2 and
+  +pi/2, spread 0.1, k = 0.5), seeded with alpha = 1e-3: on the quiet 1D
+  lattice of the stored oracle history the GPU's growth rate matches the
+  oracle's (1%) and the kinetic root 0.31824i (2%).  (In 3D the cold beams
+  are also unstable at oblique wave vectors, which random transverse
+  positions seed; those modes outgrow k = 0.5 and drive it nonlinearly, so
+  the rate is checked on the lattice.)
+* Strong Landau damping (alpha = 0.5, Section 5.3) on 16^3 x 16 per cell,
+  200 steps: the W_x history against the stored oracle history (the same
+  input), to 1e-4 of its peak.
 """
 import json
 import math
@@ -149,3 +159,39 @@ def test_bump_on_tail_langmuir_roots_at_64_cubed():
     assert found[0] == pytest.approx(want[0], rel=0.005)
     assert found[1] == pytest.approx(want[1], rel=0.005)
     assert all(abs(s[i].real) < 0.01 for i in top)
+
+
+TSI_SPECIES = ((0.5, -0.5 * math.pi, 0.1), (0.5, 0.5 * math.pi, 0.1))
+
+
+def _two_stream(n, ms, mv):
+    return pi.bump_on_tail_quiet(n=n, L=4.0 * math.pi, axis=0, m=1, alpha=1e-3, ms=ms, mv=mv,
+                                 eps=0.5, v_beam=0.5 * math.pi, sigma_beam=0.1, sigma_bulk=0.1,
+                                 u_bulk=-0.5 * math.pi)
+
+
+def test_two_stream_growth_rate_matches_oracle_on_a_quiet_lattice():
+    to, co, _ = _golden("two_stream_quiet_1d_history.json")
+    # the input of the stored history (make_physics_goldens.two_stream_quiet_1d)
+    w = _two_stream((32, 1, 1), 64, 512)
+    t, c, _ = _run(w, 400)
+    assert np.array_equal(t, to)
+    root = dispersion.root(0.5, 0.3j, species=TSI_SPECIES)
+    gamma, omega = fastest_root(t, c, 4.0, 18.0)
+    g_o, _ = fastest_root(to, co, 4.0, 18.0)
+    print(f"two-stream lattice: gamma {gamma:.5f} (oracle {g_o:.5f}, kinetic {root.imag:.5f})")
+    assert gamma == pytest.approx(g_o, rel=0.01)
+    assert gamma == pytest.approx(root.imag, rel=0.02)
+    assert omega < 0.01
+
+
+def test_strong_landau_history_matches_oracle():
+    to, _, g = _golden("strong_landau_16_history.json")
+    w = pi.landau(n=16, ppc=16, alpha=0.5, seed=1007)
+    t, _, hist = _run(w, 200)
+    assert np.array_equal(t, to)
+    Wx = np.array([d["Wx"] for d in hist])
+    Wxo = np.array(g["Wx"])
+    err = np.max(np.abs(Wx - Wxo)) / np.max(Wxo)
+    print(f"strong Landau 16^3: W_x history deviation {err:.2e} of the peak")
+    assert err <= 1e-4

@@ -277,6 +277,29 @@ def test_bump_on_tail_growth_rate_on_a_quiet_lattice():
     assert omega == pytest.approx(root.real, rel=0.005)
 
 
+def test_two_stream_growth_rate_on_a_quiet_lattice():
+    """Symmetric two-stream instability (Section 4.2, Eq. twostream_f: beams at
+    v = -pi/2 and +pi/2 with spread 0.1, k = 0.5), seeded with alpha = 1e-3
+    on a quiet 1D lattice (32 cells, 64 x 512 particles).  The fastest root
+    fitted on t in [4, 18] is purely growing at the kinetic root 0.31824i."""
+    from tests.fits import fastest_root
+
+    w = pi.bump_on_tail_quiet(n=(32, 1, 1), L=4.0 * math.pi, axis=0, m=1, alpha=1e-3, ms=64,
+                              mv=512, eps=0.5, v_beam=0.5 * math.pi, sigma_beam=0.1,
+                              sigma_bulk=0.1, u_bulk=-0.5 * math.pi)
+    grid = po.Grid(w.n, w.L)
+    p = po.Params(dt=w.dt, Q=w.Q, q_over_m=w.q_over_m)
+    _, _, hist = po.run(w.x, w.v, grid, p, 400)
+    t = np.array([d["t_field"] for d in hist])
+    c = np.array([d["mode"] for d in hist])
+    gamma, omega = fastest_root(t, c, 4.0, 18.0)
+    root = dispersion.root(0.5, 0.3j, species=((0.5, -0.5 * math.pi, 0.1),
+                                              (0.5, 0.5 * math.pi, 0.1)))
+    assert abs(root.real) < 1e-9
+    assert gamma == pytest.approx(root.imag, rel=0.02)
+    assert omega < 0.01
+
+
 def test_diagnostics_field_energy_of_a_known_field():
     grid = po.Grid((8, 8, 8), (2.0, 2.0, 2.0))
     E = np.zeros((3,) + grid.shape)
