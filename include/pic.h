@@ -256,25 +256,28 @@ int pic_read_timers(pic_handle_t h, double ms[PIC_PHASE_COUNT],
  * the field used by the last of n_steps steps (the W_d of pic_diag_t for that
  * step), as a function of the synchronised state (x_0, v_0) loaded last.
  * The gradient is the exact discrete adjoint of the drift-kick-drift step of
- * pic_step (B_ext must be zero): the gather and the deposit appear as each
- * other's transposes and the spectral operator as its conjugate symbol.
+ * pic_step, external fields included: the gather and the deposit appear as
+ * each other's transposes, the spectral operator as its conjugate symbol and
+ * the Boris rotation R (v' = R v + (dt q/m / 2)(R + I) e) as R^T.
  * Memory: the forward pass stores a checkpoint of the particle state every
  * `checkpoint_every` steps; the reverse sweep recomputes one segment at a
- * time from its checkpoint, keeping that segment's positions and fields.
- * Particles are not re-binned during these calls (their order is fixed), so
- * the deposits of long gradient runs take more global atomics.  With
- * PIC_OPT_FIXED_DEPOSIT the recomputation reproduces the forward pass bit
- * for bit.  FP32 particle and grid arithmetic; J and the final reductions in
- * FP64. */
+ * time from its checkpoint, keeping that segment's positions and fields (the
+ * last segment is kept by the forward pass itself; with checkpoint_every >=
+ * n_steps - 1 nothing is recomputed).  Both sweeps re-bin the particles at
+ * every checkpoint and every sort_period steps and record each order, and
+ * the multipliers are permuted back across each re-binning.  The reverse
+ * deposit of the 3-vector G^T le accumulates in int32 shared tiles whose
+ * scale comes from a bound on |le| carried from step to step.  FP32 particle
+ * and grid arithmetic; J and the final reductions in FP64. */
 
 /* Bytes of the caller-owned device buffer for pic_adjoint_forward/backward. */
 int pic_adjoint_buffer_bytes(pic_handle_t h, int n_steps, int checkpoint_every, size_t *bytes);
 
-/* Run n_steps >= 1 steps from the loaded state without re-binning, storing
- * checkpoints in `buf` (device, >= pic_adjoint_buffer_bytes), and write J to
+/* Run n_steps >= 1 steps from the loaded state, storing checkpoints in `buf`
+ * (device, >= pic_adjoint_buffer_bytes, 256-byte aligned), and write J to
  * host memory (synchronises).  weights: 3 non-negative finite doubles.
  * Leaves the particles at the state after n_steps - 1 steps.
- * Errors: PIC_ERR_ARG (B_ext nonzero, bad counts or weights, null buffer),
+ * Errors: PIC_ERR_ARG (bad counts or weights, null or misaligned buffer),
  * PIC_ERR_CAPACITY (buffer too small), PIC_ERR_STATE (nothing loaded). */
 int pic_adjoint_forward(pic_handle_t h, int n_steps, int checkpoint_every,
                         const double weights[3], void *buf, size_t bytes, double *J);

@@ -422,17 +422,33 @@ def field_energy_gradient(y: np.ndarray, grid: Grid, params: Params, weights=(1.
     return (qp / grid.cell_volume) * np.einsum("pc,pcj->pj", lr, dw)
 
 
+def boris_rotation(params: Params) -> np.ndarray:
+    """The rotation R of the Boris kick: boris_kick(v, e) = R v + (dt q/m / 2)(R + I) e.
+    Its columns are the kicks of the unit vectors with e = 0."""
+    return np.stack([boris_kick(np.eye(3)[j], np.zeros(3), params.q_over_m, params.B, params.dt)
+                     for j in range(3)], axis=1)
+
+
 def adjoint_step(y: np.ndarray, lam_y: np.ndarray, lam_v: np.ndarray, grid: Grid,
                  params: Params):
-    """Pull (lam_y, lam_v) of (y_{n+1}, v_{n+1}) back to (y_n, v_n)."""
-    if any(b != 0.0 for b in params.B):
-        raise NotImplementedError("adjoint of the magnetic rotation")
+    """Pull (lam_y, lam_v) of (y_{n+1}, v_{n+1}) back to (y_n, v_n).
+
+    The step is v' = R v + h (R + I) e(y), y' = y + dt v' (h = dt q/m / 2,
+    R the Boris rotation, the identity without B), so with
+    lv_tot = lam_v + dt lam_y: lam_v(n) = R^T lv_tot and the field sees
+    le = h (R^T + I) lv_tot (= 2 h lv_tot without B)."""
     N = y.shape[0]
     qp = params.Q / N if N else 0.0
     c = params.dt * params.q_over_m
     E = solve_field(deposit(y, grid, qp), grid)
     lv_tot = lam_v + params.dt * lam_y
-    le = c * lv_tot
+    if any(b != 0.0 for b in params.B):
+        R = boris_rotation(params)
+        le = 0.5 * c * (lv_tot @ R + lv_tot)        # rows: (R^T lv)^T = lv^T R
+        lv_out = lv_tot @ R
+    else:
+        le = c * lv_tot
+        lv_out = lv_tot
     nodes, w, dw = cic_weight_gradients(y, grid)
     # (dG/dy . E)^T le : sum_corner dW/dy_j (le . E_corner)
     Eg = np.stack([E[d].ravel()[nodes] for d in range(3)], axis=-1)     # (N, 8, 3)
@@ -445,7 +461,7 @@ def adjoint_step(y: np.ndarray, lam_y: np.ndarray, lam_v: np.ndarray, grid: Grid
     lamrho = solve_field_transpose(lamE, grid)
     lr = lamrho.ravel()[nodes]
     ly = ly + (qp / grid.cell_volume) * np.einsum("pc,pcj->pj", lr, dw)
-    return ly, lv_tot
+    return ly, lv_out
 
 
 def run_with_gradient(x0: np.ndarray, v0: np.ndarray, grid: Grid, params: Params,
@@ -467,7 +483,7 @@ def run_with_gradient(x0: np.ndarray, v0: np.ndarray, grid: Grid, params: Params
         e = gather(y, E, grid)
         if params.wz2 != 0.0:
             e = e + external_field(y, grid, params.wz2)
-        v = v + c * e
+        v = boris_kick(v, e, params.q_over_m, params.B, dt)
         ys.append(wrap(y + dt * v, grid))
     J = field_energy(ys[-1], grid, params, weights)
     ly = field_energy_gradient(ys[-1], grid, params, weights)

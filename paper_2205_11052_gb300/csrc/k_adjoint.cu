@@ -104,7 +104,8 @@ __global__ void k_adj_seed(int64_t ng, const float4 *__restrict__ E4, float4 *__
 }
 
 // reverse push: [ly += (dD/dy)^T lrho of the following step, when given;]
-// lv <- lv + dt ly; le = c lv; ly += (dG/dy . E)^T le + Ext^T le;
+// lv_tot = lv + dt ly; le = c lv_tot, lv <- lv_tot (with B: le = (c/2)(R^T + I)
+// lv_tot, lv <- R^T lv_tot); ly += (dG/dy . E)^T le + Ext^T le;
 // lE += G^T le (shared-memory tile per work item, strays with global atomics;
 // global updates are one 16-byte vector atomic per node).
 //
@@ -131,7 +132,8 @@ __global__ void __launch_bounds__(256, PIC_ADJ_MIN_BLOCKS) k_adj_push(Geom g, co
     const float m_ly = __uint_as_float(ctrl->adj_ly[rd]);
     const float m_lv = __uint_as_float(ctrl->adj_lv[rd]);
     const float m_rho = rt.cell ? __uint_as_float(ctrl->adj_lrho[rd]) : 0.0f;
-    const float m_le = ab.c_abs * (m_lv + ab.dt * (m_ly + ab.kb * m_rho));
+    const float m_le = ab.c_abs * (ab.mag ? 1.3660255f : 1.0f) *
+                       (m_lv + ab.dt * (m_ly + ab.kb * m_rho));
     float qs = 1073741824.0f;   // 2^30 when every |le| is 0
     int nonfinite = 0;
     if (!(m_le <= 3.0e38f)) {
@@ -179,10 +181,27 @@ __global__ void __launch_bounds__(256, PIC_ADJ_MIN_BLOCKS) k_adj_push(Geom g, co
                 ly2 += rt.sz * rz;
             }
             const float fx = yo0[p], fy = yo1[p], fz = yo2[p];
-            const float lv0 = lam.v[0][p] + dt * ly0;
-            const float lv1 = lam.v[1][p] + dt * ly1;
-            const float lv2 = lam.v[2][p] + dt * ly2;
-            const float le0 = c_kick * lv0, le1 = c_kick * lv1, le2 = c_kick * lv2;
+            float lv0 = lam.v[0][p] + dt * ly0;
+            float lv1 = lam.v[1][p] + dt * ly1;
+            float lv2 = lam.v[2][p] + dt * ly2;
+            float le0, le1, le2;
+            if (ab.mag) {
+                // lv <- R^T lv_tot, le = (c/2)(R^T lv_tot + lv_tot)
+                const float r0 = ab.R[0] * lv0 + ab.R[3] * lv1 + ab.R[6] * lv2;
+                const float r1 = ab.R[1] * lv0 + ab.R[4] * lv1 + ab.R[7] * lv2;
+                const float r2 = ab.R[2] * lv0 + ab.R[5] * lv1 + ab.R[8] * lv2;
+                const float hc = 0.5f * c_kick;
+                le0 = hc * (r0 + lv0);
+                le1 = hc * (r1 + lv1);
+                le2 = hc * (r2 + lv2);
+                lv0 = r0;
+                lv1 = r1;
+                lv2 = r2;
+            } else {
+                le0 = c_kick * lv0;
+                le1 = c_kick * lv1;
+                le2 = c_kick * lv2;
+            }
             int nd[8];
             corners(i, j, k, nx, ny, nz, nd);
             float sc[8];

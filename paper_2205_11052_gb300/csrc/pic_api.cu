@@ -527,6 +527,33 @@ int adj_restore(pic_ctx *c, const AdjLayout &L, int seg, int cur) {
     return r ? r : adj_use_items(c, L, seg, 0);
 }
 
+// The Boris rotation R (row-major) of v' = R v + (dt q/m / 2)(R + I) e, from
+// v- -> v- + (v- + v- x t) x s with t = (dt q/m / 2) B, s = 2 t / (1 + |t|^2);
+// *mag = 0 (and R = I) without a magnetic field.
+void boris_rotation(const pic_ctx *c, int *mag, float R[9]) {
+    const double h = 0.5 * c->prm.dt * c->sp.q_over_m;
+    const double t[3] = {h * c->prm.B_ext[0], h * c->prm.B_ext[1], h * c->prm.B_ext[2]};
+    const double tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    const double sc[3] = {2.0 * t[0] / (1.0 + tt), 2.0 * t[1] / (1.0 + tt), 2.0 * t[2] / (1.0 + tt)};
+    *mag = tt > 0.0;
+    for (int j = 0; j < 3; ++j) {   // column j: the rotation of unit vector e_j
+        double v[3] = {0.0, 0.0, 0.0};
+        v[j] = 1.0;
+        const double p[3] = {v[0] + (v[1] * t[2] - v[2] * t[1]), v[1] + (v[2] * t[0] - v[0] * t[2]),
+                             v[2] + (v[0] * t[1] - v[1] * t[0])};
+        const double r[3] = {v[0] + (p[1] * sc[2] - p[2] * sc[1]),
+                             v[1] + (p[2] * sc[0] - p[0] * sc[2]),
+                             v[2] + (p[0] * sc[1] - p[1] * sc[0])};
+        for (int i = 0; i < 3; ++i) R[3 * i + j] = (float)r[i];
+    }
+}
+
+AdjBound step_bound(const AdjBound &ab, int par) {
+    AdjBound b = ab;
+    b.par = par;
+    return b;
+}
+
 // field (x-paired) of step `slot` of the segment being reversed
 int adj_keep_E(pic_ctx *c, const AdjLayout &L, int slot) {
     CopyList cl{};
@@ -1002,9 +1029,6 @@ int pic_adjoint_forward(pic_handle_t c, int n_steps, int K, const double *w, voi
     if (!w || !buf || !J) return fail(PIC_ERR_ARG, "null argument");
     for (int d = 0; d < 3; ++d)
         if (!isfinite(w[d]) || w[d] < 0.0) return fail(PIC_ERR_ARG, "weights must be finite and >= 0");
-    for (int d = 0; d < 3; ++d)
-        if (c->prm.B_ext[d] != 0.0)
-            return fail(PIC_ERR_ARG, "the adjoint of the magnetic rotation is not implemented (B_ext must be 0)");
     if ((uintptr_t)buf % kAlign) return fail(PIC_ERR_ARG, "adjoint buffer not 256-byte aligned");
     const AdjLayout L = adj_layout(c, n_steps, K);
     if (bytes < L.total)
@@ -1067,6 +1091,11 @@ int pic_adjoint_backward(pic_handle_t c, double scale, double *gx, double *gv, i
     const float dt = (float)c->prm.dt, wz2 = (float)c->prm.wz2;
     const float kb = 2.0f * fabsf(qsc) *
                      (float)std::max(c->inv_h[0], std::max(c->inv_h[1], c->inv_h[2]));
+    AdjBound ab{};
+    ab.c_abs = fabsf(c_kick);
+    ab.dt = dt;
+    ab.kb = kb;
+    boris_rotation(c, &ab.mag, ab.R);
     float4 *lE4 = c->at<float4>(c->lay.adjE4);
     const float2 *lrho2 = c->at<float2>(c->lay.lrho2);
 
@@ -1119,7 +1148,7 @@ int pic_adjoint_backward(pic_handle_t c, double scale, double *gx, double *gv, i
                                                                 (size_t)(n - a0) * L.segE);
             PIC_CUDA(launch_adj_push(c->geom, c->ctrl(), c->at<int4>(c->lay.items),
                                      (int)c->max_items, ycell, yo, En, lE4, c_kick, dt, wz2, rt,
-                                     AdjBound{n & 1, fabsf(c_kick), dt, kb}, c->ctrl(), c->st));
+                                     step_bound(ab, n & 1), c->ctrl(), c->st));
             if ((r = adj_solve(c, n & 1))) return r;
             rt.cell = ycell;
             for (int d = 0; d < 3; ++d) rt.o[d] = yo[d];

@@ -176,12 +176,16 @@ cudaError_t launch_copy(const CopyList &cl, cudaStream_t st);
 // The deposit term of the adjoint of one step, (dD/dy)^T lrho evaluated at
 // that step's positions (cell, o) and scaled by q/h_d, folded into the
 // reverse push of the step before it (cell == nullptr: no such term).
-// Scale of the integer accumulation of G^T le in the reverse push of step n:
-// the step's parity and the constants of the bound on |le| (c = dt q/m,
-// kb = 2 max_d |q / h_d| bounds the deposit term per unit |lrho|).
+// Per-step constants of the reverse push of step n: the step's parity and the
+// constants of the bound on |le| that scales the integer accumulation of
+// G^T le (c = dt q/m; kb = 2 max_d |q / h_d| bounds the deposit term per unit
+// |lrho|; with B, |le_d| <= (1 + sqrt 3)/2 |c| max|lv_tot|); with mag set, the
+// Boris rotation R (row-major) of v' = R v + (c/2)(R + I) e.
 struct AdjBound {
     int par;
     float c_abs, dt, kb;
+    int mag;
+    float R[9];
 };
 struct AdjRhoTerm {
     const int32_t *cell;

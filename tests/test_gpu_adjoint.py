@@ -33,21 +33,25 @@ def _small(alpha=0.2, seed=5):
     return w
 
 
-def _oracle(w, n_steps, weights, wz2=0.0):
+def _oracle(w, n_steps, weights, wz2=0.0, B=(0.0, 0.0, 0.0)):
     g = po.Grid(w.n, w.L)
-    p = po.Params(dt=w.dt, Q=w.Q, q_over_m=w.q_over_m, wz2=wz2)
+    p = po.Params(dt=w.dt, Q=w.Q, q_over_m=w.q_over_m, wz2=wz2, B=B)
     return po.run_with_gradient(w.x, w.v, g, p, n_steps, weights)
 
 
 @pytest.mark.parametrize("options", [0, FIXED], ids=["fp32", "fixed"])
-@pytest.mark.parametrize("wz2,weights", [(0.0, (0.0, 0.0, 1.0)), (0.3, (1.0, 1.0, 1.0))])
-def test_gradient_matches_oracle_adjoint(options, wz2, weights):
+@pytest.mark.parametrize("wz2,weights,B", [(0.0, (0.0, 0.0, 1.0), (0.0, 0.0, 0.0)),
+                                           (0.3, (1.0, 1.0, 1.0), (0.0, 0.0, 0.0)),
+                                           (0.3, (1.0, 1.0, 1.0), (0.0, 0.0, 5.0)),
+                                           (0.0, (0.0, 1.0, 1.0), (1.0, -2.0, 3.0))],
+                         ids=["plain", "quadrupole", "penning", "oblique-B"])
+def test_gradient_matches_oracle_adjoint(options, wz2, weights, B):
     w = _small()
     n_steps = 6
-    sim = Simulation.from_workload(w, wz2=wz2, options=options)
+    sim = Simulation.from_workload(w, wz2=wz2, B=B, options=options)
     J = sim.adjoint_forward(n_steps, weights, checkpoint_every=4)
     gx, gv = sim.adjoint_backward()
-    Jo, gxo, gvo = _oracle(w, n_steps, weights, wz2)
+    Jo, gxo, gvo = _oracle(w, n_steps, weights, wz2, B)
     assert J == pytest.approx(Jo, rel=1e-5)
     assert np.max(np.abs(gx - gxo)) <= 1e-4 * np.max(np.abs(gxo))
     assert np.max(np.abs(gv - gvo)) <= 1e-4 * np.max(np.abs(gvo))
@@ -144,13 +148,30 @@ def test_autograd_function_returns_the_library_gradients():
     sim.close()
 
 
-def test_adjoint_rejects_magnetic_fields_and_small_buffers():
-    w = _small()
-    sim = Simulation.from_workload(w, B=(0.0, 0.0, 1.0))
-    with pytest.raises(capi.PicError) as e:
-        sim.adjoint_forward(4)
-    assert e.value.code == capi.PIC_ERR_ARG
+def test_penning_gradient_against_central_differences_of_the_oracle():
+    """A Penning-trap bunch (B_z = 5, quadrupole with axial frequency 1) on a
+    16^3 grid: <dJ/d(x0, v0), delta> against the central difference of the
+    oracle's J, through 10 Boris steps."""
+    w = pi.penning(n=16, n_particles=4096, L=20.0, seed=9)
+    n_steps, weights = 10, (1.0, 1.0, 1.0)
+    sim = Simulation.from_workload(w, options=FIXED)
+    sim.adjoint_forward(n_steps, weights, checkpoint_every=4)
+    gx, gv = sim.adjoint_backward()
     sim.close()
+    g = po.Grid(w.n, w.L)
+    p = po.Params(dt=w.dt, Q=w.Q, q_over_m=w.q_over_m, B=w.B, wz2=w.wz2)
+    rng = np.random.default_rng(4)
+    dX, dV = rng.standard_normal(w.x.shape), rng.standard_normal(w.v.shape)
+    eps = 1e-5
+    Jp = po.run_with_gradient(w.x + eps * dX, w.v + eps * dV, g, p, n_steps, weights)[0]
+    Jm = po.run_with_gradient(w.x - eps * dX, w.v - eps * dV, g, p, n_steps, weights)[0]
+    fd = (Jp - Jm) / (2 * eps)
+    ad = float(np.sum(gx * dX) + np.sum(gv * dV))
+    assert ad == pytest.approx(fd, rel=1e-4)
+
+
+def test_adjoint_rejects_small_buffers_and_missing_forward():
+    w = _small()
     sim = Simulation.from_workload(w)
     buf = torch.empty(1024, dtype=torch.uint8, device="cuda")
     with pytest.raises(capi.PicError) as e:

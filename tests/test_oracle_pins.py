@@ -358,13 +358,17 @@ def test_cic_weight_gradients_are_derivatives_of_the_weights():
         assert np.max(np.abs(fd[same] - dw[same, :, j])) < 1e-6 / float(np.min(grid.h))
 
 
-@pytest.mark.parametrize("wz2,weights", [(0.0, (0.0, 0.0, 1.0)), (0.3, (1.0, 1.0, 1.0))])
-def test_adjoint_matches_central_differences(wz2, weights):
+@pytest.mark.parametrize("wz2,weights,B", [(0.0, (0.0, 0.0, 1.0), (0.0, 0.0, 0.0)),
+                                           (0.3, (1.0, 1.0, 1.0), (0.0, 0.0, 0.0)),
+                                           (0.3, (1.0, 1.0, 1.0), (0.0, 0.0, 5.0)),
+                                           (0.0, (0.0, 1.0, 1.0), (1.0, -2.0, 3.0))])
+def test_adjoint_matches_central_differences(wz2, weights, B):
     """Directional derivative of J along a random (dx0, dv0) equals the
-    adjoint's inner product (J = final weighted field energy, 6 steps)."""
+    adjoint's inner product (J = final weighted field energy, 6 steps), with
+    and without the Boris rotation (R^T in the reverse step)."""
     w = pi.bump_on_tail(n=8, ppc=4, seed=5, alpha=0.2, k=0.5)
     grid = po.Grid(w.n, w.L)
-    p = po.Params(dt=0.1, Q=w.Q, wz2=wz2)
+    p = po.Params(dt=0.1, Q=w.Q, wz2=wz2, B=B)
     J, dx, dv = po.run_with_gradient(w.x, w.v, grid, p, 6, weights)
     rng = np.random.default_rng(1)
     dX = rng.standard_normal(w.x.shape)
@@ -375,6 +379,21 @@ def test_adjoint_matches_central_differences(wz2, weights):
     fd = (Jp - Jm) / (2 * eps)
     ad = float(np.sum(dx * dX) + np.sum(dv * dV))
     assert abs(fd - ad) <= 1e-6 * abs(ad)
+
+
+def test_boris_rotation_matrix_is_the_kick_without_field():
+    """R from the unit-vector kicks is orthogonal, rotates about B by
+    2 arctan(|q/m| |B| dt / 2), and reproduces boris_kick for any (v, e)."""
+    p = po.Params(dt=0.05, Q=-1.0, B=(0.0, 0.0, 5.0))
+    R = po.boris_rotation(p)
+    assert np.allclose(R.T @ R, np.eye(3), atol=1e-14)
+    ang = math.atan2(R[1, 0], R[0, 0])
+    assert abs(abs(ang) - 2.0 * math.atan(0.5 * 5.0 * 0.05)) < 1e-14
+    rng = np.random.default_rng(2)
+    v, e = rng.standard_normal(3), rng.standard_normal(3)
+    h = 0.5 * p.dt * p.q_over_m
+    kick = po.boris_kick(v, e, p.q_over_m, p.B, p.dt)
+    assert np.allclose(kick, R @ v + h * (R @ e + e), atol=1e-14)
 
 
 def test_gradient_with_respect_to_the_perturbation_amplitude():
