@@ -54,6 +54,7 @@ extern "C" {
 /* device error flag bits reported by pic_device_flags() */
 #define PIC_FLAG_NONFINITE   1  /* a non-finite position, velocity or field value */
 #define PIC_FLAG_BAD_CELL    2  /* a particle cell index outside the grid          */
+#define PIC_FLAG_TIMEOUT     4  /* a bounded wait inside a kernel gave up           */
 
 typedef struct pic_ctx *pic_handle_t;
 

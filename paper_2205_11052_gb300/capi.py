@@ -22,6 +22,7 @@ PIC_ERR_STATE = -7
 
 PIC_FLAG_NONFINITE = 1
 PIC_FLAG_BAD_CELL = 2
+PIC_FLAG_TIMEOUT = 4
 
 ERROR_NAMES = {
     PIC_ERR_ARG: "PIC_ERR_ARG",

@@ -75,6 +75,62 @@ __device__ __forceinline__ int table_slot(int32_t *hkey, int key, int size) {
     return -1;
 }
 
+#ifndef PIC_SORT_STAGE
+#define PIC_SORT_STAGE 512
+#endif
+constexpr int kStage = PIC_SORT_STAGE;     // particles per staged slice
+constexpr int kHash = 256;                 // slots of the per-slice tile table
+constexpr int kPerThread = kStage / 256;   // the staged kernels run 256 threads per block
+#ifndef PIC_HIST_STAGE
+#define PIC_HIST_STAGE 2048
+#endif
+constexpr int kHistStage = PIC_HIST_STAGE;   // particles per histogram slice
+constexpr int kHistPer = kHistStage / 256;
+
+// ---- bulk asynchronous copies (TMA) into shared memory, mbarrier completion ----
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// bounded wait for the phase of the given parity; false if it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Block-staged scatter.  A block takes kStage consecutive particles into
 // shared memory, finds the slice's distinct destination tiles with a small
 // shared hash table (a slice comes from one or two tiles plus strays into
@@ -82,25 +138,34 @@ __device__ __forceinline__ int table_slot(int32_t *hkey, int key, int size) {
 // with one atomic, and writes every tile's particles contiguously.  A slice
 // with more distinct tiles than the table holds (the first binning of
 // particles in arbitrary order) falls back to per-warp claims.
-#ifndef PIC_SORT_STAGE
-#define PIC_SORT_STAGE 512
-#endif
-constexpr int kStage = PIC_SORT_STAGE;
-constexpr int kHash = 256;
-constexpr int kPerThread = kStage / 256;   // the staged kernels run 256 threads per block
+//
+// The slices a block walks are double-buffered: while one is processed, the
+// eight arrays of its next slice arrive by bulk asynchronous copies (2 KB
+// each, completion counted on an mbarrier); a partial last slice is loaded
+// with plain loads.  Every wait is bounded: a copy that never completes
+// raises PIC_FLAG_TIMEOUT and the block stops.
+constexpr int kArrays = 8;                                   // cell, o[3], v[3], pid
+constexpr size_t kBufBytes = (size_t)kStage * 4 * kArrays;   // one staged slice
+constexpr size_t kStageSmem =
+    2 * kBufBytes + (size_t)kStage * 4 + (size_t)kHash * 12 + 2 * sizeof(uint64_t);
+
+__device__ __forceinline__ const void *src_array(const ParticleSet &s, int a) {
+    if (a == 0) return s.cell;
+    if (a < 4) return s.o[a - 1];
+    if (a < 7) return s.v[a - 4];
+    return s.pid;
+}
 
 __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl *ctrl,
                                                          int32_t *bins) {
-    extern __shared__ uint32_t smem[];
-    int32_t *sc = reinterpret_cast<int32_t *>(smem);          // kStage cells
-    float *so = reinterpret_cast<float *>(sc + kStage);        // 3 x kStage offsets
-    float *sv = so + 3 * kStage;                               // 3 x kStage velocities
-    int32_t *sid = reinterpret_cast<int32_t *>(sv + 3 * kStage);   // kStage ids
-    uint16_t *slid = reinterpret_cast<uint16_t *>(sid + kStage);   // kStage table slots
-    uint16_t *srank = slid + kStage;                               // kStage ranks
-    int32_t *hkey = reinterpret_cast<int32_t *>(srank + kStage);   // kHash keys
-    int32_t *hcnt = hkey + kHash;                                  // kHash counts
-    int32_t *hbase = hcnt + kHash;                                 // kHash global bases
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint32_t *buf0 = reinterpret_cast<uint32_t *>(smem);
+    uint16_t *slid = reinterpret_cast<uint16_t *>(smem + 2 * kBufBytes);    // kStage table slots
+    uint16_t *srank = slid + kStage;                                         // kStage ranks
+    int32_t *hkey = reinterpret_cast<int32_t *>(srank + kStage);             // kHash keys
+    int32_t *hcnt = hkey + kHash;                                            // kHash counts
+    int32_t *hbase = hcnt + kHash;                                           // kHash global bases
+    uint64_t *bar = reinterpret_cast<uint64_t *>(hbase + kHash);             // 2 mbarriers
     __shared__ int overflow;
 
     const int cur = ctrl->cur;
@@ -108,19 +173,49 @@ __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl 
     const ParticleSet dst = ctrl->sets[1 - cur];
     const int64_t nslices = (n + kStage - 1) / kStage;
     int bad = 0;
-    for (int64_t sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    // issue the bulk copies of a full slice into buffer b (thread 0)
+    auto issue = [&](int64_t sl, int b) {
+        uint32_t *bb = buf0 + (size_t)b * kStage * kArrays;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar[b], (uint32_t)kBufBytes);
+        for (int a = 0; a < kArrays; ++a)
+            bulk_load(bb + (size_t)a * kStage,
+                      static_cast<const uint32_t *>(src_array(src, a)) + sl * kStage,
+                      (uint32_t)(kStage * 4), &bar[b]);
+    };
+    uint32_t phase[2] = {0u, 0u};
+    int b = 0;
+    int64_t sl = blockIdx.x;
+    if (sl < nslices && (sl + 1) * kStage <= n && threadIdx.x == 0) issue(sl, 0);
+    for (; sl < nslices; sl += gridDim.x, b ^= 1) {
         const int64_t s0 = sl * kStage;
         const int m = (int)(s0 + kStage <= n ? kStage : n - s0);
+        uint32_t *bb = buf0 + (size_t)b * kStage * kArrays;
+        int32_t *sc = reinterpret_cast<int32_t *>(bb);
+        float *so = reinterpret_cast<float *>(bb + kStage);          // 3 x kStage offsets
+        float *sv = reinterpret_cast<float *>(bb + 4 * kStage);      // 3 x kStage velocities
+        int32_t *sid = reinterpret_cast<int32_t *>(bb + 7 * kStage); // kStage ids
         for (int h = threadIdx.x; h < kHash; h += blockDim.x) {
             hkey[h] = -1;
             hcnt[h] = 0;
         }
         if (threadIdx.x == 0) overflow = 0;
-        // all of the slice's loads in flight at once (kStage / 256 per thread)
-#pragma unroll
-        for (int u = 0; u < kPerThread; ++u) {
-            const int j = u * 256 + threadIdx.x;
-            if (j < m) {
+        if (m == kStage) {
+            const bool ok = mbar_wait(&bar[b], phase[b]);
+            phase[b] ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicOr(&ctrl->flags, PIC_FLAG_TIMEOUT);
+                mbar_wait(&bar[b], phase[b] ^ 1u);   // one more bounded wait for the copies
+                return;
+            }
+        } else {
+            for (int j = threadIdx.x; j < m; j += blockDim.x) {
                 const int64_t p = s0 + j;
                 sc[j] = __ldcs(src.cell + p);
                 so[j] = __ldcs(src.o[0] + p);
@@ -131,8 +226,13 @@ __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl 
                 sv[2 * kStage + j] = __ldcs(src.v[2] + p);
                 sid[j] = __ldcs(src.pid + p);
             }
+            __syncthreads();
         }
-        __syncthreads();
+        // the next slice of this block streams into the other buffer meanwhile
+        {
+            const int64_t nx = sl + gridDim.x;
+            if (nx < nslices && (nx + 1) * kStage <= n && threadIdx.x == 0) issue(nx, b ^ 1);
+        }
         // slot of each particle's tile in the table and its rank there; the
         // first lane of each run of equal keys in a warp acts for the run
         for (int jb = 0; jb < m; jb += blockDim.x) {
@@ -203,7 +303,7 @@ __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl 
                 }
             }
         }
-        __syncthreads();
+        __syncthreads();   // buffer b and the table are free again
     }
     if (bad) atomicOr(&ctrl->flags, PIC_FLAG_BAD_CELL);
 }
@@ -216,25 +316,25 @@ __global__ void __launch_bounds__(256) k_histogram_staged(int64_t n, Geom g, Ctr
     __shared__ int32_t hkey[kHash];
     __shared__ int32_t hcnt[kHash];
     const ParticleSet ps = ctrl->sets[ctrl->cur];
-    const int64_t nslices = (n + kStage - 1) / kStage;
+    const int64_t nslices = (n + kHistStage - 1) / kHistStage;
     int bad = 0;
     for (int64_t sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
-        const int64_t s0 = sl * kStage;
-        const int m = (int)(s0 + kStage <= n ? kStage : n - s0);
+        const int64_t s0 = sl * kHistStage;
+        const int m = (int)(s0 + kHistStage <= n ? kHistStage : n - s0);
         for (int h = threadIdx.x; h < kHash; h += blockDim.x) {
             hkey[h] = -1;
             hcnt[h] = 0;
         }
         __syncthreads();
-        // the slice's cells first (kStage / 256 loads in flight per thread)
-        int32_t cv[kPerThread];
+        // the slice's cells first (kHistStage / 256 loads in flight per thread)
+        int32_t cv[kHistPer];
 #pragma unroll
-        for (int u = 0; u < kPerThread; ++u) {
+        for (int u = 0; u < kHistPer; ++u) {
             const int j = u * 256 + threadIdx.x;
             cv[u] = j < m ? __ldcs(ps.cell + s0 + j) : 0;
         }
 #pragma unroll
-        for (int u = 0; u < kPerThread; ++u) {
+        for (int u = 0; u < kHistPer; ++u) {
             const int j = u * 256 + threadIdx.x;
             const bool act = j < m;
             const int lane = threadIdx.x & 31;
@@ -254,7 +354,6 @@ __global__ void __launch_bounds__(256) k_histogram_staged(int64_t n, Geom g, Ctr
     if (bad) atomicOr(&ctrl->flags, PIC_FLAG_BAD_CELL);
 }
 
-constexpr size_t kStageSmem = (size_t)kStage * (4 + 12 + 12 + 4 + 2 + 2) + (size_t)kHash * 12;
 
 // ---- exclusive scan of int32 (in place), total written to data[n] -------------
 
@@ -410,7 +509,7 @@ cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t
     if (e != cudaSuccess) return e;
     const int T = 256;
     if (n > 0) {
-        const int hblocks = (int)std::min<int64_t>((n + kStage - 1) / kStage, 152 * 8);
+        const int hblocks = (int)std::min<int64_t>((n + kHistStage - 1) / kHistStage, 152 * 8);
         k_histogram_staged<<<hblocks, T, 0, st>>>(n, g, ctrl, bins);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
