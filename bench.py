@@ -60,9 +60,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--workload", default="landau", choices=["landau", "ensemble", "adjoint"],
-                    help="landau: the benchmark step; ensemble: batched instances vs per-instance "
-                         "launches; adjoint: only the adjoint cost measurement")
+    ap.add_argument("--workload", default="landau",
+                    choices=["landau", "uniform", "ensemble", "adjoint"],
+                    help="landau: the benchmark step; uniform: the uniform plasma test (random "
+                         "moves instead of the push) on the same grid; ensemble: batched instances "
+                         "vs per-instance launches; adjoint: only the adjoint cost measurement")
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--ens-count", type=int, default=512, help="ensemble instances")
     ap.add_argument("--record-traffic", metavar="NCU_CSV",
@@ -74,6 +76,9 @@ def parse():
 
 def workload_name(args):
     n = args.grid
+    if args.workload == "uniform":
+        return (f"uniform_plasma_3d (random moves in [-h, h)): {n}^3 grid, {args.ppc} "
+                f"particles/cell ({n ** 3 * args.ppc:,} particles), L=4pi, dt={args.dt:g}")
     return (f"landau_damping_3d: {n}^3 grid, {args.ppc} particles/cell "
             f"({n ** 3 * args.ppc:,} particles), L=4pi, alpha=0.05, k=0.5, dt={args.dt:g}")
 
@@ -171,28 +176,39 @@ class ClockSampler:
 
 def oracle_sample(args, n_particles):
     """A bounded sample of the benchmark workload: the same grid and physics,
-    n_particles drawn from the same Landau distribution."""
+    n_particles drawn from the same distribution."""
     import pic_inputs as pi
 
     ppc = max(1, -(-n_particles // args.grid ** 3))
-    w = pi.landau(n=args.grid, ppc=ppc, seed=1001, dt=args.dt)
+    if args.workload == "uniform":
+        w = pi.uniform_plasma(n=args.grid, ppc=ppc, seed=1004, dt=args.dt)
+    else:
+        w = pi.landau(n=args.grid, ppc=ppc, seed=1001, dt=args.dt)
     if w.n_particles > n_particles:
         w.x = w.x[:n_particles].copy()
         w.v = w.v[:n_particles].copy()
     return w
 
 
-def time_oracle(w, steps, warmup=0):
+def time_oracle(w, steps, warmup=0, uniform=False):
     from oracle import pic_oracle as po
 
     g = po.Grid(w.n, w.L)
     p = po.Params(dt=w.dt, q_over_m=w.q_over_m, Q=w.Q, B=w.B, wz2=w.wz2)
+
+    def one(x, v, n, diag):
+        if uniform:
+            out = po.step_uniform(x, v, g, p, n, 2022, with_diag=diag)
+        else:
+            out = po.step(x, v, g, p, with_diag=diag)
+        return out[0], out[1]
+
     x, v = w.x, w.v
-    for _ in range(warmup):
-        x, v = po.step(x, v, g, p)
+    for n in range(warmup):
+        x, v = one(x, v, n, False)
     t0 = time.perf_counter()
-    for _ in range(steps):
-        x, v, _ = po.step(x, v, g, p, with_diag=True)
+    for n in range(steps):
+        x, v = one(x, v, warmup + n, True)
     dt = time.perf_counter() - t0
     return w.n_particles * steps / dt, dt
 
@@ -201,7 +217,7 @@ def run_reference(args, rank):
     if rank != 0:
         return
     w = oracle_sample(args, args.cpu_sample)
-    val, secs = time_oracle(w, args.steps, args.warmup)
+    val, secs = time_oracle(w, args.steps, args.warmup, uniform=args.workload == "uniform")
     sample = (f"{w.n_particles:,} particles of the workload on the full {args.grid}^3 grid, "
               f"{args.steps} oracle steps (numpy FP64, single thread)")
     line = {
@@ -422,11 +438,17 @@ def main():
     build()
 
     # ---- inputs: seeded synthetic Landau damping (per-rank seed offset)
-    w = pi.landau(n=args.grid, ppc=args.ppc, seed=1001 + rank, n_steps=args.steps, dt=args.dt)
+    options = args.options
+    if args.workload == "uniform":
+        w = pi.uniform_plasma(n=args.grid, ppc=args.ppc, seed=1004 + rank, n_steps=args.steps,
+                              dt=args.dt)
+        options |= capi.PIC_OPT_UNIFORM_MOVE
+    else:
+        w = pi.landau(n=args.grid, ppc=args.ppc, seed=1001 + rank, n_steps=args.steps, dt=args.dt)
     N = w.n_particles
     ng = args.grid ** 3
-    sim = Simulation.from_workload(w, sort_period=args.sort_period, options=args.options,
-                                   diag_every=args.diag_every, guard=args.guard)
+    sim = Simulation.from_workload(w, sort_period=args.sort_period, options=options,
+                                   diag_every=args.diag_every, guard=args.guard, seed=2022 + rank)
     stream = sim.stream
 
     def barrier():
@@ -468,6 +490,11 @@ def main():
     # per particle), E read once (16 B per node), rho written once (4 B per node)
     algo = {"push": 56.0 * N + 20.0 * ng, "deposit": 16.0 * N + 4.0 * ng}
     kernel_names = {"push": "k_push_deposit", "deposit": "k_deposit_tiles"}
+    if args.workload == "uniform":
+        # random move + deposit: cell, offsets and pid read, cell and offsets
+        # written (36 B), velocities read for the moments when diagnostics run
+        algo["push"] = (48.0 if args.diag_every > 0 else 36.0) * N + 4.0 * ng
+        kernel_names["push"] = "k_move_deposit"
     dom = max(algo, key=lambda k: phases[k][0])
     avg_ms = phases[dom][0] / max(1, phases[dom][1])
     achieved = algo[dom] / (avg_ms * 1e-3) / 1e9
@@ -479,8 +506,8 @@ def main():
                 tj = json.load(f)
             ent = tj.get(kernel_names[dom])
             # the record is for the 128^3 x 64 workload in the default launch configuration
-            same = (args.grid, args.ppc, args.sort_period, args.options, args.guard, args.dt) == \
-                (128, 64, LAUNCH["sort_period"], LAUNCH["options"], 0, 0.05)
+            same = (args.workload, args.grid, args.ppc, args.sort_period, args.options, args.guard,
+                    args.dt) == ("landau", 128, 64, LAUNCH["sort_period"], LAUNCH["options"], 0, 0.05)
             if same and ent and ent.get("source_sha") == _source_sha(ent.get("source")):
                 traffic = ent["bytes_per_launch_full_size"]
         except Exception:
@@ -522,7 +549,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         ws = oracle_sample(args, args.cpu_sample)
-        val, secs = time_oracle(ws, 2)
+        val, secs = time_oracle(ws, 2, uniform=args.workload == "uniform")
         cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{ws.n_particles:,} particles of the workload on the full "
                          f"{args.grid}^3 grid, 2 oracle steps ({secs:.1f} s, numpy FP64, "

@@ -90,6 +90,7 @@ typedef struct {
     int32_t chunk;         /* max particles per deposit work item, 32..4095
                               (default 4095)                                     */
     int32_t options;       /* PIC_OPT_* bits (default 0)                         */
+    uint64_t seed;         /* random stream of PIC_OPT_UNIFORM_MOVE              */
 } pic_params_t;
 
 /* options: accumulate the deposit in 2^-20 fixed point (u32 shared-memory
@@ -97,6 +98,15 @@ typedef struct {
  * the deposit is then deterministic and conserves charge exactly; weights are
  * rounded to 2^-20 (relative error below 1e-6 of a node's charge). */
 #define PIC_OPT_FIXED_DEPOSIT 1
+/* The uniform plasma test (Section 4.4): each step moves every particle by an
+ * independent uniform displacement in [-h_d, h_d) per axis instead of the
+ * gather and push; deposit, field solve and diagnostics run as usual and the
+ * velocities are left unchanged.  The displacement of axis d of the particle
+ * loaded as number pid in step n is (2u - 1) h_d with u = (r >> 40) 2^-24,
+ * r = the c-th output of the SplitMix64 generator (Steele, Lea and Flood,
+ * 2014) seeded with params.seed, c = ((n 2^32) + pid) 4 + d + 1.  Not
+ * available with the adjoint or in ensembles. */
+#define PIC_OPT_UNIFORM_MOVE 2
 
 /* Sizes the caller must provide before any device work. */
 typedef struct {

@@ -422,6 +422,57 @@ def field_energy_gradient(y: np.ndarray, grid: Grid, params: Params, weights=(1.
     return (qp / grid.cell_volume) * np.einsum("pc,pcj->pj", lr, dw)
 
 
+# ---------------------------------------------------------------------------
+# uniform plasma test (Section 4.4)
+# ---------------------------------------------------------------------------
+
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, c: np.ndarray) -> np.ndarray:
+    """The c-th outputs (c >= 1, uint64 array) of the SplitMix64 generator
+    seeded with `seed` (Steele, Lea and Flood, 2014): state seed + c * golden
+    gamma, then the two xor-shift-multiply rounds and a final xor-shift."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & _M64) + np.asarray(c, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform_displacement(n: int, pid: np.ndarray, seed: int) -> np.ndarray:
+    """(N, 3) displacements in cell units, uniform in [-1, 1): axis d of particle
+    pid in step n uses output c = ((n 2^32) + pid) 4 + d + 1, u = its top 24
+    bits times 2^-24, displacement 2u - 1."""
+    pid = np.asarray(pid, dtype=np.uint64)
+    base = (np.uint64(n) << np.uint64(32)) + pid
+    out = np.empty((pid.shape[0], 3), dtype=np.float64)
+    for d in range(3):
+        c = base * np.uint64(4) + np.uint64(d + 1)
+        u = (splitmix64(seed, c) >> np.uint64(40)).astype(np.float64) * 2.0 ** -24
+        out[:, d] = 2.0 * u - 1.0
+    return out
+
+
+def step_uniform(x: np.ndarray, v: np.ndarray, grid: Grid, params: Params, n: int, seed: int,
+                 pid=None, with_diag=False, mode=(1, 0, 0), mode_comp=0):
+    """One step of the uniform plasma test: the scatter and field solve of the
+    drift-kick-drift cycle (at x_h = x_n + dt/2 v_n), then every particle
+    moves by a uniform random displacement in [-h, h) per axis instead of the
+    gather and push; velocities unchanged."""
+    N = x.shape[0]
+    qp = params.Q / N if N else 0.0
+    xh = wrap(x + 0.5 * params.dt * v, grid)
+    rho = deposit(xh, grid, qp)
+    E = solve_field(rho, grid)
+    if pid is None:
+        pid = np.arange(N)
+    x1 = wrap(x + uniform_displacement(n, pid, seed) * np.asarray(grid.h), grid)
+    if with_diag:
+        return x1, v, diagnostics(rho, E, v, grid, params, N, mode, mode_comp)
+    return x1, v
+
+
 def boris_rotation(params: Params) -> np.ndarray:
     """The rotation R of the Boris kick: boris_kick(v, e) = R v + (dt q/m / 2)(R + I) e.
     Its columns are the kicks of the unit vectors with e = 0."""

@@ -49,10 +49,11 @@ class pic_params_t(C.Structure):
                 ("tile", C.c_int32 * 3), ("guard", C.c_int32), ("sort_period", C.c_int32),
                 ("diag_every", C.c_int32), ("diag_capacity", C.c_int32),
                 ("mode", C.c_int32 * 3), ("mode_comp", C.c_int32), ("block", C.c_int32),
-                ("chunk", C.c_int32), ("options", C.c_int32)]
+                ("chunk", C.c_int32), ("options", C.c_int32), ("seed", C.c_uint64)]
 
 
 PIC_OPT_FIXED_DEPOSIT = 1
+PIC_OPT_UNIFORM_MOVE = 2
 
 
 class pic_bufsizes_t(C.Structure):

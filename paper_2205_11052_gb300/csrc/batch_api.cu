@@ -239,7 +239,9 @@ int pic_batch_create(const pic_instance_t *inst, int n_inst, double q_over_m,
     if (params->guard < 0 || params->guard > 8) return record_error(PIC_ERR_ARG, "guard outside 0..8");
     if (params->diag_every < 0 || params->diag_capacity < 0) return record_error(PIC_ERR_ARG, "negative diagnostic setting");
     if (params->mode_comp < 0 || params->mode_comp > 2) return record_error(PIC_ERR_ARG, "mode_comp must be 0, 1 or 2");
-    if (params->options & ~PIC_OPT_FIXED_DEPOSIT) return record_error(PIC_ERR_ARG, "unknown option bits");
+    if (params->options & ~PIC_OPT_FIXED_DEPOSIT)
+        return record_error(PIC_ERR_ARG, "unknown option bits (the uniform-plasma move is not "
+                                         "available in ensembles)");
     for (int d = 0; d < 3; ++d)
         if (params->tile[d] < 0 || !isfinite(params->B_ext[d])) return record_error(PIC_ERR_ARG, "bad tile or B_ext");
     if (!isfinite(params->wz2)) return record_error(PIC_ERR_ARG, "wz2 must be finite");

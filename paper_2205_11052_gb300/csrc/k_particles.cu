@@ -376,6 +376,166 @@ cudaError_t launch_gather_push(int64_t n, const Geom &g, const PushConst &pc, bo
 
 namespace pic {
 
+// ---------------------------------------------------------------------------
+// uniform plasma test (Section 4.4): random displacements instead of the push
+// ---------------------------------------------------------------------------
+
+// c-th output (c >= 1) of the SplitMix64 generator seeded with `seed`
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t c) {
+    uint64_t z = seed + c * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// displacement along axis d (in cells, in [-1, 1)) of particle pid in step n:
+// 2u - 1 with u = the top 24 bits of output ((n 2^32 + pid) 4 + d + 1)
+__device__ __forceinline__ float move_cells(uint64_t seed, long long n, int32_t pid, int d) {
+    const uint64_t c = (((uint64_t)n << 32) + (uint64_t)(uint32_t)pid) * 4ull + (uint64_t)d + 1ull;
+    const uint32_t r = (uint32_t)(splitmix64(seed, c) >> 40);
+    return (float)r * (1.0f / 8388608.0f) - 1.0f;   // exact: r < 2^24
+}
+
+__device__ __forceinline__ void move_one(const Geom &g, uint64_t seed, long long n, int32_t pid,
+                                         int32_t &c, float &fx, float &fy, float &fz, int &bad) {
+    int i, j, k;
+    decode_base(g, c, i, j, k, bad);
+    advance_cells(g, fx + move_cells(seed, n, pid, 0), fy + move_cells(seed, n, pid, 1),
+                  fz + move_cells(seed, n, pid, 2), i, j, k, c, fx, fy, fz, bad);
+}
+
+template <bool DIAG>
+__device__ __forceinline__ void block_moments(const float (&a)[4], double *part) {
+    if (!DIAG) return;
+    double d[4] = {(double)a[0], (double)a[1], (double)a[2], (double)a[3]};
+    __shared__ double red[4][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = 0; q < 4; ++q) {
+        double tt = d[q];
+        for (int o = 16; o > 0; o >>= 1) tt += __shfl_down_sync(0xffffffffu, tt, o);
+        if (lane == 0) red[q][wid] = tt;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double tt = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tt += red[threadIdx.x][w];
+        part[4 * blockIdx.x + threadIdx.x] = tt;
+    }
+}
+
+// the random move of every particle with the deposit of the new positions
+// (the work items and shared tiles of k_push_deposit); velocities untouched
+template <bool DIAG, bool FIXED>
+__global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_move_deposit(
+    Geom g, uint64_t seed, Ctrl *ctrl, const int4 *__restrict__ items, float *rho,
+    unsigned long long *rho64, float qscale, int sparse_below, double *__restrict__ part) {
+    extern __shared__ uint32_t acc[];
+    const ParticleSet ps = ctrl->sets[ctrl->cur];
+    const int n_items = ctrl->n_items;
+    const long long n = ctrl->step;   // advanced after this kernel (k_step_inc)
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    int bad = 0;
+    unsigned long long strays = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int4 item = items[it];
+        const bool sparse = item.z - item.y < sparse_below;
+        const cic::Tile t = cic::tile_of(g, item.x);
+        if (!sparse) {
+            for (int s = threadIdx.x; s < t.S; s += blockDim.x) acc[s] = 0u;
+            __syncthreads();
+        }
+        for (int p = item.y + threadIdx.x; p < item.z; p += blockDim.x) {
+            int32_t c = __ldcs(ps.cell + p);
+            float fx = __ldcs(ps.o[0] + p), fy = __ldcs(ps.o[1] + p), fz = __ldcs(ps.o[2] + p);
+            move_one(g, seed, n, ps.pid[p], c, fx, fy, fz, bad);
+            const int i = cell_i(c), j = cell_j(c), k = cell_k(c);
+            if (sparse) {
+                float w[8];
+                cic::weights(fx, fy, fz, w);
+                cic::deposit_global<FIXED>(rho, rho64, g, i, j, k, w, fx, fy, fz, qscale);
+            } else if (!cic::tile_add<FIXED>(acc, t, g, i, j, k, fx, fy, fz, rho, rho64, qscale)) {
+                ++strays;
+            }
+            if (DIAG) {
+                const float vx = ps.v[0][p], vy = ps.v[1][p], vz = ps.v[2][p];
+                a[0] += vx;
+                a[1] += vy;
+                a[2] += vz;
+                a[3] += vx * vx + vy * vy + vz * vz;
+            }
+            __stcs(ps.cell + p, c);
+            __stcs(ps.o[0] + p, fx);
+            __stcs(ps.o[1] + p, fy);
+            __stcs(ps.o[2] + p, fz);
+        }
+        if (!sparse) {
+            __syncthreads();
+            cic::tile_flush<FIXED>(acc, t, g, rho, rho64, qscale);
+            __syncthreads();
+        }
+    }
+    if (bad) raise_flag(ctrl, bad);
+    if (strays) atomicAdd(&ctrl->stray, strays);
+    block_moments<DIAG>(a, part);
+}
+
+// the random move alone (split calls: pic_gather_push)
+template <bool DIAG>
+__global__ void __launch_bounds__(256) k_move(int64_t np, Geom g, uint64_t seed, Ctrl *ctrl,
+                                               double *__restrict__ part) {
+    const ParticleSet ps = ctrl->sets[ctrl->cur];
+    const long long n = ctrl->step;
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    int bad = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += stride) {
+        int32_t c = ps.cell[p];
+        float fx = ps.o[0][p], fy = ps.o[1][p], fz = ps.o[2][p];
+        move_one(g, seed, n, ps.pid[p], c, fx, fy, fz, bad);
+        ps.cell[p] = c;
+        ps.o[0][p] = fx;
+        ps.o[1][p] = fy;
+        ps.o[2][p] = fz;
+        if (DIAG) {
+            const float vx = ps.v[0][p], vy = ps.v[1][p], vz = ps.v[2][p];
+            a[0] += vx;
+            a[1] += vy;
+            a[2] += vz;
+            a[3] += vx * vx + vy * vy + vz * vz;
+        }
+    }
+    if (bad) raise_flag(ctrl, bad);
+    block_moments<DIAG>(a, part);
+}
+
+__global__ void k_step_inc(Ctrl *ctrl) { ctrl->step += 1; }
+
+cudaError_t launch_move(int64_t np, const Geom &g, uint64_t seed, bool diag, bool fixed, bool deposit,
+                        Ctrl *ctrl, const int4 *items, int max_items, float *rho,
+                        unsigned long long *rho64, double qscale, int sparse_below, double *part,
+                        int blocks, cudaStream_t st) {
+    const int nb = std::max(1, std::min(blocks, deposit ? max_items : blocks));
+    if (deposit) {
+        const size_t smem = push_deposit_smem(g);
+        const float qs = (float)qscale;
+        if (diag) {
+            if (fixed) k_move_deposit<true, true><<<nb, 256, smem, st>>>(g, seed, ctrl, items, rho, rho64, qs, sparse_below, part);
+            else k_move_deposit<true, false><<<nb, 256, smem, st>>>(g, seed, ctrl, items, rho, rho64, qs, sparse_below, part);
+        } else {
+            if (fixed) k_move_deposit<false, true><<<nb, 256, smem, st>>>(g, seed, ctrl, items, rho, rho64, qs, sparse_below, part);
+            else k_move_deposit<false, false><<<nb, 256, smem, st>>>(g, seed, ctrl, items, rho, rho64, qs, sparse_below, part);
+        }
+    } else {
+        if (diag) k_move<true><<<nb, 256, 0, st>>>(np, g, seed, ctrl, part);
+        else k_move<false><<<nb, 256, 0, st>>>(np, g, seed, ctrl, part);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_step_inc<<<1, 1, 0, st>>>(ctrl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return (deposit && fixed) ? launch_rho_finish(g, rho64, rho, qscale, st) : cudaSuccess;
+}
+
 size_t push_deposit_smem(const Geom &g) {
     const cic::Tile t0 = cic::tile_of(g, 0);
     return sizeof(uint32_t) * (size_t)t0.S;   // the deposit tile

@@ -336,12 +336,20 @@ int do_solve(pic_ctx *c) {
     return timer_end(c, PIC_PHASE_SOLVE, 2);
 }
 
+bool uniform_move(const pic_ctx *c) { return (c->prm.options & PIC_OPT_UNIFORM_MOVE) != 0; }
+
 int do_gather_push(pic_ctx *c, bool diag) {
     int r = timer_begin(c, PIC_PHASE_PUSH);
     if (r) return r;
-    PIC_CUDA(launch_gather_push(c->np, c->geom, push_const(c), diag, c->ctrl(),
-                                c->at<float4>(c->lay.E8), c->at<double>(c->lay.ppart),
-                                push_blocks_of(c), c->block, c->st));
+    if (uniform_move(c) && c->np > 0) {
+        PIC_CUDA(launch_move(c->np, c->geom, c->prm.seed, diag, false, false, c->ctrl(), nullptr, 0,
+                             nullptr, nullptr, 0.0, 0, c->at<double>(c->lay.ppart),
+                             push_blocks_of(c), c->st));
+    } else {
+        PIC_CUDA(launch_gather_push(c->np, c->geom, push_const(c), diag, c->ctrl(),
+                                    c->at<float4>(c->lay.E8), c->at<double>(c->lay.ppart),
+                                    push_blocks_of(c), c->block, c->st));
+    }
     c->step += 1;
     c->since_sort += 1;
     c->rho_current = false;
@@ -377,7 +385,13 @@ int do_push_deposit(pic_ctx *c, bool diag, const SaveY &save = SaveY{}) {
         PIC_CUDA(cudaMemsetAsync(c->at<float>(c->lay.rho), 0, (size_t)c->ng * 4, c->st));
     int r = timer_begin(c, PIC_PHASE_PUSH);
     if (r) return r;
-    if (c->np > 0) {
+    if (c->np > 0 && uniform_move(c)) {
+        PIC_CUDA(launch_move(c->np, c->geom, c->prm.seed, diag, fixed, true, c->ctrl(),
+                             c->at<int4>(c->lay.items), (int)c->max_items, c->at<float>(c->lay.rho),
+                             c->at<unsigned long long>(c->lay.rho64), qscale_of(c),
+                             c->sparse_below, c->at<double>(c->lay.ppart), fused_blocks_of(c),
+                             c->st));
+    } else if (c->np > 0) {
         PIC_CUDA(launch_push_deposit(c->geom, push_const(c), diag, fixed, c->ctrl(),
                                      c->at<int4>(c->lay.items), (int)c->max_items,
                                      c->at<float4>(c->lay.E8), c->at<float>(c->lay.rho),
@@ -698,7 +712,8 @@ int pic_create(const pic_grid_t *grid, const pic_species_t *species, const pic_p
         return fail(PIC_ERR_ARG, "block must be 0 or a multiple of 32 in 32..256");
     if (params->chunk != 0 && (params->chunk < 32 || params->chunk > kMaxChunk))
         return fail(PIC_ERR_ARG, "chunk must be 0 or in 32..%d", kMaxChunk);
-    if (params->options & ~PIC_OPT_FIXED_DEPOSIT) return fail(PIC_ERR_ARG, "unknown option bits");
+    if (params->options & ~(PIC_OPT_FIXED_DEPOSIT | PIC_OPT_UNIFORM_MOVE))
+        return fail(PIC_ERR_ARG, "unknown option bits");
 
     pic_ctx *c = new (std::nothrow) pic_ctx();
     if (!c) return fail(PIC_ERR_ARG, "out of host memory");
@@ -1030,6 +1045,7 @@ int pic_adjoint_forward(pic_handle_t c, int n_steps, int K, const double *w, voi
     for (int d = 0; d < 3; ++d)
         if (!isfinite(w[d]) || w[d] < 0.0) return fail(PIC_ERR_ARG, "weights must be finite and >= 0");
     if ((uintptr_t)buf % kAlign) return fail(PIC_ERR_ARG, "adjoint buffer not 256-byte aligned");
+    if (uniform_move(c)) return fail(PIC_ERR_ARG, "the uniform-plasma move has no adjoint");
     const AdjLayout L = adj_layout(c, n_steps, K);
     if (bytes < L.total)
         return fail(PIC_ERR_CAPACITY, "adjoint buffer of %zu bytes < required %zu", bytes, L.total);

@@ -130,6 +130,13 @@ cudaError_t launch_deposit(int64_t n, const Geom &g, const Ctrl *ctrl, const int
 
 cudaError_t launch_rho_finish(const Geom &g, unsigned long long *rho64, float *rho, double qscale,
                               cudaStream_t st);
+// the uniform-plasma random move (PIC_OPT_UNIFORM_MOVE) of every particle,
+// with the deposit of the new positions when `deposit` (then over the work
+// items, like launch_push_deposit); advances the device step counter
+cudaError_t launch_move(int64_t np, const Geom &g, uint64_t seed, bool diag, bool fixed, bool deposit,
+                        Ctrl *ctrl, const int4 *items, int max_items, float *rho,
+                        unsigned long long *rho64, double qscale, int sparse_below, double *part,
+                        int blocks, cudaStream_t st);
 // dynamic shared memory of the fused push + deposit kernel for geometry g,
 // and the one-time attribute setting it needs above 48 KiB
 size_t push_deposit_smem(const Geom &g);

@@ -12,6 +12,10 @@
 
 namespace pic {
 
+__device__ __forceinline__ void advance_cells(const Geom &g, float sx, float sy, float sz, int i,
+                                              int j, int k, int32_t &c, float &fx, float &fy,
+                                              float &fz, int &bad);
+
 // CIC interpolation of the eight corner values (corner bits a | b<<1 | c<<2)
 __device__ __forceinline__ void interp_E(const float4 e[8], float fx, float fy, float fz,
                                         float &ex, float &ey, float &ez) {
@@ -116,9 +120,17 @@ __device__ __forceinline__ void kick_drift(const Geom &g, const PushConst &pc, f
     vz = mz + pc.qm_half_dt * ez;
 
     // drift a full step in cell units, carry into the cell index, wrap
-    const float sx = fx + pc.dt_over_h[0] * vx;
-    const float sy = fy + pc.dt_over_h[1] * vy;
-    const float sz = fz + pc.dt_over_h[2] * vz;
+    advance_cells(g, fx + pc.dt_over_h[0] * vx, fy + pc.dt_over_h[1] * vy,
+                  fz + pc.dt_over_h[2] * vz, i, j, k, c, fx, fy, fz, bad);
+}
+
+// New in-cell offsets s (in cell units, relative to the stencil base
+// (i, j, k)): carry floor(s) into the cell index, keep the fraction, wrap
+// periodically, repack the cell
+__device__ __forceinline__ void advance_cells(const Geom &g, float sx, float sy, float sz, int i,
+                                              int j, int k, int32_t &c, float &fx, float &fy,
+                                              float &fz, int &bad) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     float flx = floorf(sx), fly = floorf(sy), flz = floorf(sz);
     fx = sx - flx;
     fy = sy - fly;

@@ -300,6 +300,34 @@ def test_two_stream_growth_rate_on_a_quiet_lattice():
     assert omega < 0.01
 
 
+def test_splitmix64_matches_its_published_outputs():
+    """The first outputs of SplitMix64 from seeds 0 and 1234567 as published
+    with the generator's reference implementation."""
+    c = np.array([1, 2, 3], dtype=np.uint64)
+    assert [int(r) for r in po.splitmix64(0, c)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                                    0x06C45D188009454F]
+    assert [int(r) for r in po.splitmix64(1234567, c[:2])] == [6457827717110365317,
+                                                              3203168211198807973]
+
+
+def test_uniform_displacements_are_uniform_and_keep_velocities():
+    """Section 4.4: displacements fill [-1, 1) cells uniformly (mean 0,
+    variance 1/3), differ by step, particle and axis, and the step leaves
+    the velocities alone."""
+    d = po.uniform_displacement(5, np.arange(200_000), seed=7)
+    assert d.min() >= -1.0 and d.max() < 1.0
+    assert abs(d.mean()) < 3e-3 and abs(d.var() - 1.0 / 3.0) < 3e-3
+    assert not np.array_equal(d, po.uniform_displacement(6, np.arange(200_000), seed=7))
+    assert abs(np.corrcoef(d[:, 0], d[:, 1])[0, 1]) < 1e-2
+    w = pi.uniform_plasma(n=8, ppc=4, seed=3)
+    g = po.Grid(w.n, w.L)
+    x1, v1 = po.step_uniform(w.x, w.v, g, po.Params(dt=0.05, Q=w.Q), 0, seed=7)
+    assert np.array_equal(v1, w.v)
+    dx = x1 - w.x
+    dx -= np.asarray(w.L) * np.round(dx / np.asarray(w.L))
+    assert np.all(np.abs(dx) <= np.asarray(g.h) + 1e-12)
+
+
 def test_diagnostics_field_energy_of_a_known_field():
     grid = po.Grid((8, 8, 8), (2.0, 2.0, 2.0))
     E = np.zeros((3,) + grid.shape)
