@@ -61,10 +61,11 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--workload", default="landau",
-                    choices=["landau", "uniform", "ensemble", "adjoint"],
+                    choices=["landau", "uniform", "penning", "ensemble", "adjoint"],
                     help="landau: the benchmark step; uniform: the uniform plasma test (random "
-                         "moves instead of the push) on the same grid; ensemble: batched instances "
-                         "vs per-instance launches; adjoint: only the adjoint cost measurement")
+                         "moves instead of the push) on the same grid; penning: the Penning-trap "
+                         "bunch (256^3, 1.3e8 particles, Boris + quadrupole); ensemble: batched "
+                         "instances vs per-instance launches; adjoint: only the adjoint cost")
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--ens-count", type=int, default=512, help="ensemble instances")
     ap.add_argument("--record-traffic", metavar="NCU_CSV",
@@ -76,6 +77,9 @@ def parse():
 
 def workload_name(args):
     n = args.grid
+    if args.workload == "penning":
+        return (f"penning_trap_3d: {n}^3 grid on [0,20)^3, 130,000,000 particles in a Gaussian "
+                f"bunch sigma=(1,1,2), Bz=5, axial frequency 1, Q=-1562.5, dt={args.dt:g}")
     if args.workload == "uniform":
         return (f"uniform_plasma_3d (random moves in [-h, h)): {n}^3 grid, {args.ppc} "
                 f"particles/cell ({n ** 3 * args.ppc:,} particles), L=4pi, dt={args.dt:g}")
@@ -182,6 +186,8 @@ def oracle_sample(args, n_particles):
     ppc = max(1, -(-n_particles // args.grid ** 3))
     if args.workload == "uniform":
         w = pi.uniform_plasma(n=args.grid, ppc=ppc, seed=1004, dt=args.dt)
+    elif args.workload == "penning":
+        w = pi.penning(n=args.grid, n_particles=n_particles, seed=1002, dt=args.dt)
     else:
         w = pi.landau(n=args.grid, ppc=ppc, seed=1001, dt=args.dt)
     if w.n_particles > n_particles:
@@ -439,7 +445,9 @@ def main():
 
     # ---- inputs: seeded synthetic Landau damping (per-rank seed offset)
     options = args.options
-    if args.workload == "uniform":
+    if args.workload == "penning":
+        w = pi.penning(n=args.grid, seed=1002 + rank, dt=args.dt)
+    elif args.workload == "uniform":
         w = pi.uniform_plasma(n=args.grid, ppc=args.ppc, seed=1004 + rank, n_steps=args.steps,
                               dt=args.dt)
         options |= capi.PIC_OPT_UNIFORM_MOVE

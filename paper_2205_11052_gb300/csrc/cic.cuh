@@ -195,5 +195,50 @@ __device__ __forceinline__ void tile_flush(const uint32_t *acc, const Tile &t, c
     }
 }
 
+// Second level of a block's deposit: the block walks a contiguous run of
+// work items, folds each item's tile into `sum` (FIXED: 64-bit sums of the
+// 32-bit item tiles, which cannot overflow; FP32: float sums) and flushes
+// `sum` to the grid only when the run moves to another tile, so the items of
+// one densely filled tile cost one set of grid atomics per block instead of
+// one per item.  Each slot is touched by one thread in both loops.
+template <bool FIXED>
+__device__ __forceinline__ void tile_fold(uint32_t *acc, void *sum, int S) {
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        if (FIXED) reinterpret_cast<unsigned long long *>(sum)[s] += acc[s];
+        else reinterpret_cast<float *>(sum)[s] += __uint_as_float(acc[s]);
+        acc[s] = 0u;
+    }
+}
+
+template <bool FIXED>
+__device__ __forceinline__ void tile_flush_sum(void *sum, const Tile &t, const Geom &g, float *rho,
+                                               unsigned long long *rho64, float qscale) {
+    const int G = g.guard;
+    for (int s = threadIdx.x; s < t.S; s += blockDim.x) {
+        unsigned long long q = 0ull;
+        float f = 0.0f;
+        if (FIXED) {
+            q = reinterpret_cast<unsigned long long *>(sum)[s];
+            reinterpret_cast<unsigned long long *>(sum)[s] = 0ull;
+        } else {
+            f = reinterpret_cast<float *>(sum)[s];
+            reinterpret_cast<float *>(sum)[s] = 0.0f;
+        }
+        if (FIXED ? q != 0ull : f != 0.0f) {
+            int a, b, cz;
+            tile_pos(t, s, a, b, cz);
+            const int gi = wrap_index(t.ox - G + a, g.n[0]);
+            const int gj = wrap_index(t.oy - G + b, g.n[1]);
+            const int gk = wrap_index(t.oz - G + cz, g.n[2]);
+            const int64_t node = gi + (int64_t)g.n[0] * (gj + (int64_t)g.n[1] * gk);
+            if (FIXED) atomicAdd(rho64 + node, q);
+            else atomicAdd(rho + node, f * qscale);
+        }
+    }
+}
+
+// the two shared tiles of a block: 32-bit item tile, then the 8-byte sums
+__host__ __device__ __forceinline__ size_t sum_offset(int S) { return ((size_t)S * 4 + 7) & ~(size_t)7; }
+
 }  // namespace cic
 }  // namespace pic

@@ -224,19 +224,33 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g,
                                                           float qscale, int sparse_below,
                                                           double *__restrict__ part,
                                                           SaveY save) {
-    extern __shared__ uint32_t acc[];
+    extern __shared__ __align__(16) uint32_t acc[];
     const ParticleSet ps = ctrl->sets[ctrl->cur];
     const int n_items = ctrl->n_items;
     float a[4] = {0.f, 0.f, 0.f, 0.f};
     int bad = 0;
     unsigned long long strays = 0;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    // a contiguous run of work items per block (consecutive items share tiles)
+    const int per = (n_items + gridDim.x - 1) / gridDim.x;
+    const int it0 = min(n_items, (int)blockIdx.x * per), it1 = min(n_items, it0 + per);
+    const int S = cic::tile_of(g, 0).S;
+    void *sum = reinterpret_cast<char *>(acc) + cic::sum_offset(S);
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        acc[s] = 0u;
+        if (FIXED) reinterpret_cast<unsigned long long *>(sum)[s] = 0ull;
+        else reinterpret_cast<float *>(sum)[s] = 0.0f;
+    }
+    __syncthreads();
+    int cur_tile = -1;
+    cic::Tile tc = cic::tile_of(g, 0);
+    for (int it = it0; it < it1; ++it) {
         const int4 item = items[it];
         const bool sparse = item.z - item.y < sparse_below;
         const cic::Tile t = cic::tile_of(g, item.x);
-        if (!sparse) {
-            for (int s = threadIdx.x; s < t.S; s += blockDim.x) acc[s] = 0u;
-            __syncthreads();
+        if (!sparse && item.x != cur_tile) {
+            if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, tc, g, rho, rho64, qscale);
+            cur_tile = item.x;
+            tc = t;
         }
         // one particle per thread and iteration (coalesced 4-byte streams)
         for (int p = item.y + threadIdx.x; p < item.z; p += blockDim.x) {
@@ -261,10 +275,11 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g,
         }
         if (!sparse) {
             __syncthreads();
-            cic::tile_flush<FIXED>(acc, t, g, rho, rho64, qscale);
+            cic::tile_fold<FIXED>(acc, sum, S);
             __syncthreads();
         }
     }
+    if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, tc, g, rho, rho64, qscale);
     if (bad) raise_flag(ctrl, bad);
     if (strays) atomicAdd(&ctrl->stray, strays);
     if (DIAG) {
@@ -429,20 +444,33 @@ template <bool DIAG, bool FIXED>
 __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_move_deposit(
     Geom g, uint64_t seed, Ctrl *ctrl, const int4 *__restrict__ items, float *rho,
     unsigned long long *rho64, float qscale, int sparse_below, double *__restrict__ part) {
-    extern __shared__ uint32_t acc[];
+    extern __shared__ __align__(16) uint32_t acc[];
     const ParticleSet ps = ctrl->sets[ctrl->cur];
     const int n_items = ctrl->n_items;
     const long long n = ctrl->step;   // advanced after this kernel (k_step_inc)
     float a[4] = {0.f, 0.f, 0.f, 0.f};
     int bad = 0;
     unsigned long long strays = 0;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int per = (n_items + gridDim.x - 1) / gridDim.x;
+    const int it0 = min(n_items, (int)blockIdx.x * per), it1 = min(n_items, it0 + per);
+    const int S = cic::tile_of(g, 0).S;
+    void *sum = reinterpret_cast<char *>(acc) + cic::sum_offset(S);
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        acc[s] = 0u;
+        if (FIXED) reinterpret_cast<unsigned long long *>(sum)[s] = 0ull;
+        else reinterpret_cast<float *>(sum)[s] = 0.0f;
+    }
+    __syncthreads();
+    int cur_tile = -1;
+    cic::Tile tc = cic::tile_of(g, 0);
+    for (int it = it0; it < it1; ++it) {
         const int4 item = items[it];
         const bool sparse = item.z - item.y < sparse_below;
         const cic::Tile t = cic::tile_of(g, item.x);
-        if (!sparse) {
-            for (int s = threadIdx.x; s < t.S; s += blockDim.x) acc[s] = 0u;
-            __syncthreads();
+        if (!sparse && item.x != cur_tile) {
+            if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, tc, g, rho, rho64, qscale);
+            cur_tile = item.x;
+            tc = t;
         }
         for (int p = item.y + threadIdx.x; p < item.z; p += blockDim.x) {
             int32_t c = __ldcs(ps.cell + p);
@@ -470,10 +498,11 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_move_deposit(
         }
         if (!sparse) {
             __syncthreads();
-            cic::tile_flush<FIXED>(acc, t, g, rho, rho64, qscale);
+            cic::tile_fold<FIXED>(acc, sum, S);
             __syncthreads();
         }
     }
+    if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, tc, g, rho, rho64, qscale);
     if (bad) raise_flag(ctrl, bad);
     if (strays) atomicAdd(&ctrl->stray, strays);
     block_moments<DIAG>(a, part);
@@ -538,7 +567,7 @@ cudaError_t launch_move(int64_t np, const Geom &g, uint64_t seed, bool diag, boo
 
 size_t push_deposit_smem(const Geom &g) {
     const cic::Tile t0 = cic::tile_of(g, 0);
-    return sizeof(uint32_t) * (size_t)t0.S;   // the deposit tile
+    return cic::sum_offset(t0.S) + 8 * (size_t)t0.S;   // item tile + the block's tile sums
 }
 
 // Allow the fused kernel's shared memory (call outside any stream capture)
