@@ -662,6 +662,39 @@ int adj_solve(pic_ctx *c, int par) {
     return PIC_OK;
 }
 
+// Device address of `bytes` of page-locked host memory mapped into the GPU's
+// address space (e.g. from cudaHostAlloc or torch's pin_memory), or nullptr
+// when the range is ordinary pageable memory.  Both ends must resolve into
+// the same mapping.  On this Grace-coupled part kernels then read and write
+// the host buffers directly over the chip-to-chip link instead of staging
+// them through copies.
+const void *mapped_host(const void *p, size_t bytes) {
+#if PIC_ZERO_COPY
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const char *last = static_cast<const char *>(p) + bytes - 1;
+    if (cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer ||
+        !b.devicePointer)
+        return nullptr;
+    if (static_cast<const char *>(b.devicePointer) - static_cast<const char *>(a.devicePointer) !=
+        (ptrdiff_t)(bytes - 1))
+        return nullptr;
+    return a.devicePointer;
+#else
+    (void)p;
+    (void)bytes;
+    return nullptr;
+#endif
+}
+
 // Reset the resettable head of the control block (everything before `cur`).
 int reset_ctrl(pic_ctx *c) {
     PIC_CUDA(cudaMemsetAsync(c->ctrl(), 0, offsetof(Ctrl, cur), c->st));
@@ -881,8 +914,14 @@ int pic_load_particles(pic_handle_t c, const double *x, const double *v, int64_t
                                 (long long)n, (long long)c->cap);
     if (n > 0 && (!x || !v)) return fail(PIC_ERR_ARG, "null particle array");
     if ((r = reset_ctrl(c))) return r;
+    const double *mx = src_is_device ? nullptr
+                                     : static_cast<const double *>(mapped_host(x, (size_t)n * 24));
+    const double *mv = mx ? static_cast<const double *>(mapped_host(v, (size_t)n * 24)) : nullptr;
     if (src_is_device) {
         PIC_CUDA(launch_load(x, v, n, 0, c->geom, c->inv_h, c->prm.dt, c->ctrl(), c->st));
+    } else if (mx && mv) {
+        // page-locked host arrays: read in place by the load kernel
+        PIC_CUDA(launch_load(mx, mv, n, 0, c->geom, c->inv_h, c->prm.dt, c->ctrl(), c->st));
     } else {
         double *sx = c->at<double>(c->lay.stage_x), *sv = c->at<double>(c->lay.stage_v);
         for (int64_t o = 0; o < n; o += c->staging) {
@@ -909,6 +948,16 @@ int pic_get_particles(pic_handle_t c, double *x, double *v, int dst_is_device) {
     PIC_CUDA(launch_invperm(c->np, c->ctrl(), inv, c->st));
     if (dst_is_device) {
         PIC_CUDA(launch_unload(0, c->np, inv, c->geom, c->h, c->L, c->prm.dt, c->ctrl(), x, v, c->st));
+        return PIC_OK;
+    }
+    double *mx = static_cast<double *>(const_cast<void *>(mapped_host(x, (size_t)c->np * 24)));
+    double *mv = mx ? static_cast<double *>(const_cast<void *>(mapped_host(v, (size_t)c->np * 24)))
+                    : nullptr;
+    if (mx && mv) {
+        // page-locked host arrays: written in place by the unload kernel
+        PIC_CUDA(launch_unload(0, c->np, inv, c->geom, c->h, c->L, c->prm.dt, c->ctrl(), mx, mv,
+                               c->st));
+        PIC_CUDA(cudaStreamSynchronize(c->st));
         return PIC_OK;
     }
     double *sx = c->at<double>(c->lay.stage_x), *sv = c->at<double>(c->lay.stage_v);
