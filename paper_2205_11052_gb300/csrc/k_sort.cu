@@ -135,7 +135,11 @@ __device__ __forceinline__ void fence_proxy_async() {
 // shared memory, finds the slice's distinct destination tiles with a small
 // shared hash table (a slice comes from one or two tiles plus strays into
 // their neighbours, i.e. a few dozen keys), claims one global range per tile
-// with one atomic, and writes every tile's particles contiguously.  A slice
+// with one atomic, and writes every tile's particles contiguously, in
+// destination order (a slice-local scan of the table's counts gives each
+// particle its position in the slice's output runs; thread t then writes the
+// t-th particle of those runs, so a warp's stores fall into one or two runs of
+// consecutive addresses even when half the slice changes tile).  A slice
 // with more distinct tiles than the table holds (the first binning of
 // particles in arbitrary order) falls back to per-warp claims.
 //
@@ -146,8 +150,9 @@ __device__ __forceinline__ void fence_proxy_async() {
 // raises PIC_FLAG_TIMEOUT and the block stops.
 constexpr int kArrays = 8;                                   // cell, o[3], v[3], pid
 constexpr size_t kBufBytes = (size_t)kStage * 4 * kArrays;   // one staged slice
-constexpr size_t kStageSmem =
-    2 * kBufBytes + (size_t)kStage * 4 + (size_t)kHash * 12 + 2 * sizeof(uint64_t);
+static_assert(kHash == 256, "the staged scatter scans its table with one thread per slot");
+constexpr size_t kStageSmem = 2 * kBufBytes + (size_t)kStage * 4 + (size_t)kHash * 12 +
+                              2 * sizeof(uint64_t) + (size_t)kStage * 2;
 
 __device__ __forceinline__ const void *src_array(const ParticleSet &s, int a) {
     if (a == 0) return s.cell;
@@ -166,7 +171,9 @@ __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl 
     int32_t *hcnt = hkey + kHash;                                            // kHash counts
     int32_t *hbase = hcnt + kHash;                                           // kHash global bases
     uint64_t *bar = reinterpret_cast<uint64_t *>(hbase + kHash);             // 2 mbarriers
+    uint16_t *inv = reinterpret_cast<uint16_t *>(bar + 2);                   // kStage positions
     __shared__ int overflow;
+    __shared__ int wsum[8];
 
     const int cur = ctrl->cur;
     const ParticleSet src = ctrl->sets[cur];
@@ -284,13 +291,35 @@ __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl 
                 }
             }
         } else {
-            for (int h = threadIdx.x; h < kHash; h += blockDim.x)
-                if (hcnt[h] > 0) hbase[h] = atomicAdd(bins + hkey[h], hcnt[h]);
+            {
+                // claim, then turn hcnt into the slots' slice-local offsets
+                // (exclusive scan, one thread per slot)
+                const int h = threadIdx.x, lane = h & 31, w = h >> 5;
+                const int cnt = hcnt[h];
+                if (cnt > 0) hbase[h] = atomicAdd(bins + hkey[h], cnt);
+                int incl = cnt;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (lane == 31) wsum[w] = incl;
+                __syncthreads();
+                int before = 0;
+                for (int q = 0; q < w; ++q) before += wsum[q];
+                hcnt[h] = before + incl - cnt;
+            }
             __syncthreads();
 #pragma unroll
             for (int u = 0; u < kPerThread; ++u) {
                 const int j = u * 256 + threadIdx.x;
-                if (j < m) {
+                if (j < m) inv[hcnt[slid[j]] + srank[j]] = (uint16_t)j;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < kPerThread; ++u) {
+                const int t = u * 256 + threadIdx.x;
+                if (t < m) {
+                    const int j = inv[t];
                     const int q = hbase[slid[j]] + srank[j];
                     dst.cell[q] = sc[j];
                     dst.o[0][q] = so[j];

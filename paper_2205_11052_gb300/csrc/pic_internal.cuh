@@ -94,11 +94,11 @@ constexpr int kMaxSmemPerBlock = 227 * 1024;   // opt-in shared memory per block
 #ifndef PIC_PD_MIN_BLOCKS
 #define PIC_PD_MIN_BLOCKS 4
 #endif
-// resident blocks per SM the reverse push is compiled for
 // read and write page-locked host particle arrays in place (no staging copies)
 #ifndef PIC_ZERO_COPY
 #define PIC_ZERO_COPY 1
 #endif
+// resident blocks per SM the reverse push is compiled for
 #ifndef PIC_ADJ_MIN_BLOCKS
 #define PIC_ADJ_MIN_BLOCKS 4
 #endif
