@@ -162,7 +162,7 @@ __device__ __forceinline__ const void *src_array(const ParticleSet &s, int a) {
 }
 
 __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl *ctrl,
-                                                         int32_t *bins) {
+                                                         int32_t *bins, int shift) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint32_t *buf0 = reinterpret_cast<uint32_t *>(smem);
     uint16_t *slid = reinterpret_cast<uint16_t *>(smem + 2 * kBufBytes);    // kStage table slots
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl 
             const int j = jb + threadIdx.x;
             const bool act = j < m;
             const int lane = threadIdx.x & 31;
-            const int key = act ? tile_key(sc[j], g, bad) : -1 - lane;
+            const int key = act ? tile_key(sc[j], g, bad) >> shift : -1 - lane;
             const WarpRun r = warp_run(key);
             int h = 0, base = 0;
             if (act && lane == r.head) {
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl 
                 const bool act = j < m;
                 const unsigned active = __ballot_sync(0xffffffffu, act);
                 if (act) {
-                    const int key = tile_key(sc[j], g, bad);
+                    const int key = tile_key(sc[j], g, bad) >> shift;
                     const unsigned peers = __match_any_sync(active, key);
                     const int leader = __ffs(peers) - 1;
                     int old = 0;
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl 
 // distinct tiles in a shared hash table, one global atomic per tile and
 // slice (per-warp aggregated atomics when the table overflows).
 __global__ void __launch_bounds__(256) k_histogram_staged(int64_t n, Geom g, Ctrl *ctrl,
-                                                           int32_t *bins) {
+                                                           int32_t *bins, int shift) {
     __shared__ int32_t hkey[kHash];
     __shared__ int32_t hcnt[kHash];
     const ParticleSet ps = ctrl->sets[ctrl->cur];
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256) k_histogram_staged(int64_t n, Geom g, Ctr
             const int j = u * 256 + threadIdx.x;
             const bool act = j < m;
             const int lane = threadIdx.x & 31;
-            const int key = act ? tile_key(cv[u], g, bad) : -1 - lane;
+            const int key = act ? tile_key(cv[u], g, bad) >> shift : -1 - lane;
             const WarpRun r = warp_run(key);
             if (act && lane == r.head) {
                 const int h = table_slot(hkey, key, kHash);
@@ -505,6 +505,8 @@ __global__ void k_fill_items(int ntiles, int chunk, const int32_t *__restrict__ 
     }
 }
 
+__global__ void k_flip(Ctrl *ctrl) { ctrl->cur = 1 - ctrl->cur; }
+
 }  // namespace
 
 cudaError_t exclusive_scan(int32_t *data, int64_t n, int32_t *tmp, cudaStream_t st) {
@@ -531,25 +533,66 @@ cudaError_t sort_prepare() {
                                 (int)kStageSmem);
 }
 
-cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t *bins,
-                        int64_t nbins, int32_t *scan_tmp, int32_t *tile_items,
-                        int2 *tile_range, int4 *items, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(nbins + 1), st);
+// histogram, scan and staged scatter by tile key >> shift (nb keys)
+cudaError_t sort_pass(int64_t n, const Geom &g, int shift, int64_t nb, Ctrl *ctrl, int32_t *bins,
+                      int32_t *scan_tmp, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(nb + 1), st);
     if (e != cudaSuccess) return e;
     const int T = 256;
     if (n > 0) {
         const int hblocks = (int)std::min<int64_t>((n + kHistStage - 1) / kHistStage, 152 * 8);
-        k_histogram_staged<<<hblocks, T, 0, st>>>(n, g, ctrl, bins);
+        k_histogram_staged<<<hblocks, T, 0, st>>>(n, g, ctrl, bins, shift);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if ((e = exclusive_scan_impl(bins, nbins, scan_tmp, st)) != cudaSuccess) return e;
+    if ((e = exclusive_scan_impl(bins, nb, scan_tmp, st)) != cudaSuccess) return e;
     if (n > 0) {
         // resident blocks per SM as the staging buffer allows (228 KB per SM)
         const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (228 * 1024) / (kStageSmem + 1024)));
         const int sblocks = (int)std::min<int64_t>((n + kStage - 1) / kStage, 152 * per_sm);
-        k_scatter_staged<<<sblocks, T, kStageSmem, st>>>(n, g, ctrl, bins);
+        k_scatter_staged<<<sblocks, T, kStageSmem, st>>>(n, g, ctrl, bins, shift);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    return cudaSuccess;
+}
+
+// Shifts of the coarse passes that precede the full-key pass for particles in
+// arbitrary order: the first leaves at most 128 keys, each later one splits a
+// bucket of the previous pass into at most 64, so a 512-particle slice (which
+// spans one or two buckets of the pass before) meets at most 128 distinct keys
+// and never overflows the staged table.
+int coarse_shifts(int ntiles, int *shifts) {
+    int bits = 0;
+    while ((1 << bits) < ntiles) ++bits;
+    int k = 0;
+    for (int sft = bits - 7; sft > 0; sft -= 6) shifts[k++] = sft;
+    return k;
+}
+
+int sort_launches(int64_t n, int ntiles, bool presort) {
+    int sh[8];
+    const int passes = (presort && n > 0) ? coarse_shifts(ntiles, sh) : 0;
+    // per coarse pass: histogram, 3 scan, scatter, flip; then the full-key pass
+    // (histogram, 3 scan, scatter) and the work list (ranges, 3 scan, fill)
+    return passes * 6 + (n > 0 ? 10 : 8);
+}
+
+cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t *bins,
+                        int64_t nbins, int32_t *scan_tmp, int32_t *tile_items,
+                        int2 *tile_range, int4 *items, bool presort, cudaStream_t st) {
+    cudaError_t e;
+    if (presort && n > 0) {
+        const int nt = g.ntile[0] * g.ntile[1] * g.ntile[2];
+        int sh[8];
+        const int passes = coarse_shifts(nt, sh);
+        for (int p = 0; p < passes; ++p) {
+            if ((e = sort_pass(n, g, sh[p], ((nt - 1) >> sh[p]) + 1, ctrl, bins, scan_tmp, st)))
+                return e;
+            k_flip<<<1, 1, 0, st>>>(ctrl);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    if ((e = sort_pass(n, g, 0, nbins, ctrl, bins, scan_tmp, st)) != cudaSuccess) return e;
+    const int T = 256;
     const int ntiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
     const int tb = (ntiles + T - 1) / T;
     k_tile_ranges<<<tb, T, 0, st>>>(bins, ntiles, chunk, tile_items, tile_range);

@@ -293,16 +293,16 @@ int timer_end(pic_ctx *c, int ph, int kernels) {
     return PIC_OK;
 }
 
-int do_sort(pic_ctx *c) {
+// presort: the store is in arbitrary order (right after a load)
+int do_sort(pic_ctx *c, bool presort = false) {
     int r = timer_begin(c, PIC_PHASE_SORT);
     if (r) return r;
     PIC_CUDA(launch_sort(c->np, c->geom, c->chunk, c->ctrl(), c->at<int32_t>(c->lay.bins),
                          c->nbins, c->at<int32_t>(c->lay.scan_tmp),
                          c->at<int32_t>(c->lay.tile_items), c->at<int2>(c->lay.tile_range),
-                         c->at<int4>(c->lay.items), c->st));
+                         c->at<int4>(c->lay.items), presort, c->st));
     c->since_sort = 0;
-    // histogram, 3 scan, scatter, ranges, 3 scan, fill (histogram/scatter skipped when empty)
-    return timer_end(c, PIC_PHASE_SORT, c->np > 0 ? 10 : 8);
+    return timer_end(c, PIC_PHASE_SORT, sort_launches(c->np, (int)c->ntiles, presort));
 }
 
 int do_deposit(pic_ctx *c) {
@@ -935,7 +935,7 @@ int pic_load_particles(pic_handle_t c, const double *x, const double *v, int64_t
     c->step = 0;
     c->loaded = true;
     c->rho_current = false;
-    if ((r = do_sort(c))) return r;
+    if ((r = do_sort(c, true))) return r;
     if (!src_is_device) PIC_CUDA(cudaStreamSynchronize(c->st));
     return PIC_OK;
 }

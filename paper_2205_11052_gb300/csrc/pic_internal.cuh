@@ -123,9 +123,13 @@ cudaError_t sort_prepare();   // kernel attributes; call once per device outside
 cudaError_t launch_worklist(const int32_t *bin_end, int ntiles, int chunk, int32_t *tile_items,
                             int2 *tile_range, int4 *items, int32_t *scan_tmp, Ctrl *ctrl, int flip,
                             cudaStream_t st);
+// presort: the particles are in arbitrary order (just loaded); coarse passes
+// by tile key >> shift run first so that no slice overflows the staged table
 cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t *bins,
                         int64_t nbins, int32_t *scan_tmp, int32_t *tile_items,
-                        int2 *tile_range, int4 *items, cudaStream_t st);
+                        int2 *tile_range, int4 *items, bool presort, cudaStream_t st);
+// kernels launch_sort issues
+int sort_launches(int64_t n, int ntiles, bool presort);
 
 cudaError_t launch_deposit(int64_t n, const Geom &g, const Ctrl *ctrl, const int4 *items,
                            int max_items, double qscale, float *rho, unsigned long long *rho64,

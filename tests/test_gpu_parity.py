@@ -130,6 +130,41 @@ def test_deposit_is_independent_of_tiling(tile, guard, chunk, options):
     sim.close()
 
 
+@pytest.mark.parametrize("n,tile,ppc", [((32, 32, 32), (2, 2, 2), 4),     # 4096 tiles: 1 coarse pass
+                                         ((64, 64, 32), (2, 2, 2), 2),     # 16384 tiles: 2 passes
+                                         ((36, 20, 28), (3, 2, 2), 3),     # 1680 tiles, ragged keys
+                                         ((32, 32, 32), (2, 2, 2), 0.1)])  # sparse: slices overflow
+def test_first_binning_of_arbitrary_order_with_many_tiles(n, tile, ppc):
+    """The load's coarse pre-passes (tile key >> shift) and the full-key pass
+    bin particles given in random order: readback, deposit and one step agree
+    with the oracle."""
+    n_cells = int(np.prod(n))
+    w = pi.landau(n=n, ppc=max(1, int(ppc)), seed=31, alpha=0.2)
+    if ppc < 1:
+        keep = int(ppc * n_cells)
+        w.x = w.x[:keep].copy()
+        w.v = w.v[:keep].copy()
+    rng = np.random.default_rng(5)
+    order = rng.permutation(w.x.shape[0])
+    w.x = w.x[order].copy()
+    w.v = w.v[order].copy()
+    sim = Simulation.from_workload(w, tile=tile, options=1)
+    x, v = sim.particles()
+    assert _pos_err_in_cells(x, w.x, w) < 1e-6
+    assert np.max(np.abs(v - w.v)) <= 1e-6 * max(1.0, np.max(np.abs(w.v)))
+    sim.deposit()
+    rho, _ = sim.field()
+    rho_o = po.deposit(_oracle_half_step_positions(w), _grid(w), w.Q / w.n_particles)
+    assert np.max(np.abs(rho - rho_o)) <= TOL * np.max(np.abs(rho_o))
+    sim.step(1)
+    x1, v1 = sim.particles()
+    xo, vo = po.step(w.x, w.v, _grid(w), _params(w))
+    assert _pos_err_in_cells(x1, xo, w) <= 1e-5
+    assert np.max(np.abs(v1 - vo)) <= 1e-5 * np.max(np.abs(vo))
+    assert sim.flags() == 0
+    sim.close()
+
+
 @pytest.mark.parametrize("options", [0, 1], ids=["fp32", "fixed"])
 def test_deposit_of_strays_after_many_steps_without_rebinning(options):
     """Particles far outside their tile since the last sort still deposit exactly."""
