@@ -23,28 +23,62 @@ __device__ __forceinline__ void raise_flag(Ctrl *ctrl, int bit) { atomicOr(&ctrl
 // ---------------------------------------------------------------------------
 // load: FP64 (x_0, v_0) -> x_{1/2} = x_0 + dt/2 v_0 -> (cell, offset, v)
 // ---------------------------------------------------------------------------
-__global__ void k_load(const double *__restrict__ x, const double *__restrict__ v, int64_t m,
-                       int64_t base, Geom g, double ih0, double ih1, double ih2, double dt,
-                       Ctrl *ctrl) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= m) return;
+constexpr int kLoadThreads = 256;
+
+__global__ void __launch_bounds__(kLoadThreads) k_load(const double *__restrict__ x,
+                                                      const double *__restrict__ v, int64_t m,
+                                                      int64_t base, Geom g, double ih0,
+                                                      double ih1, double ih2, double dt,
+                                                      Ctrl *ctrl) {
+    // the block's 256 (x, y, z) triples of x and of v are read as contiguous
+    // runs (every byte once, six independent loads per thread) and staged in
+    // shared memory: the source may be host memory read over the chip-to-chip
+    // link, where strided 8-byte reads would fetch each line three times
+    __shared__ double sx[3 * kLoadThreads], sv[3 * kLoadThreads];
+    const int64_t p0 = (int64_t)blockIdx.x * kLoadThreads;
+    const int cnt = (int)(m - p0 < kLoadThreads ? m - p0 : kLoadThreads);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int j = r * kLoadThreads + threadIdx.x;
+        if (j < 3 * cnt) {
+            sx[j] = x[3 * p0 + j];
+            sv[j] = v[3 * p0 + j];
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x >= cnt) return;
+    const int64_t p = p0 + threadIdx.x;
     const ParticleSet ps = ctrl->sets[ctrl->cur];
     const double ih[3] = {ih0, ih1, ih2};
+    double xr[3], vr[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        xr[d] = sx[3 * threadIdx.x + d];
+        vr[d] = sv[3 * threadIdx.x + d];
+    }
     int idx[3];
     float off[3];
     bool ok = true;
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
-        double vd = v[3 * p + d];
-        double xd = x[3 * p + d] + 0.5 * dt * vd;
+        double vd = vr[d];
+        double xd = xr[d] + 0.5 * dt * vd;
         double s = xd * ih[d] - 0.5;      // node g at (g + 1/2) h
-        if (!isfinite(s) || !isfinite(vd) || fabs(s) > 4.0e15) {
+        // finite v and |s| < 2^52, tested on the exponent fields (FP64
+        // instructions are scarce on this GPU; integer ones are not)
+        const unsigned es = (unsigned)((unsigned long long)__double_as_longlong(s) >> 52) & 0x7ffu;
+        const unsigned ev = (unsigned)((unsigned long long)__double_as_longlong(vd) >> 52) & 0x7ffu;
+        if (es >= 1023u + 52u || ev == 0x7ffu) {
             ok = false;
             s = 0.0;
         }
         double fl = floor(s);
         double f = s - fl;
-        long long il = (long long)fl % g.n[d];
-        if (il < 0) il += g.n[d];
+        long long il = (long long)fl;
+        if ((unsigned long long)il >= (unsigned long long)g.n[d]) {   // outside the box: wrap
+            il %= g.n[d];
+            if (il < 0) il += g.n[d];
+        }
         float ff = (float)f;
         if (ff >= 1.0f) {             // rounding to 1.0f moves to the next node
             ff = 0.0f;
@@ -71,26 +105,45 @@ __global__ void k_invperm(int64_t n, const Ctrl *ctrl, int32_t *inv) {
 }
 
 // synchronised readback: x_n = x_{n+1/2} - dt/2 v_n, in load order
-__global__ void k_unload(int64_t o0, int64_t m, const int32_t *__restrict__ inv, Geom g,
-                         double h0, double h1, double h2, double L0, double L1, double L2,
-                         double dt, const Ctrl *ctrl, double *__restrict__ x,
-                         double *__restrict__ v) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= m) return;
-    const ParticleSet ps = ctrl->sets[ctrl->cur];
-    int64_t p = inv[o0 + q];
-    int32_t c = ps.cell[p];
-    const int idx[3] = {cell_i(c), cell_j(c), cell_k(c)};
-    const double h[3] = {h0, h1, h2};
-    const double L[3] = {L0, L1, L2};
-    for (int d = 0; d < 3; ++d) {
-        double vd = (double)ps.v[d][p];
-        double xd = ((double)idx[d] + 0.5 + (double)ps.o[d][p]) * h[d] - 0.5 * dt * vd;
-        xd -= L[d] * floor(xd / L[d]);
-        if (xd >= L[d]) xd -= L[d];
-        if (xd < 0.0) xd = 0.0;
-        x[3 * q + d] = xd;
-        v[3 * q + d] = vd;
+__global__ void __launch_bounds__(kLoadThreads) k_unload(int64_t o0, int64_t m,
+                                                        const int32_t *__restrict__ inv, Geom g,
+                                                        double h0, double h1, double h2,
+                                                        double L0, double L1, double L2, double dt,
+                                                        const Ctrl *ctrl, double *__restrict__ x,
+                                                        double *__restrict__ v) {
+    // results are staged in shared memory and written as contiguous runs (the
+    // destination may be host memory written over the chip-to-chip link)
+    __shared__ double sx[3 * kLoadThreads], sv[3 * kLoadThreads];
+    const int64_t q0 = (int64_t)blockIdx.x * kLoadThreads;
+    const int cnt = (int)(m - q0 < kLoadThreads ? m - q0 : kLoadThreads);
+    if ((int)threadIdx.x < cnt) {
+        const ParticleSet ps = ctrl->sets[ctrl->cur];
+        const int64_t p = inv[o0 + q0 + threadIdx.x];
+        const int32_t c = ps.cell[p];
+        const int idx[3] = {cell_i(c), cell_j(c), cell_k(c)};
+        const double h[3] = {h0, h1, h2};
+        const double L[3] = {L0, L1, L2};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double vd = (double)ps.v[d][p];
+            double xd = ((double)idx[d] + 0.5 + (double)ps.o[d][p]) * h[d] - 0.5 * dt * vd;
+            if (xd < 0.0 || xd >= L[d]) {   // wrap (the FP64 division only when needed)
+                xd -= L[d] * floor(xd / L[d]);
+                if (xd >= L[d]) xd -= L[d];
+                if (xd < 0.0) xd = 0.0;
+            }
+            sx[3 * threadIdx.x + d] = xd;
+            sv[3 * threadIdx.x + d] = vd;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int j = r * kLoadThreads + threadIdx.x;
+        if (j < 3 * cnt) {
+            x[3 * q0 + j] = sx[j];
+            v[3 * q0 + j] = sv[j];
+        }
     }
 }
 
@@ -306,7 +359,7 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g,
 cudaError_t launch_load(const double *x, const double *v, int64_t m, int64_t base, const Geom &g,
                         const double *inv_h_d, double dt, Ctrl *ctrl, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
-    const int T = 256;
+    const int T = kLoadThreads;
     const int64_t B = (m + T - 1) / T;
     k_load<<<(unsigned)B, T, 0, st>>>(x, v, m, base, g, inv_h_d[0], inv_h_d[1], inv_h_d[2], dt,
                                       ctrl);
@@ -364,7 +417,7 @@ cudaError_t launch_unload(int64_t o0, int64_t m, const int32_t *inv, const Geom 
                           const double *h_d, const double *L_d, double dt, const Ctrl *ctrl,
                           double *x, double *v, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
-    const int T = 256;
+    const int T = kLoadThreads;
     k_unload<<<(unsigned)((m + T - 1) / T), T, 0, st>>>(o0, m, inv, g, h_d[0], h_d[1], h_d[2],
                                                         L_d[0], L_d[1], L_d[2], dt, ctrl, x, v);
     return cudaGetLastError();

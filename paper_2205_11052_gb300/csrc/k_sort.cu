@@ -556,20 +556,27 @@ cudaError_t sort_pass(int64_t n, const Geom &g, int shift, int64_t nb, Ctrl *ctr
 }
 
 // Shifts of the coarse passes that precede the full-key pass for particles in
-// arbitrary order: the first leaves at most 128 keys, each later one splits a
-// bucket of the previous pass into at most 64, so a 512-particle slice (which
-// spans one or two buckets of the pass before) meets at most 128 distinct keys
-// and never overflows the staged table.
+// arbitrary order.  Each pass sorts by the next kDigit bits of the tile key
+// (most significant first): a 512-particle slice of pass p spans one or two
+// buckets of pass p - 1, so it meets at most 2^(kDigit + 1) distinct keys
+// (never overflowing the staged table) and writes runs of ~512 / 2^kDigit
+// consecutive particles per key.
+#ifndef PIC_PRESORT_DIGIT
+#define PIC_PRESORT_DIGIT 4
+#endif
+constexpr int kDigit = PIC_PRESORT_DIGIT;
+static_assert(kDigit >= 1 && (2 << kDigit) <= kHash, "presort digit too wide for the table");
+
 int coarse_shifts(int ntiles, int *shifts) {
     int bits = 0;
     while ((1 << bits) < ntiles) ++bits;
     int k = 0;
-    for (int sft = bits - 7; sft > 0; sft -= 6) shifts[k++] = sft;
+    for (int sft = bits - kDigit; sft > 0; sft -= kDigit) shifts[k++] = sft;
     return k;
 }
 
 int sort_launches(int64_t n, int ntiles, bool presort) {
-    int sh[8];
+    int sh[32];
     const int passes = (presort && n > 0) ? coarse_shifts(ntiles, sh) : 0;
     // per coarse pass: histogram, 3 scan, scatter, flip; then the full-key pass
     // (histogram, 3 scan, scatter) and the work list (ranges, 3 scan, fill)
@@ -582,7 +589,7 @@ cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t
     cudaError_t e;
     if (presort && n > 0) {
         const int nt = g.ntile[0] * g.ntile[1] * g.ntile[2];
-        int sh[8];
+        int sh[32];
         const int passes = coarse_shifts(nt, sh);
         for (int p = 0; p < passes; ++p) {
             if ((e = sort_pass(n, g, sh[p], ((nt - 1) >> sh[p]) + 1, ctrl, bins, scan_tmp, st)))
