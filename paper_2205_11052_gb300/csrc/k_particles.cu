@@ -35,66 +35,74 @@ __global__ void __launch_bounds__(kLoadThreads) k_load(const double *__restrict_
     // shared memory: the source may be host memory read over the chip-to-chip
     // link, where strided 8-byte reads would fetch each line three times
     __shared__ double sx[3 * kLoadThreads], sv[3 * kLoadThreads];
-    const int64_t p0 = (int64_t)blockIdx.x * kLoadThreads;
-    const int cnt = (int)(m - p0 < kLoadThreads ? m - p0 : kLoadThreads);
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        const int j = r * kLoadThreads + threadIdx.x;
-        if (j < 3 * cnt) {
-            sx[j] = x[3 * p0 + j];
-            sv[j] = v[3 * p0 + j];
-        }
-    }
-    __syncthreads();
-    if ((int)threadIdx.x >= cnt) return;
-    const int64_t p = p0 + threadIdx.x;
     const ParticleSet ps = ctrl->sets[ctrl->cur];
     const double ih[3] = {ih0, ih1, ih2};
-    double xr[3], vr[3];
+    bool any_bad = false;
+    // blocks stride over runs of kLoadThreads particles
+    for (int64_t p0 = (int64_t)blockIdx.x * kLoadThreads; p0 < m;
+         p0 += (int64_t)gridDim.x * kLoadThreads) {
+        const int cnt = (int)(m - p0 < kLoadThreads ? m - p0 : kLoadThreads);
+        __syncthreads();   // the previous run's shared values are consumed
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        xr[d] = sx[3 * threadIdx.x + d];
-        vr[d] = sv[3 * threadIdx.x + d];
-    }
-    int idx[3];
-    float off[3];
-    bool ok = true;
+        for (int r = 0; r < 3; ++r) {
+            const int j = r * kLoadThreads + threadIdx.x;
+            if (j < 3 * cnt) {
+                sx[j] = x[3 * p0 + j];
+                sv[j] = v[3 * p0 + j];
+            }
+        }
+        __syncthreads();
+        if ((int)threadIdx.x >= cnt) continue;
+        const int64_t p = p0 + threadIdx.x;
+        double xr[3], vr[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        double vd = vr[d];
-        double xd = xr[d] + 0.5 * dt * vd;
-        double s = xd * ih[d] - 0.5;      // node g at (g + 1/2) h
-        // finite v and |s| < 2^52, tested on the exponent fields (FP64
-        // instructions are scarce on this GPU; integer ones are not)
-        const unsigned es = (unsigned)((unsigned long long)__double_as_longlong(s) >> 52) & 0x7ffu;
-        const unsigned ev = (unsigned)((unsigned long long)__double_as_longlong(vd) >> 52) & 0x7ffu;
-        if (es >= 1023u + 52u || ev == 0x7ffu) {
-            ok = false;
-            s = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            xr[d] = sx[3 * threadIdx.x + d];
+            vr[d] = sv[3 * threadIdx.x + d];
         }
-        double fl = floor(s);
-        double f = s - fl;
-        long long il = (long long)fl;
-        if ((unsigned long long)il >= (unsigned long long)g.n[d]) {   // outside the box: wrap
-            il %= g.n[d];
-            if (il < 0) il += g.n[d];
+        int idx[3];
+        float off[3];
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double vd = vr[d];
+            double xd = xr[d] + 0.5 * dt * vd;
+            double s = xd * ih[d] - 0.5;      // node g at (g + 1/2) h
+            // finite v and |s| < 2^52, tested on the exponent fields (FP64
+            // instructions are scarce on this GPU; integer ones are not)
+            const unsigned es =
+                (unsigned)((unsigned long long)__double_as_longlong(s) >> 52) & 0x7ffu;
+            const unsigned ev =
+                (unsigned)((unsigned long long)__double_as_longlong(vd) >> 52) & 0x7ffu;
+            if (es >= 1023u + 52u || ev == 0x7ffu) {
+                ok = false;
+                s = 0.0;
+            }
+            double fl = floor(s);
+            double f = s - fl;
+            long long il = (long long)fl;
+            if ((unsigned long long)il >= (unsigned long long)g.n[d]) {   // outside: wrap
+                il %= g.n[d];
+                if (il < 0) il += g.n[d];
+            }
+            float ff = (float)f;
+            if (ff >= 1.0f) {             // rounding to 1.0f moves to the next node
+                ff = 0.0f;
+                il += 1;
+                if (il == g.n[d]) il = 0;
+            }
+            idx[d] = (int)il;
+            off[d] = ff;
+            ps.v[d][base + p] = ok ? (float)vd : 0.0f;
         }
-        float ff = (float)f;
-        if (ff >= 1.0f) {             // rounding to 1.0f moves to the next node
-            ff = 0.0f;
-            il += 1;
-            if (il == g.n[d]) il = 0;
-        }
-        idx[d] = (int)il;
-        off[d] = ff;
-        ps.v[d][base + p] = ok ? (float)vd : 0.0f;
+        if (!ok) any_bad = true;
+        ps.cell[base + p] = pack_cell(idx[0], idx[1], idx[2]);
+        ps.o[0][base + p] = off[0];
+        ps.o[1][base + p] = off[1];
+        ps.o[2][base + p] = off[2];
+        ps.pid[base + p] = (int32_t)(base + p);
     }
-    if (!ok) raise_flag(ctrl, PIC_FLAG_NONFINITE);
-    ps.cell[base + p] = pack_cell(idx[0], idx[1], idx[2]);
-    ps.o[0][base + p] = off[0];
-    ps.o[1][base + p] = off[1];
-    ps.o[2][base + p] = off[2];
-    ps.pid[base + p] = (int32_t)(base + p);
+    if (any_bad) raise_flag(ctrl, PIC_FLAG_NONFINITE);
 }
 
 __global__ void k_invperm(int64_t n, const Ctrl *ctrl, int32_t *inv) {
@@ -357,10 +365,12 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g,
 }  // namespace
 
 cudaError_t launch_load(const double *x, const double *v, int64_t m, int64_t base, const Geom &g,
-                        const double *inv_h_d, double dt, Ctrl *ctrl, cudaStream_t st) {
+                        const double *inv_h_d, double dt, Ctrl *ctrl, cudaStream_t st,
+                        int max_blocks) {
     if (m <= 0) return cudaSuccess;
     const int T = kLoadThreads;
-    const int64_t B = (m + T - 1) / T;
+    int64_t B = (m + T - 1) / T;
+    if (max_blocks > 0) B = std::min<int64_t>(B, max_blocks);
     k_load<<<(unsigned)B, T, 0, st>>>(x, v, m, base, g, inv_h_d[0], inv_h_d[1], inv_h_d[2], dt,
                                       ctrl);
     return cudaGetLastError();

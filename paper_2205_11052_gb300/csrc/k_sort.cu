@@ -154,6 +154,17 @@ static_assert(kHash == 256, "the staged scatter scans its table with one thread 
 constexpr size_t kStageSmem = 2 * kBufBytes + (size_t)kStage * 4 + (size_t)kHash * 12 +
                               2 * sizeof(uint64_t) + (size_t)kStage * 2;
 
+// the arrays of a set from particle o on
+__device__ __forceinline__ ParticleSet offset_set(ParticleSet s, int64_t o) {
+    s.cell += o;
+    for (int d = 0; d < 3; ++d) {
+        s.o[d] += o;
+        s.v[d] += o;
+    }
+    s.pid += o;
+    return s;
+}
+
 __device__ __forceinline__ const void *src_array(const ParticleSet &s, int a) {
     if (a == 0) return s.cell;
     if (a < 4) return s.o[a - 1];
@@ -161,8 +172,15 @@ __device__ __forceinline__ const void *src_array(const ParticleSet &s, int a) {
     return s.pid;
 }
 
+// SortRange: particles [o, o + n) of set ctrl->cur ^ rel move to the same
+// range of the other set
+struct SortRange {
+    int64_t o;
+    int rel;
+};
+
 __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl *ctrl,
-                                                         int32_t *bins, int shift) {
+                                                         int32_t *bins, int shift, SortRange rg) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint32_t *buf0 = reinterpret_cast<uint32_t *>(smem);
     uint16_t *slid = reinterpret_cast<uint16_t *>(smem + 2 * kBufBytes);    // kStage table slots
@@ -175,9 +193,9 @@ __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl 
     __shared__ int overflow;
     __shared__ int wsum[8];
 
-    const int cur = ctrl->cur;
-    const ParticleSet src = ctrl->sets[cur];
-    const ParticleSet dst = ctrl->sets[1 - cur];
+    const int cur = ctrl->cur ^ rg.rel;
+    const ParticleSet src = offset_set(ctrl->sets[cur], rg.o);
+    const ParticleSet dst = offset_set(ctrl->sets[1 - cur], rg.o);
     const int64_t nslices = (n + kStage - 1) / kStage;
     int bad = 0;
     if (threadIdx.x == 0) {
@@ -341,10 +359,10 @@ __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Geom g, Ctrl 
 // distinct tiles in a shared hash table, one global atomic per tile and
 // slice (per-warp aggregated atomics when the table overflows).
 __global__ void __launch_bounds__(256) k_histogram_staged(int64_t n, Geom g, Ctrl *ctrl,
-                                                           int32_t *bins, int shift) {
+                                                           int32_t *bins, int shift, SortRange rg) {
     __shared__ int32_t hkey[kHash];
     __shared__ int32_t hcnt[kHash];
-    const ParticleSet ps = ctrl->sets[ctrl->cur];
+    const ParticleSet ps = offset_set(ctrl->sets[ctrl->cur ^ rg.rel], rg.o);
     const int64_t nslices = (n + kHistStage - 1) / kHistStage;
     int bad = 0;
     for (int64_t sl = blockIdx.x; sl < nslices; sl += gridDim.x) {
@@ -535,13 +553,13 @@ cudaError_t sort_prepare() {
 
 // histogram, scan and staged scatter by tile key >> shift (nb keys)
 cudaError_t sort_pass(int64_t n, const Geom &g, int shift, int64_t nb, Ctrl *ctrl, int32_t *bins,
-                      int32_t *scan_tmp, cudaStream_t st) {
+                      int32_t *scan_tmp, cudaStream_t st, SortRange rg = SortRange{0, 0}) {
     cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(nb + 1), st);
     if (e != cudaSuccess) return e;
     const int T = 256;
     if (n > 0) {
         const int hblocks = (int)std::min<int64_t>((n + kHistStage - 1) / kHistStage, 152 * 8);
-        k_histogram_staged<<<hblocks, T, 0, st>>>(n, g, ctrl, bins, shift);
+        k_histogram_staged<<<hblocks, T, 0, st>>>(n, g, ctrl, bins, shift, rg);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if ((e = exclusive_scan_impl(bins, nb, scan_tmp, st)) != cudaSuccess) return e;
@@ -549,7 +567,7 @@ cudaError_t sort_pass(int64_t n, const Geom &g, int shift, int64_t nb, Ctrl *ctr
         // resident blocks per SM as the staging buffer allows (228 KB per SM)
         const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (228 * 1024) / (kStageSmem + 1024)));
         const int sblocks = (int)std::min<int64_t>((n + kStage - 1) / kStage, 152 * per_sm);
-        k_scatter_staged<<<sblocks, T, kStageSmem, st>>>(n, g, ctrl, bins, shift);
+        k_scatter_staged<<<sblocks, T, kStageSmem, st>>>(n, g, ctrl, bins, shift, rg);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -607,6 +625,37 @@ cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t
     if ((e = exclusive_scan_impl(tile_items, ntiles, scan_tmp, st)) != cudaSuccess) return e;
     k_fill_items<<<tb, T, 0, st>>>(ntiles, chunk, tile_items, tile_range, items, ctrl,
                                    n > 0 ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// Coarse passes and the full-key pass over particles [o, o + n) alone, set
+// to set (starting in the current set, which no kernel here changes); the
+// range ends in set cur ^ (*passes & 1).  Used while later ranges are still
+// being loaded; o must be a multiple of 4 (bulk copies start on 16 bytes).
+cudaError_t launch_sort_range(int64_t n, int64_t o, const Geom &g, Ctrl *ctrl, int32_t *bins,
+                              int64_t nbins, int32_t *scan_tmp, int *passes, int *kernels,
+                              cudaStream_t st) {
+    *passes = 0;
+    *kernels = 0;
+    if (n <= 0) return cudaSuccess;
+    if (o % 4 != 0) return cudaErrorInvalidValue;
+    const int nt = g.ntile[0] * g.ntile[1] * g.ntile[2];
+    int sh[33];
+    const int k = coarse_shifts(nt, sh);
+    sh[k] = 0;
+    cudaError_t e;
+    for (int p = 0; p <= k; ++p) {
+        const int64_t nb = p < k ? ((nt - 1) >> sh[p]) + 1 : nbins;
+        if ((e = sort_pass(n, g, sh[p], nb, ctrl, bins, scan_tmp, st, SortRange{o, p & 1})))
+            return e;
+        *kernels += 5;
+    }
+    *passes = k + 1;
+    return cudaSuccess;
+}
+
+cudaError_t launch_flip(Ctrl *ctrl, cudaStream_t st) {
+    k_flip<<<1, 1, 0, st>>>(ctrl);
     return cudaGetLastError();
 }
 

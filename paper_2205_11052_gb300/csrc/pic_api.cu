@@ -63,6 +63,11 @@ int pic::record_error(int code, const char *fmt, ...) {
     return code;
 }
 
+// ranges a page-locked host load is split into (each binned on a side stream
+// while the next is read over the host link)
+constexpr int kLoadRanges = 8;
+constexpr int64_t kOverlapMin = 1 << 22;   // particles below which loads are not split
+
 struct pic_ctx {
     pic_grid_t grid;
     pic_species_t sp;
@@ -99,6 +104,10 @@ struct pic_ctx {
     int64_t ev_drained[PIC_PHASE_COUNT];   // pairs already summed
     double ms[PIC_PHASE_COUNT];
     int64_t launches;
+    // overlapped load: a second stream sorts loaded ranges while the next ones load
+    bool side_made;
+    cudaStream_t side;
+    cudaEvent_t side_ev[kLoadRanges + 1];
     // host mirror of the run
     int64_t np;
     int64_t step;
@@ -898,12 +907,57 @@ int pic_set_stream(pic_handle_t c, void *stream) {
 void pic_destroy(pic_handle_t c) {
     if (!c) return;
     destroy_plans(c);
+    if (c->side_made) {
+        for (cudaEvent_t e : c->side_ev) cudaEventDestroy(e);
+        cudaStreamDestroy(c->side);
+    }
     if (c->events_made)
         for (int p = 0; p < PIC_PHASE_COUNT; ++p)
             for (int s = 0; s < kTimerRing; ++s)
                 for (int e = 0; e < 2; ++e) cudaEventDestroy(c->ev[p][s][e]);
     delete c;
 }
+
+namespace {
+
+// coarse passes the first binning of particles in arbitrary order needs
+int presort_passes(const pic_ctx *c) {
+    return (sort_launches(1, (int)c->ntiles, true) - sort_launches(1, (int)c->ntiles, false)) / 6;
+}
+
+int load_overlapped(pic_ctx *c, const double *mx, const double *mv, int64_t n) {
+    if (!c->side_made) {
+        PIC_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : c->side_ev) PIC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->side_made = true;
+    }
+    // ranges of a multiple of 512 particles (bulk copies start on 16 bytes)
+    const int64_t per = ((n + kLoadRanges - 1) / kLoadRanges + 511) / 512 * 512;
+    int passes = 0;
+    for (int k = 0; k < kLoadRanges; ++k) {
+        const int64_t o = (int64_t)k * per;
+        if (o >= n) break;
+        const int64_t m = std::min(per, n - o);
+        PIC_CUDA(launch_load(mx + 3 * o, mv + 3 * o, m, o, c->geom, c->inv_h, c->prm.dt, c->ctrl(),
+                             c->st, kNumSMs));
+        c->launches += 1;
+        PIC_CUDA(cudaEventRecord(c->side_ev[k], c->st));
+        PIC_CUDA(cudaStreamWaitEvent(c->side, c->side_ev[k], 0));
+        int kernels = 0;
+        PIC_CUDA(launch_sort_range(m, o, c->geom, c->ctrl(), c->at<int32_t>(c->lay.bins), c->nbins,
+                                   c->at<int32_t>(c->lay.scan_tmp), &passes, &kernels, c->side));
+        c->launches += kernels;
+    }
+    PIC_CUDA(cudaEventRecord(c->side_ev[kLoadRanges], c->side));
+    PIC_CUDA(cudaStreamWaitEvent(c->st, c->side_ev[kLoadRanges], 0));
+    if (passes & 1) {   // the ranges now live in the other set
+        PIC_CUDA(launch_flip(c->ctrl(), c->st));
+        c->launches += 1;
+    }
+    return PIC_OK;
+}
+
+}  // namespace
 
 int pic_load_particles(pic_handle_t c, const double *x, const double *v, int64_t n,
                        int src_is_device) {
@@ -919,6 +973,19 @@ int pic_load_particles(pic_handle_t c, const double *x, const double *v, int64_t
     const double *mv = mx ? static_cast<const double *>(mapped_host(v, (size_t)n * 24)) : nullptr;
     if (src_is_device) {
         PIC_CUDA(launch_load(x, v, n, 0, c->geom, c->inv_h, c->prm.dt, c->ctrl(), c->st));
+    } else if (mx && mv && n >= kOverlapMin && presort_passes(c) > 0) {
+        // page-locked host arrays, read in place by the load kernel one range
+        // at a time on one block per SM (the host link, not the SMs, bounds
+        // it); each loaded range is binned on the side stream meanwhile, so
+        // the final full-key pass sees tile-ordered runs
+        if ((r = load_overlapped(c, mx, mv, n))) return r;
+        c->np = n;
+        c->step = 0;
+        c->loaded = true;
+        c->rho_current = false;
+        if ((r = do_sort(c))) return r;
+        PIC_CUDA(cudaStreamSynchronize(c->st));
+        return PIC_OK;
     } else if (mx && mv) {
         // page-locked host arrays: read in place by the load kernel
         PIC_CUDA(launch_load(mx, mv, n, 0, c->geom, c->inv_h, c->prm.dt, c->ctrl(), c->st));

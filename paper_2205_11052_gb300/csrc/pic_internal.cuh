@@ -88,7 +88,8 @@ struct PushConst {
 
 // Diagnostic partial layout: 4 doubles per block.
 constexpr int kDiagFieldBlocks = 512;
-constexpr int kMaxPushBlocks = 152 * 8;
+constexpr int kNumSMs = 152;   // streaming multiprocessors of the GPU (two dies of 76)
+constexpr int kMaxPushBlocks = kNumSMs * 8;
 constexpr int kMaxSmemPerBlock = 227 * 1024;   // opt-in shared memory per block
 // resident blocks per SM the fused push + deposit kernel is compiled for
 #ifndef PIC_PD_MIN_BLOCKS
@@ -110,9 +111,10 @@ int record_error(int code, const char *fmt, ...);
 // ----------------------------------------------------------------------------
 // kernel launchers (defined in the k_*.cu files); all enqueue on `st`.
 // ----------------------------------------------------------------------------
+// max_blocks > 0 caps the grid (blocks then stride over the particles)
 cudaError_t launch_load(const double *x, const double *v, int64_t m, int64_t base,
                         const Geom &g, const double *inv_h_d, double dt, Ctrl *ctrl,
-                        cudaStream_t st);
+                        cudaStream_t st, int max_blocks = 0);
 cudaError_t launch_invperm(int64_t n, Ctrl *ctrl, int32_t *inv, cudaStream_t st);
 cudaError_t launch_unload(int64_t o0, int64_t m, const int32_t *inv, const Geom &g,
                           const double *h_d, const double *L_d, double dt, const Ctrl *ctrl,
@@ -130,6 +132,12 @@ cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t
                         int2 *tile_range, int4 *items, bool presort, cudaStream_t st);
 // kernels launch_sort issues
 int sort_launches(int64_t n, int ntiles, bool presort);
+// coarse passes + full-key pass over particles [o, o + n) of the current set
+// (which stays unchanged); the range ends in set cur ^ (*passes & 1)
+cudaError_t launch_sort_range(int64_t n, int64_t o, const Geom &g, Ctrl *ctrl, int32_t *bins,
+                              int64_t nbins, int32_t *scan_tmp, int *passes, int *kernels,
+                              cudaStream_t st);
+cudaError_t launch_flip(Ctrl *ctrl, cudaStream_t st);   // ctrl->cur = 1 - ctrl->cur
 
 cudaError_t launch_deposit(int64_t n, const Geom &g, const Ctrl *ctrl, const int4 *items,
                            int max_items, double qscale, float *rho, unsigned long long *rho64,
