@@ -29,9 +29,10 @@ cudaError_t launch_b_unload(int64_t o0, int64_t m, const int32_t *inv, const Ins
 cudaError_t launch_b_sort(int64_t n, const InstDesc *desc, const long long *p0, int n_inst,
                           int ntiles, int chunk, Ctrl *ctrl, int32_t *bins, int32_t *scan_tmp,
                           int32_t *tile_items, int2 *tile_range, int4 *items, cudaStream_t st);
+cudaError_t batch_sort_prepare();   // kernel attributes; once per device outside capture
 cudaError_t launch_b_push_deposit(bool push, bool diag, bool ext, bool mag, bool fixed,
                                   const InstDesc *desc, const int32_t *tile_inst, Ctrl *ctrl,
-                                  const int4 *items, int blocks, size_t smem, const float4 *E4,
+                                  const int4 *items, int blocks, size_t smem, const float4 *E8,
                                   float *rho, unsigned long long *rho64, int sparse_below,
                                   double *part, cudaStream_t st);
 cudaError_t launch_b_rho_finish(int64_t ng, const InstDesc *desc, const long long *g0, int n_inst,
@@ -44,7 +45,9 @@ cudaError_t launch_b_diag_finalize(const InstDesc *desc, int n_inst, const int32
                                    const double *fpart, const double *ppart, const double *modes,
                                    Ctrl *ctrl, double dt, pic_diag_t *ring, int ring_cap,
                                    cudaStream_t st);
-cudaError_t launch_b_pack(int64_t mng, const float *planar, float4 *E4, cudaStream_t st);
+// planar E of a size class (grids of nx points per row) -> E4 and x-paired E8
+cudaError_t launch_b_pack(int64_t mng, int nx, const float *planar, float4 *E4, float4 *E8,
+                          cudaStream_t st);
 cudaError_t launch_b_step_done(Ctrl *ctrl, bool diag, cudaStream_t st);
 
 }  // namespace pic

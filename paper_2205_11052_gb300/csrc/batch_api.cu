@@ -60,7 +60,7 @@ struct pic_batch {
     size_t smem, fft_reserve;
     int64_t staging;
     // arena layout
-    size_t o_ctrl, o_desc, o_p0, o_g0, o_tinst, o_sets, set_stride, o_rho, o_rho64, o_E4, o_rhoh,
+    size_t o_ctrl, o_desc, o_p0, o_g0, o_tinst, o_sets, set_stride, o_rho, o_rho64, o_E4, o_E8, o_rhoh,
         o_Eh, o_Epl, o_bins, o_scan, o_titems, o_trange, o_items, o_fpart, o_ppart, o_modes, o_ring, o_inv,
         o_sx, o_sv, o_fft, total;
     char *arena;
@@ -146,6 +146,7 @@ void batch_layout(pic_batch *b) {
     b->o_rho = take((size_t)b->ng * 4);
     b->o_rho64 = take((size_t)b->ng * 8);
     b->o_E4 = take((size_t)b->ng * 16);
+    b->o_E8 = take((size_t)b->ng * 32);
     b->o_rhoh = take((size_t)b->nhalf_tot * 8);
     b->o_Eh = take((size_t)b->nhalf_tot * 8 * 3);
     b->o_Epl = take((size_t)b->ng * 4 * 3);
@@ -188,7 +189,7 @@ int b_deposit_pass(pic_batch *b, bool push, bool diag) {
     if (!b_fixed(b)) B_CUDA(cudaMemsetAsync(b->at<float>(b->o_rho), 0, (size_t)b->ng * 4, b->st));
     B_CUDA(launch_b_push_deposit(push, diag, b_ext(b), b_mag(b), b_fixed(b), b->at<InstDesc>(b->o_desc),
                                  b->at<int32_t>(b->o_tinst), b->ctrl(), b->at<int4>(b->o_items),
-                                 b->fused_blocks, b->smem, b->at<float4>(b->o_E4),
+                                 b->fused_blocks, b->smem, b->at<float4>(b->o_E8),
                                  b->at<float>(b->o_rho), b->at<unsigned long long>(b->o_rho64),
                                  b->sparse_below, b->at<double>(b->o_ppart), b->st));
     if (b_fixed(b))
@@ -219,7 +220,8 @@ int b_solve(pic_batch *b) {
         // 3m inverse transforms into planar (Ex, Ey, Ez) of the class, then interleave
         float *pl = b->at<float>(b->o_Epl) + 3 * c.g0;
         B_CUFFT(cufftExecC2R(c.c2r, reinterpret_cast<cufftComplex *>(Eh + 3 * c.h0), pl));
-        B_CUDA(launch_b_pack((int64_t)c.m * c.ng, pl, reinterpret_cast<float4 *>(E) + c.g0, b->st));
+        B_CUDA(launch_b_pack((int64_t)c.m * c.ng, c.n[0], pl, reinterpret_cast<float4 *>(E) + c.g0,
+                             b->at<float4>(b->o_E8) + 2 * c.g0, b->st));
     }
     return PIC_OK;
 }
@@ -420,6 +422,7 @@ int pic_batch_bind_workspace(pic_batch_t b, void *arena, size_t bytes, void *str
             B_CUFFT(cufftSetWorkArea(p, b->arena + b->o_fft));
             B_CUFFT(cufftSetStream(p, b->st));
         }
+    B_CUDA(batch_sort_prepare());
     Ctrl h;
     memset(&h, 0, sizeof(h));
     for (int s = 0; s < 2; ++s) {
@@ -441,6 +444,7 @@ int pic_batch_bind_workspace(pic_batch_t b, void *arena, size_t bytes, void *str
     B_CUDA(cudaMemcpyAsync(b->at<int32_t>(b->o_tinst), b->tile_inst.data(), sizeof(int32_t) * b->ntiles,
                            cudaMemcpyHostToDevice, b->st));
     B_CUDA(cudaMemsetAsync(b->at<char>(b->o_E4), 0, (size_t)b->ng * 16, b->st));
+    B_CUDA(cudaMemsetAsync(b->at<char>(b->o_E8), 0, (size_t)b->ng * 32, b->st));
     B_CUDA(cudaMemsetAsync(b->at<char>(b->o_rho), 0, (size_t)b->ng * 4, b->st));
     B_CUDA(cudaMemsetAsync(b->at<char>(b->o_rho64), 0, (size_t)b->ng * 8, b->st));
     B_CUDA(cudaMemsetAsync(b->at<char>(b->o_modes), 0, (size_t)b->n_inst * 16, b->st));

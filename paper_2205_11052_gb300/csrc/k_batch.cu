@@ -18,6 +18,7 @@
 #include "batch.cuh"
 #include "cic.cuh"
 #include "push.cuh"
+#include "sort_staged.cuh"
 
 namespace pic {
 
@@ -112,72 +113,25 @@ __device__ __forceinline__ void b_slice(int64_t n, int64_t &b0, int64_t &b1) {
     b1 = b0 + per < n ? b0 + per : n;
 }
 
-__global__ void __launch_bounds__(256) k_b_histogram(int64_t n, const InstDesc *__restrict__ desc,
-                                                      const long long *__restrict__ p0, int n_inst,
-                                                      Ctrl *ctrl, int32_t *bins) {
-    const ParticleSet ps = ctrl->sets[ctrl->cur];
-    int64_t b0, b1;
-    b_slice(n, b0, b1);
-    int bad = 0;
-    const int lane = threadIdx.x & 31;
-    for (int64_t base = b0; base < b1; base += blockDim.x) {
-        const int64_t p = base + threadIdx.x;
-        const bool act = p < b1;
-        const unsigned active = __ballot_sync(0xffffffffu, act);
-        if (act) {
-            const int key = b_key(ps.cell[p], desc[inst_of_particle(p0, n_inst, p)], bad);
-            const unsigned peers = __match_any_sync(active, key);
-            if (lane == __ffs(peers) - 1) atomicAdd(bins + key, (int)__popc(peers));
+// binning key of particle p: the global tile id of its instance's tile.  A
+// thread's copy remembers the particle range of the last instance it looked
+// up (a thread meets consecutive particles of one instance), so the binary
+// search runs only when p leaves it.
+struct BatchKey {
+    const InstDesc *desc;
+    const long long *p0;
+    int n_inst;
+    mutable long long lo = 0, hi = 0;
+    mutable int inst = 0;
+    __device__ __forceinline__ int operator()(int32_t c, int64_t p, int &bad) const {
+        if (p < lo || p >= hi) {
+            inst = inst_of_particle(p0, n_inst, p);
+            lo = p0[inst];
+            hi = p0[inst + 1];
         }
+        return b_key(c, desc[inst], bad);
     }
-    if (bad) atomicOr(&ctrl->flags, PIC_FLAG_BAD_CELL);
-}
-
-__global__ void __launch_bounds__(256) k_b_scatter(int64_t n, const InstDesc *__restrict__ desc,
-                                                    const long long *__restrict__ p0, int n_inst,
-                                                    Ctrl *ctrl, int32_t *bins) {
-    const int cur = ctrl->cur;
-    const ParticleSet src = ctrl->sets[cur];
-    const ParticleSet dst = ctrl->sets[1 - cur];
-    int64_t b0, b1;
-    b_slice(n, b0, b1);
-    const int lane = threadIdx.x & 31;
-    for (int64_t base = b0; base < b1; base += blockDim.x) {
-        const int64_t p = base + threadIdx.x;
-        const bool act = p < b1;
-        int32_t c = 0, id = 0;
-        float o0 = 0.f, o1 = 0.f, o2 = 0.f, v0 = 0.f, v1 = 0.f, v2 = 0.f;
-        int key = 0;
-        if (act) {
-            c = src.cell[p];
-            int bad = 0;
-            key = b_key(c, desc[inst_of_particle(p0, n_inst, p)], bad);
-            o0 = src.o[0][p];
-            o1 = src.o[1][p];
-            o2 = src.o[2][p];
-            v0 = src.v[0][p];
-            v1 = src.v[1][p];
-            v2 = src.v[2][p];
-            id = src.pid[p];
-        }
-        const unsigned active = __ballot_sync(0xffffffffu, act);
-        if (act) {
-            const unsigned peers = __match_any_sync(active, key);
-            const int leader = __ffs(peers) - 1;
-            int old = 0;
-            if (lane == leader) old = atomicAdd(bins + key, __popc(peers));
-            const int q = __shfl_sync(peers, old, leader) + __popc(peers & ((1u << lane) - 1u));
-            dst.cell[q] = c;
-            dst.o[0][q] = o0;
-            dst.o[1][q] = o1;
-            dst.o[2][q] = o2;
-            dst.v[0][q] = v0;
-            dst.v[1][q] = v1;
-            dst.v[2][q] = v2;
-            dst.pid[q] = id;
-        }
-    }
-}
+};
 
 // One work item per block iteration: the deposit of the instance's tile, and
 // (PUSH) the gather + push before it.  With DIAG each item leaves its FP32
@@ -185,7 +139,7 @@ __global__ void __launch_bounds__(256) k_b_scatter(int64_t n, const InstDesc *__
 template <bool PUSH, bool DIAG, bool EXT, bool MAG, bool FIXED>
 __global__ void __launch_bounds__(256, 3) k_b_push_deposit(
     const InstDesc *__restrict__ desc, const int32_t *__restrict__ tile_inst, Ctrl *ctrl,
-    const int4 *__restrict__ items, const float4 *__restrict__ E4, float *rho,
+    const int4 *__restrict__ items, const float4 *__restrict__ E8, float *rho,
     unsigned long long *rho64, int sparse_below, double *__restrict__ part) {
     extern __shared__ uint32_t acc[];
     __shared__ double red[4][8];
@@ -197,7 +151,7 @@ __global__ void __launch_bounds__(256, 3) k_b_push_deposit(
         const InstDesc &D = desc[tile_inst[item.x]];
         const Geom g = D.g;
         const PushConst pc = D.pc;
-        const float4 *Ei = E4 + D.g0;
+        const float4 *Ei = E8 + 2 * D.g0;
         float *rhoi = rho + D.g0;
         unsigned long long *rho64i = rho64 + D.g0;
         const float qscale = D.qscale;
@@ -213,7 +167,7 @@ __global__ void __launch_bounds__(256, 3) k_b_push_deposit(
             float fx = ps.o[0][p], fy = ps.o[1][p], fz = ps.o[2][p];
             if (PUSH) {
                 float vx = ps.v[0][p], vy = ps.v[1][p], vz = ps.v[2][p];
-                push_one<EXT, MAG>(g, pc, Ei, c, fx, fy, fz, vx, vy, vz, bad);
+                push_one_pairs<EXT, MAG>(g, pc, Ei, c, fx, fy, fz, vx, vy, vz, bad);
                 ps.cell[p] = c;
                 ps.o[0][p] = fx;
                 ps.o[1][p] = fy;
@@ -383,10 +337,20 @@ __global__ void k_b_diag_finalize(const InstDesc *__restrict__ desc, int n_inst,
 }
 
 // planar (Ex, Ey, Ez) of a size class -> interleaved float4 E of its instances
-__global__ void k_b_pack(int64_t mng, const float *__restrict__ planar, float4 *__restrict__ E4) {
+// planar (Ex, Ey, Ez) of a size class -> E4 and the x-paired E8 (E at q and at
+// its +x neighbour; instances and rows start at multiples of nx, so the row
+// position of q is q mod nx)
+__global__ void k_b_pack(int64_t mng, int nx, const float *__restrict__ planar,
+                         float4 *__restrict__ E4, float4 *__restrict__ E8) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < mng; q += stride)
-        E4[q] = make_float4(planar[q], planar[q + mng], planar[q + 2 * mng], 0.0f);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < mng; q += stride) {
+        const int i = (int)(q % nx);
+        const int64_t q1 = (i + 1 == nx) ? q - i : q + 1;
+        const float4 e = make_float4(planar[q], planar[q + mng], planar[q + 2 * mng], 0.0f);
+        E4[q] = e;
+        E8[2 * q] = e;
+        E8[2 * q + 1] = make_float4(planar[q1], planar[q1 + mng], planar[q1 + 2 * mng], 0.0f);
+    }
 }
 
 __global__ void k_b_step_done(Ctrl *ctrl, int diag) {
@@ -416,25 +380,17 @@ cudaError_t launch_b_unload(int64_t o0, int64_t m, const int32_t *inv, const Ins
 cudaError_t launch_b_sort(int64_t n, const InstDesc *desc, const long long *p0, int n_inst,
                           int ntiles, int chunk, Ctrl *ctrl, int32_t *bins, int32_t *scan_tmp,
                           int32_t *tile_items, int2 *tile_range, int4 *items, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(int32_t) * ((size_t)ntiles + 1), st);
+    cudaError_t e = staged_pass(n, BatchKey{desc, p0, n_inst}, ntiles, ctrl, bins, scan_tmp, st);
     if (e != cudaSuccess) return e;
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
-    if (n > 0) {
-        k_b_histogram<<<blocks, 256, 0, st>>>(n, desc, p0, n_inst, ctrl, bins);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if ((e = exclusive_scan(bins, ntiles, scan_tmp, st)) != cudaSuccess) return e;
-    if (n > 0) {
-        k_b_scatter<<<blocks, 256, 0, st>>>(n, desc, p0, n_inst, ctrl, bins);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
     return launch_worklist(bins, ntiles, chunk, tile_items, tile_range, items, scan_tmp, ctrl,
                            n > 0 ? 1 : 0, st);
 }
 
+cudaError_t batch_sort_prepare() { return staged_prepare<BatchKey>(); }
+
 cudaError_t launch_b_push_deposit(bool push, bool diag, bool ext, bool mag, bool fixed,
                                   const InstDesc *desc, const int32_t *tile_inst, Ctrl *ctrl,
-                                  const int4 *items, int blocks, size_t smem, const float4 *E4,
+                                  const int4 *items, int blocks, size_t smem, const float4 *E8,
                                   float *rho, unsigned long long *rho64, int sparse_below,
                                   double *part, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
@@ -445,7 +401,7 @@ cudaError_t launch_b_push_deposit(bool push, bool diag, bool ext, bool mag, bool
             (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                                       (int)smem)) != cudaSuccess)                               \
             return e;                                                                           \
-        kern<<<blocks, 256, smem, st>>>(desc, tile_inst, ctrl, items, E4, rho, rho64,          \
+        kern<<<blocks, 256, smem, st>>>(desc, tile_inst, ctrl, items, E8, rho, rho64,          \
                                         sparse_below, part);                                    \
     } while (0)
 #define PIC_BPD_F(P, D, X, M) \
@@ -495,9 +451,10 @@ cudaError_t launch_b_diag_finalize(const InstDesc *desc, int n_inst, const int32
     return cudaGetLastError();
 }
 
-cudaError_t launch_b_pack(int64_t mng, const float *planar, float4 *E4, cudaStream_t st) {
+cudaError_t launch_b_pack(int64_t mng, int nx, const float *planar, float4 *E4, float4 *E8,
+                          cudaStream_t st) {
     const int b = (int)std::max<int64_t>(1, std::min<int64_t>((mng + 255) / 256, 152 * 8));
-    k_b_pack<<<b, 256, 0, st>>>(mng, planar, E4);
+    k_b_pack<<<b, 256, 0, st>>>(mng, nx, planar, E4, E8);
     return cudaGetLastError();
 }
 
