@@ -6,6 +6,11 @@
 
 namespace pic {
 
+// resident blocks per SM the batched push + deposit kernel is compiled for
+#ifndef PIC_BATCH_PD_MIN_BLOCKS
+#define PIC_BATCH_PD_MIN_BLOCKS 4
+#endif
+
 // One instance of an ensemble (device copy in the batch arena).
 struct InstDesc {
     Geom g;                    // grid, tiles, guard (FP32 spacing)
@@ -30,9 +35,11 @@ cudaError_t launch_b_sort(int64_t n, const InstDesc *desc, const long long *p0, 
                           int ntiles, int chunk, Ctrl *ctrl, int32_t *bins, int32_t *scan_tmp,
                           int32_t *tile_items, int2 *tile_range, int4 *items, cudaStream_t st);
 cudaError_t batch_sort_prepare();   // kernel attributes; once per device outside capture
+// shared memory of the batched push + deposit: u32 tile slots + 64-bit per-tile sums
+size_t batch_push_smem(int max_S);
 cudaError_t launch_b_push_deposit(bool push, bool diag, bool ext, bool mag, bool fixed,
                                   const InstDesc *desc, const int32_t *tile_inst, Ctrl *ctrl,
-                                  const int4 *items, int blocks, size_t smem, const float4 *E8,
+                                  const int4 *items, int blocks, int max_S, const float4 *E8,
                                   float *rho, unsigned long long *rho64, int sparse_below,
                                   double *part, cudaStream_t st);
 cudaError_t launch_b_rho_finish(int64_t ng, const InstDesc *desc, const long long *g0, int n_inst,

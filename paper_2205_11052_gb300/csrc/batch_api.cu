@@ -57,7 +57,8 @@ struct pic_batch {
     std::vector<SizeClass> cls;
     int64_t np, ng, nhalf_tot;
     int ntiles, max_items, chunk, sparse_below, fused_blocks;
-    size_t smem, fft_reserve;
+    int max_S;                 // largest tile (plus guard) of any instance, in nodes
+    size_t fft_reserve;
     int64_t staging;
     // arena layout
     size_t o_ctrl, o_desc, o_p0, o_g0, o_tinst, o_sets, set_stride, o_rho, o_rho64, o_E4, o_E8, o_rhoh,
@@ -189,7 +190,7 @@ int b_deposit_pass(pic_batch *b, bool push, bool diag) {
     if (!b_fixed(b)) B_CUDA(cudaMemsetAsync(b->at<float>(b->o_rho), 0, (size_t)b->ng * 4, b->st));
     B_CUDA(launch_b_push_deposit(push, diag, b_ext(b), b_mag(b), b_fixed(b), b->at<InstDesc>(b->o_desc),
                                  b->at<int32_t>(b->o_tinst), b->ctrl(), b->at<int4>(b->o_items),
-                                 b->fused_blocks, b->smem, b->at<float4>(b->o_E8),
+                                 b->fused_blocks, b->max_S, b->at<float4>(b->o_E8),
                                  b->at<float>(b->o_rho), b->at<unsigned long long>(b->o_rho64),
                                  b->sparse_below, b->at<double>(b->o_ppart), b->st));
     if (b_fixed(b))
@@ -379,8 +380,13 @@ int pic_batch_create(const pic_instance_t *inst, int n_inst, double q_over_m,
     b->nhalf_tot = h0;
     b->ntiles = tile0;
     b->max_items = (int)std::min<int64_t>(max_items, 2147483647LL);
-    b->smem = sizeof(uint32_t) * (size_t)max_S;
-    b->fused_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(b->max_items, 152 * 3 * 2));
+    b->max_S = max_S;
+    if (batch_push_smem(max_S) > (size_t)kMaxSmemPerBlock) {
+        delete b;
+        return record_error(PIC_ERR_ARG, "deposit tile plus guard too large for shared memory");
+    }
+    b->fused_blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>(b->max_items, (int64_t)kNumSMs * PIC_BATCH_PD_MIN_BLOCKS * 2));
     b->staging = std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)1 << 22));
     size_t ws = 0;
     size_t bound = (size_t)b->nhalf_tot * 8 * 3 + ((size_t)4 << 20);

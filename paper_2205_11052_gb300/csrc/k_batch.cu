@@ -133,20 +133,36 @@ struct BatchKey {
     }
 };
 
-// One work item per block iteration: the deposit of the instance's tile, and
-// (PUSH) the gather + push before it.  With DIAG each item leaves its FP32
-// particle moments, summed in FP64 in a fixed order, in part[item].
+// Work items (instance tile, particle range) in contiguous runs per block:
+// the deposit of the instance's tile and (PUSH) the gather + push before it.
+// Each item's tile accumulates in shared memory (u32 fixed point, or FP32
+// bits) and is folded into a 64-bit per-tile sum after the item; the sum is
+// flushed to the instance's grid when the block moves to another tile, so
+// consecutive items of one tile cost one flush.  With DIAG each item leaves
+// its FP32 particle moments, summed in FP64 in a fixed order, in part[item].
 template <bool PUSH, bool DIAG, bool EXT, bool MAG, bool FIXED>
-__global__ void __launch_bounds__(256, 3) k_b_push_deposit(
+__global__ void __launch_bounds__(256, PIC_BATCH_PD_MIN_BLOCKS) k_b_push_deposit(
     const InstDesc *__restrict__ desc, const int32_t *__restrict__ tile_inst, Ctrl *ctrl,
     const int4 *__restrict__ items, const float4 *__restrict__ E8, float *rho,
-    unsigned long long *rho64, int sparse_below, double *__restrict__ part) {
-    extern __shared__ uint32_t acc[];
+    unsigned long long *rho64, int sparse_below, int max_S, double *__restrict__ part) {
+    extern __shared__ __align__(16) uint32_t acc[];
     __shared__ double red[4][8];
+    void *sum = reinterpret_cast<char *>(acc) + cic::sum_offset(max_S);
     const ParticleSet ps = ctrl->sets[ctrl->cur];
     const int n_items = ctrl->n_items;
+    const int per = (n_items + gridDim.x - 1) / gridDim.x;
+    const int it0 = min(n_items, (int)blockIdx.x * per), it1 = min(n_items, it0 + per);
+    for (int s = threadIdx.x; s < max_S; s += blockDim.x) {
+        acc[s] = 0u;
+        if (FIXED) reinterpret_cast<unsigned long long *>(sum)[s] = 0ull;
+        else reinterpret_cast<float *>(sum)[s] = 0.0f;
+    }
+    __syncthreads();
     int bad = 0;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    int cur_tile = -1;
+    const InstDesc *Dc = desc;
+    cic::Tile tc{};
+    for (int it = it0; it < it1; ++it) {
         const int4 item = items[it];
         const InstDesc &D = desc[tile_inst[item.x]];
         const Geom g = D.g;
@@ -157,9 +173,12 @@ __global__ void __launch_bounds__(256, 3) k_b_push_deposit(
         const float qscale = D.qscale;
         const bool sparse = item.z - item.y < sparse_below;
         const cic::Tile t = cic::tile_of(g, item.x - D.tile0);
-        if (!sparse) {
-            for (int s = threadIdx.x; s < t.S; s += blockDim.x) acc[s] = 0u;
-            __syncthreads();
+        if (!sparse && item.x != cur_tile) {
+            if (cur_tile >= 0)
+                cic::tile_flush_sum<FIXED>(sum, tc, Dc->g, rho + Dc->g0, rho64 + Dc->g0, Dc->qscale);
+            cur_tile = item.x;
+            tc = t;
+            Dc = &D;
         }
         float a[4] = {0.f, 0.f, 0.f, 0.f};
         for (int p = item.y + threadIdx.x; p < item.z; p += blockDim.x) {
@@ -194,7 +213,7 @@ __global__ void __launch_bounds__(256, 3) k_b_push_deposit(
         }
         if (!sparse) {
             __syncthreads();
-            cic::tile_flush<FIXED>(acc, t, g, rhoi, rho64i, qscale);
+            cic::tile_fold<FIXED>(acc, sum, t.S);
             __syncthreads();
         }
         if (DIAG) {
@@ -213,6 +232,8 @@ __global__ void __launch_bounds__(256, 3) k_b_push_deposit(
             __syncthreads();
         }
     }
+    if (cur_tile >= 0)
+        cic::tile_flush_sum<FIXED>(sum, tc, Dc->g, rho + Dc->g0, rho64 + Dc->g0, Dc->qscale);
     if (bad) atomicOr(&ctrl->flags, bad);
 }
 
@@ -388,11 +409,14 @@ cudaError_t launch_b_sort(int64_t n, const InstDesc *desc, const long long *p0, 
 
 cudaError_t batch_sort_prepare() { return staged_prepare<BatchKey>(); }
 
+size_t batch_push_smem(int max_S) { return cic::sum_offset(max_S) + 8 * (size_t)max_S; }
+
 cudaError_t launch_b_push_deposit(bool push, bool diag, bool ext, bool mag, bool fixed,
                                   const InstDesc *desc, const int32_t *tile_inst, Ctrl *ctrl,
-                                  const int4 *items, int blocks, size_t smem, const float4 *E8,
+                                  const int4 *items, int blocks, int max_S, const float4 *E8,
                                   float *rho, unsigned long long *rho64, int sparse_below,
                                   double *part, cudaStream_t st) {
+    const size_t smem = batch_push_smem(max_S);
     cudaError_t e = cudaSuccess;
 #define PIC_BPD(P, D, X, M, F)                                                                  \
     do {                                                                                        \
@@ -402,7 +426,7 @@ cudaError_t launch_b_push_deposit(bool push, bool diag, bool ext, bool mag, bool
                                       (int)smem)) != cudaSuccess)                               \
             return e;                                                                           \
         kern<<<blocks, 256, smem, st>>>(desc, tile_inst, ctrl, items, E8, rho, rho64,          \
-                                        sparse_below, part);                                    \
+                                        sparse_below, max_S, part);                             \
     } while (0)
 #define PIC_BPD_F(P, D, X, M) \
     do { if (fixed) PIC_BPD(P, D, X, M, true); else PIC_BPD(P, D, X, M, false); } while (0)
