@@ -46,13 +46,16 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--grid", type=int, default=128)
     ap.add_argument("--ppc", type=int, default=64)
-    ap.add_argument("--sort-period", type=int, default=LAUNCH["sort_period"])
+    ap.add_argument("--sort-period", type=int, default=None,
+                    help="steps between re-binnings (default 4; 2 for the Penning bunch, whose "
+                         "particles cross cells faster on its 256^3 mesh)")
     ap.add_argument("--options", type=int, default=LAUNCH["options"])
     ap.add_argument("--diag-every", type=int, default=1)
     ap.add_argument("--dt", type=float, default=0.05,
                     help="time step (0.05: the Landau benchmark; the paper's scaling runs use "
                          "0.5 h_min, i.e. 0.005 for its finest mesh)")
-    ap.add_argument("--guard", type=int, default=0, help="deposit tile guard layers (0: default 2)")
+    ap.add_argument("--guard", type=int, default=None,
+                    help="deposit tile guard layers (default 2; 3 for the Penning bunch)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=1 << 21,
                     help="particles in the oracle's bounded sample")
@@ -72,7 +75,13 @@ def parse():
                     help="write profiles/traffic.json from an ncu --csv capture of "
                          "k_push_deposit on the 64^3 x 64 case (dram__bytes_read/write.sum), "
                          "then exit")
-    return ap.parse_args()
+    args = ap.parse_args()
+    penning = args.workload == "penning"
+    if args.sort_period is None:
+        args.sort_period = 2 if penning else LAUNCH["sort_period"]
+    if args.guard is None:
+        args.guard = 3 if penning else 0
+    return args
 
 
 def workload_name(args):

@@ -150,8 +150,8 @@ __global__ void __launch_bounds__(256, PIC_BATCH_PD_MIN_BLOCKS) k_b_push_deposit
     void *sum = reinterpret_cast<char *>(acc) + cic::sum_offset(max_S);
     const ParticleSet ps = ctrl->sets[ctrl->cur];
     const int n_items = ctrl->n_items;
-    const int per = (n_items + gridDim.x - 1) / gridDim.x;
-    const int it0 = min(n_items, (int)blockIdx.x * per), it1 = min(n_items, it0 + per);
+    int it0, it1;
+    item_run(items, n_items, it0, it1);
     for (int s = threadIdx.x; s < max_S; s += blockDim.x) {
         acc[s] = 0u;
         if (FIXED) reinterpret_cast<unsigned long long *>(sum)[s] = 0ull;

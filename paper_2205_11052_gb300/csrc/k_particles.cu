@@ -292,8 +292,8 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g,
     int bad = 0;
     unsigned long long strays = 0;
     // a contiguous run of work items per block (consecutive items share tiles)
-    const int per = (n_items + gridDim.x - 1) / gridDim.x;
-    const int it0 = min(n_items, (int)blockIdx.x * per), it1 = min(n_items, it0 + per);
+    int it0, it1;
+    item_run(items, n_items, it0, it1);
     const int S = cic::tile_of(g, 0).S;
     void *sum = reinterpret_cast<char *>(acc) + cic::sum_offset(S);
     for (int s = threadIdx.x; s < S; s += blockDim.x) {
@@ -514,8 +514,8 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_move_deposit(
     float a[4] = {0.f, 0.f, 0.f, 0.f};
     int bad = 0;
     unsigned long long strays = 0;
-    const int per = (n_items + gridDim.x - 1) / gridDim.x;
-    const int it0 = min(n_items, (int)blockIdx.x * per), it1 = min(n_items, it0 + per);
+    int it0, it1;
+    item_run(items, n_items, it0, it1);
     const int S = cic::tile_of(g, 0).S;
     void *sum = reinterpret_cast<char *>(acc) + cic::sum_offset(S);
     for (int s = threadIdx.x; s < S; s += blockDim.x) {

@@ -108,6 +108,31 @@ constexpr int kMaxChunk = 4095;   // fixed-point tile slots stay below 2^32
 // Set the thread-local message returned by pic_last_error(); returns `code`.
 int record_error(int code, const char *fmt, ...);
 
+// The run of work items [it0, it1) of this block.  Items cover the particles
+// [0, P) in order; item i costs its particles plus a fixed kItemCost for its
+// tile's fold and flush, so the cost before item i is y_i + kItemCost i, and
+// the block takes the items that start within its equal share of the total.
+#ifndef PIC_ITEM_COST
+#define PIC_ITEM_COST 1024
+#endif
+constexpr long long kItemCost = PIC_ITEM_COST;
+__device__ __forceinline__ void item_run(const int4 *__restrict__ items, int n_items, int &it0,
+                                         int &it1) {
+    const long long total =
+        n_items > 0 ? (long long)items[n_items - 1].z + kItemCost * n_items : 0;
+    auto first_from = [&](long long cost) {   // first item whose cost prefix is >= cost
+        int lo = 0, hi = n_items;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((long long)items[mid].y + kItemCost * mid < cost) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    it0 = first_from(total * blockIdx.x / gridDim.x);
+    it1 = blockIdx.x + 1 == gridDim.x ? n_items : first_from(total * (blockIdx.x + 1) / gridDim.x);
+}
+
 // ----------------------------------------------------------------------------
 // kernel launchers (defined in the k_*.cu files); all enqueue on `st`.
 // ----------------------------------------------------------------------------
