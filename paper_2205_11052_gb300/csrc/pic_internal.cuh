@@ -111,26 +111,51 @@ int record_error(int code, const char *fmt, ...);
 // The run of work items [it0, it1) of this block.  Items cover the particles
 // [0, P) in order; item i costs its particles plus a fixed kItemCost for its
 // tile's fold and flush, so the cost before item i is y_i + kItemCost i, and
-// the block takes the items that start within its equal share of the total.
+// the block takes the items that start within its equal share of the total
+// (with fewer items than blocks, block b takes item b).
 #ifndef PIC_ITEM_COST
 #define PIC_ITEM_COST 1024
 #endif
 constexpr long long kItemCost = PIC_ITEM_COST;
+// Called by every thread of the block (it synchronises): the two item
+// indices are found by a two-level search in which each thread tests one
+// sample per round, so a block start costs a few dependent loads (two while
+// n_items <= blockDim^2), not log2(n_items).
 __device__ __forceinline__ void item_run(const int4 *__restrict__ items, int n_items, int &it0,
                                          int &it1) {
+    if (n_items <= (int)gridDim.x) {
+        // at most one item per block: consecutive blocks (spread over the SMs)
+        // take consecutive items, however large
+        it0 = min((int)blockIdx.x, n_items);
+        it1 = min((int)blockIdx.x + 1, n_items);
+        return;
+    }
     const long long total =
         n_items > 0 ? (long long)items[n_items - 1].z + kItemCost * n_items : 0;
-    auto first_from = [&](long long cost) {   // first item whose cost prefix is >= cost
-        int lo = 0, hi = n_items;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if ((long long)items[mid].y + kItemCost * mid < cost) lo = mid + 1;
-            else hi = mid;
-        }
-        return lo;
-    };
-    it0 = first_from(total * blockIdx.x / gridDim.x);
-    it1 = blockIdx.x + 1 == gridDim.x ? n_items : first_from(total * (blockIdx.x + 1) / gridDim.x);
+    const long long c0 = total * blockIdx.x / gridDim.x;
+    const long long c1 = total * (blockIdx.x + 1) / gridDim.x;
+    auto cost = [&](int i) { return (long long)items[i].y + kItemCost * i; };
+    // level 1: sample i_t = (t + 1) * step - 1; the first index with cost >= c lies
+    // in the step-wide bucket after the last sample below c
+    const int nt = (int)blockDim.x;
+    const int step = (n_items + nt - 1) / nt;   // >= 1 when n_items > 0
+    const int t = (int)threadIdx.x;
+    const int si = min((t + 1) * step, n_items) - 1;
+    const long long cs = (n_items > 0 && si >= 0) ? cost(si) : 0;
+    const int b0 = __syncthreads_count(n_items > 0 && si >= 0 && cs < c0 && (t + 1) * step <= n_items);
+    const int b1 = __syncthreads_count(n_items > 0 && si >= 0 && cs < c1 && (t + 1) * step <= n_items);
+    // level 2: the first index with cost >= c lies in [b * step, min(n, (b + 1) * step)):
+    // count the costs below c there, blockDim at a time
+    const int lo0 = b0 * step, lo1 = b1 * step;
+    const int hi0 = min(n_items, lo0 + step), hi1 = min(n_items, lo1 + step);
+    int r0 = 0, r1 = 0;
+    for (int k = 0; k < step; k += nt) {
+        const int j0 = lo0 + k + t, j1 = lo1 + k + t;
+        r0 += __syncthreads_count(j0 < hi0 && cost(j0) < c0);
+        r1 += __syncthreads_count(j1 < hi1 && cost(j1) < c1);
+    }
+    it0 = min(n_items, lo0 + r0);
+    it1 = blockIdx.x + 1 == gridDim.x ? n_items : min(n_items, lo1 + r1);
 }
 
 // ----------------------------------------------------------------------------
