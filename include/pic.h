@@ -165,13 +165,17 @@ const char *pic_last_error(void);
 /* ------------------------------------------------------------ state I/O */
 
 /* Load n synchronised particles (x_0, v_0), FP64 arrays of shape (n, 3),
- * from host memory (src_is_device = 0; copied in chunks through the arena)
- * or device memory (src_is_device = 1).  Positions may lie outside [0, L)
- * and are wrapped periodically.  Resets the step counter and diagnostics,
- * half-drifts to x_{1/2} = x_0 + dt/2 v_0 (the drift-kick-drift state kept
- * on the device), stores each particle as (cell, FP32 offset, FP32 velocity)
- * and bins it (Section 3.2; particle storage as in Section 2's SoA layout).
- * Host sources synchronise; device sources are enqueued.
+ * from host memory (src_is_device = 0) or device memory (src_is_device = 1).
+ * Page-locked host arrays are read in place by the load kernel (above 2^22
+ * particles in ranges, each binned on a library-owned side stream while the
+ * next one is read); pageable host arrays are copied in chunks through the
+ * arena.  Positions may lie outside [0, L) and are wrapped periodically.
+ * Resets the step counter and diagnostics, half-drifts to
+ * x_{1/2} = x_0 + dt/2 v_0 (the drift-kick-drift state kept on the device),
+ * stores each particle as (cell, FP32 offset, FP32 velocity) and bins it
+ * (Section 3.2; particle storage as in Section 2's SoA layout); particles in
+ * arbitrary order go through coarse binning passes first.  Host sources
+ * synchronise; device sources are enqueued.
  * Errors: PIC_ERR_CAPACITY (n > capacity), PIC_ERR_ARG, PIC_ERR_CUDA. */
 int pic_load_particles(pic_handle_t h, const double *x, const double *v,
                        int64_t n, int src_is_device);
