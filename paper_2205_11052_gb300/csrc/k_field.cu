@@ -56,18 +56,43 @@ __global__ void k_green(int nx, int ny, int nz, int nh, double tpx, double tpy, 
     }
 }
 
+// (hi, lo) += a, with the rounding error of the FP32 sum (Knuth's TwoSum,
+// exact in round-to-nearest) carried in lo.
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float a) {
+    const float s = __fadd_rn(hi, a);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(a, bb));
+    lo = __fadd_rn(lo, err);
+    hi = s;
+}
+
+// (hi, lo) += x^2: the product x*x is split exactly into its rounded value
+// and the FMA residual x*x - fl(x*x) (an FP32 product of FP32 inputs is exact
+// in 48 bits)
+__device__ __forceinline__ void ff_add_sq(float &hi, float &lo, float x) {
+    const float p = __fmul_rn(x, x);
+    const float e = __fmaf_rn(x, x, -p);
+    ff_add(hi, lo, p);
+    lo = __fadd_rn(lo, e);
+}
+
+// Per-block partial sums of Ex^2, Ey^2, Ez^2 and rho.  Each thread keeps FP32
+// (hi, lo) pairs whose error is that of ~48-bit arithmetic (FP64 instructions
+// run at a small fraction of the FP32 rate on this part); the pairs are
+// combined in FP64 across threads and blocks in a fixed order.
 __global__ void __launch_bounds__(256) k_diag_field(int64_t ng, const float *__restrict__ rho,
                                                      const float4 *__restrict__ E4, double *part) {
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += stride) {
         const float4 e = E4[g];
-        const double ex = e.x, ey = e.y, ez = e.z;
-        s[0] += ex * ex;
-        s[1] += ey * ey;
-        s[2] += ez * ez;
-        s[3] += (double)rho[g];
+        ff_add_sq(hi[0], lo[0], e.x);
+        ff_add_sq(hi[1], lo[1], e.y);
+        ff_add_sq(hi[2], lo[2], e.z);
+        ff_add(hi[3], lo[3], rho[g]);
     }
+    double s[4];
+    for (int q = 0; q < 4; ++q) s[q] = (double)hi[q] + (double)lo[q];
     __shared__ double red[4][8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int q = 0; q < 4; ++q) {
