@@ -515,9 +515,50 @@ def adjoint_step(y: np.ndarray, lam_y: np.ndarray, lam_v: np.ndarray, grid: Grid
     return ly, lv_out
 
 
+def boris_rotation_dt(vm: np.ndarray, t: np.ndarray) -> np.ndarray:
+    """d/dt_k of the Boris rotation f(t) = vm + (vm + vm x t) x s(t),
+    s = 2t / (1 + |t|^2), for each row vm: (N, 3 (k), 3).
+
+    d(vm x t)/dt_k = vm x e_k and ds/dt_k = (2 / (1 + |t|^2)) (e_k - t_k s)."""
+    D = 1.0 + float(np.dot(t, t))
+    s = 2.0 * t / D
+    w = vm + np.cross(vm, t)
+    out = np.empty((vm.shape[0], 3, 3), dtype=np.float64)
+    for k in range(3):
+        ek = np.zeros(3)
+        ek[k] = 1.0
+        ds = (2.0 / D) * (ek - t[k] * s)
+        out[:, k, :] = np.cross(np.cross(vm, ek), s) + np.cross(w, ds)
+    return out
+
+
+def param_gradient_terms(y: np.ndarray, v: np.ndarray, e: np.ndarray, lam_y: np.ndarray,
+                         lam_v: np.ndarray, grid: Grid, params: Params):
+    """Contribution of one step to dJ/dB_ext (3) and dJ/d(wz2).
+
+    The step is v' = R(B) vm + h e, vm = v + h e, h = dt q/m / 2,
+    t = h B, e = G(y) E + wz2 Q(y) with Q(y) = (-(y-c)_x/2, -(y-c)_y/2, (y-c)_z)
+    (Section 4.3), and y' = y + dt v'.  With lv_tot = lam_v + dt lam_y (the
+    adjoint of v'), dJ/dB_k gets sum_p lv_tot . h df/dt_k(vm) and dJ/dwz2 gets
+    sum_p lv_tot . dv'/dwz2 = sum_p le . Q(y), le = h (R^T + I) lv_tot."""
+    h = 0.5 * params.dt * params.q_over_m
+    t = h * np.asarray(params.B, dtype=np.float64)
+    lv_tot = lam_v + params.dt * lam_y
+    vm = v + h * e
+    dB = h * np.einsum("pj,pkj->k", lv_tot, boris_rotation_dt(vm, t))
+    R = boris_rotation(params)
+    le = h * (lv_tot @ R + lv_tot)
+    c = 0.5 * np.asarray(grid.L, dtype=np.float64)
+    d = y - c
+    Q = np.stack([-0.5 * d[:, 0], -0.5 * d[:, 1], d[:, 2]], axis=1)
+    dwz2 = float(np.sum(le * Q))
+    return dB, dwz2
+
+
 def run_with_gradient(x0: np.ndarray, v0: np.ndarray, grid: Grid, params: Params,
-                      n_steps: int, weights=(1.0, 1.0, 1.0)):
-    """J of the field used by the last of n_steps steps, and dJ/dx0, dJ/dv0.
+                      n_steps: int, weights=(1.0, 1.0, 1.0), param_grad: bool = False):
+    """J of the field used by the last of n_steps steps, and dJ/dx0, dJ/dv0
+    (with param_grad, also dJ/dB_ext (3) and dJ/d(wz2)).
 
     Forward: y_0 = x_0 + dt/2 v_0, then n_steps - 1 updates of (y, v); the
     objective is the field energy at y_{n_steps-1}.  The forward states are
@@ -525,8 +566,8 @@ def run_with_gradient(x0: np.ndarray, v0: np.ndarray, grid: Grid, params: Params
     dt = params.dt
     N = x0.shape[0]
     qp = params.Q / N
-    c = dt * params.q_over_m
     ys = [wrap(x0 + 0.5 * dt * v0, grid)]
+    vs, es = [], []
     v = v0.copy()
     for _ in range(n_steps - 1):
         y = ys[-1]
@@ -534,15 +575,25 @@ def run_with_gradient(x0: np.ndarray, v0: np.ndarray, grid: Grid, params: Params
         e = gather(y, E, grid)
         if params.wz2 != 0.0:
             e = e + external_field(y, grid, params.wz2)
+        vs.append(v)
+        es.append(e)
         v = boris_kick(v, e, params.q_over_m, params.B, dt)
         ys.append(wrap(y + dt * v, grid))
     J = field_energy(ys[-1], grid, params, weights)
     ly = field_energy_gradient(ys[-1], grid, params, weights)
     lv = np.zeros_like(ly)
+    gB = np.zeros(3)
+    gw = 0.0
     for n in range(n_steps - 2, -1, -1):
+        if param_grad:
+            dB, dw = param_gradient_terms(ys[n], vs[n], es[n], ly, lv, grid, params)
+            gB += dB
+            gw += dw
         ly, lv = adjoint_step(ys[n], ly, lv, grid, params)
     dx0 = ly
     dv0 = lv + 0.5 * dt * ly
+    if param_grad:
+        return J, dx0, dv0, gB, gw
     return J, dx0, dv0
 
 

@@ -443,3 +443,49 @@ def test_gradient_with_respect_to_the_perturbation_amplitude():
     fd = (po.run_with_gradient(wp.x, wp.v, grid, p, 6, wts)[0]
           - po.run_with_gradient(wm.x, wm.v, grid, p, 6, wts)[0]) / (2 * eps)
     assert abs(fd - ad) <= 1e-5 * abs(ad)
+
+
+@pytest.mark.parametrize("wz2,B", [(0.3, (0.0, 0.0, 5.0)), (0.0, (1.0, -2.0, 3.0)),
+                                   (0.3, (0.0, 0.0, 0.0))])
+def test_parameter_gradients_match_central_differences(wz2, B):
+    """dJ/dB_k and dJ/d(wz2) from the reverse sweep equal central differences
+    of J over the field parameters (the particles' initial state fixed),
+    including the sensitivity to a magnetic field at B = 0."""
+    w = pi.bump_on_tail(n=8, ppc=4, seed=5, alpha=0.2, k=0.5)
+    grid = po.Grid(w.n, w.L)
+    wts = (1.0, 1.0, 1.0)
+    p = po.Params(dt=0.1, Q=w.Q, wz2=wz2, B=B)
+    J, _, _, gB, gw = po.run_with_gradient(w.x, w.v, grid, p, 6, wts, param_grad=True)
+    eps = 1e-5
+    for k in range(3):
+        Bp = list(B)
+        Bm = list(B)
+        Bp[k] += eps
+        Bm[k] -= eps
+        Jp = po.run_with_gradient(w.x, w.v, grid, po.Params(dt=0.1, Q=w.Q, wz2=wz2, B=tuple(Bp)), 6, wts)[0]
+        Jm = po.run_with_gradient(w.x, w.v, grid, po.Params(dt=0.1, Q=w.Q, wz2=wz2, B=tuple(Bm)), 6, wts)[0]
+        fd = (Jp - Jm) / (2 * eps)
+        assert abs(fd - gB[k]) <= 1e-6 * max(abs(fd), 1e-3 * J), (k, fd, gB[k])
+    Jp = po.run_with_gradient(w.x, w.v, grid, po.Params(dt=0.1, Q=w.Q, wz2=wz2 + eps, B=B), 6, wts)[0]
+    Jm = po.run_with_gradient(w.x, w.v, grid, po.Params(dt=0.1, Q=w.Q, wz2=wz2 - eps, B=B), 6, wts)[0]
+    fd = (Jp - Jm) / (2 * eps)
+    assert abs(fd - gw) <= 1e-6 * max(abs(fd), 1e-3 * J), (fd, gw)
+
+
+def test_boris_rotation_derivative_matches_central_differences():
+    """boris_rotation_dt against central differences of the rotation in t."""
+    rng = np.random.default_rng(4)
+    vm = rng.standard_normal((5, 3))
+    t = np.array([0.3, -0.2, 0.5])
+    d = po.boris_rotation_dt(vm, t)
+
+    def f(tt):
+        s = 2.0 * tt / (1.0 + float(np.dot(tt, tt)))
+        return vm + np.cross(vm + np.cross(vm, tt), s)
+
+    eps = 1e-6
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = eps
+        fd = (f(t + e) - f(t - e)) / (2 * eps)
+        assert np.max(np.abs(fd - d[:, k, :])) < 1e-8
