@@ -107,6 +107,13 @@ typedef struct {
  * 2014) seeded with params.seed, c = ((n 2^32) + pid) 4 + d + 1.  Not
  * available with the adjoint or in ensembles. */
 #define PIC_OPT_UNIFORM_MOVE 2
+/* The adjoint also yields the gradient of J with respect to the field
+ * parameters: B_ext (Eq. momentum_eqn through the Boris rotation) and the
+ * quadrupole strength wz2 = omega_z^2 (Section 4.3), read with
+ * pic_adjoint_param_gradient.  The forward sweep then also stores each step's
+ * velocities before the kick (12 more bytes per particle and stored step in
+ * the adjoint buffer). */
+#define PIC_OPT_ADJOINT_PARAMS 4
 
 /* Sizes the caller must provide before any device work. */
 typedef struct {
@@ -304,6 +311,16 @@ int pic_adjoint_forward(pic_handle_t h, int n_steps, int checkpoint_every,
  * to its FP32 storage) and the step counter. */
 int pic_adjoint_backward(pic_handle_t h, double scale, double *dJdx, double *dJdv,
                          int dst_is_device);
+
+/* After pic_adjoint_backward on a run created with PIC_OPT_ADJOINT_PARAMS:
+ * grad = scale * (dJ/dB_x, dJ/dB_y, dJ/dB_z, dJ/d(wz2)) on the host.  Each
+ * reverse step adds sum_p lv_tot^T (dR/dB_k) vm (R the Boris rotation, vm the
+ * velocity after the first half kick, lv_tot the adjoint of the step's new
+ * velocity) and sum_p le . Q(y_p) (Q the quadrupole's direction field, le the
+ * adjoint of the particle's field); the per-step sums are FP64 over FP32
+ * per-thread partials.  Errors: PIC_ERR_STATE (option not set, or no
+ * backward pass since the last forward), PIC_ERR_ARG (null grad). */
+int pic_adjoint_param_gradient(pic_handle_t h, double grad[4]);
 
 /* sum_i a_i b_i over n FP64 device values, accumulated in FP64 in a fixed
  * order (e.g. dJ/dalpha = <dJ/dx_0, dx_0/dalpha>); result to host memory. */

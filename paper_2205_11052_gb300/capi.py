@@ -54,6 +54,7 @@ class pic_params_t(C.Structure):
 
 PIC_OPT_FIXED_DEPOSIT = 1
 PIC_OPT_UNIFORM_MOVE = 2
+PIC_OPT_ADJOINT_PARAMS = 4
 
 
 class pic_bufsizes_t(C.Structure):
@@ -105,6 +106,7 @@ _SIGNATURES = {
     "pic_adjoint_forward": (C.c_int, [pic_handle_t, C.c_int, C.c_int, C.POINTER(C.c_double),
                                       C.c_void_p, C.c_size_t, C.POINTER(C.c_double)]),
     "pic_adjoint_backward": (C.c_int, [pic_handle_t, C.c_double, C.c_void_p, C.c_void_p, C.c_int]),
+    "pic_adjoint_param_gradient": (C.c_int, [pic_handle_t, C.POINTER(C.c_double)]),
     "pic_dot_f64": (C.c_int, [pic_handle_t, C.c_void_p, C.c_void_p, C.c_int64,
                               C.POINTER(C.c_double)]),
     "pic_batch_create": (C.c_int, [C.POINTER(pic_instance_t), C.c_int, C.c_double,
@@ -310,6 +312,13 @@ def pic_adjoint_forward(h, n_steps: int, checkpoint_every: int, weights, buf_ptr
 def pic_adjoint_backward(h, scale: float, gx_ptr: int, gv_ptr: int, dst_is_device: bool) -> None:
     check(_call("pic_adjoint_backward", h, C.c_double(scale), C.c_void_p(gx_ptr),
                 C.c_void_p(gv_ptr), C.c_int(1 if dst_is_device else 0)), "pic_adjoint_backward")
+
+
+def pic_adjoint_param_gradient(h):
+    """(dJ/dB_x, dJ/dB_y, dJ/dB_z, dJ/d(wz2)) of the last backward pass."""
+    out = (C.c_double * 4)()
+    check(_call("pic_adjoint_param_gradient", h, out), "pic_adjoint_param_gradient")
+    return tuple(out)
 
 
 def pic_dot_f64(h, a_ptr: int, b_ptr: int, n: int) -> float:

@@ -111,6 +111,7 @@ __global__ void k_adj_seed(int64_t ng, const float4 *__restrict__ E4, float4 *__
 //
 // The gather term is the offset gradient (interp_grad) of the CIC
 // interpolation of s_abc = le . E at the 8 corners.
+template <bool PG>
 __global__ void __launch_bounds__(256, PIC_ADJ_MIN_BLOCKS) k_adj_push(Geom g, const Ctrl *__restrict__ ctrl,
                                                       const int4 *__restrict__ items,
                                                       const int32_t *__restrict__ ycell,
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(256, PIC_ADJ_MIN_BLOCKS) k_adj_push(Geom g, co
                                                       const float4 *__restrict__ E8,
                                                       float4 *__restrict__ lE4, float c_kick,
                                                       float dt, float wz2, AdjRhoTerm rt,
-                                                      AdjBound ab, Ctrl *ctrl_w) {
+                                                      AdjBound ab, PGrad pg, Ctrl *ctrl_w) {
     // 3 * S integer accumulators (x, y, z components) in units of 1 / qs
     extern __shared__ int acc[];
     const int cur = ctrl->cur;
@@ -154,6 +155,10 @@ __global__ void __launch_bounds__(256, PIC_ADJ_MIN_BLOCKS) k_adj_push(Geom g, co
     const int S0 = g.tile[0] + 2 * G + 1, S1 = g.tile[1] + 2 * G + 1, S2 = g.tile[2] + 2 * G + 1;
     const int S01 = S0 * S1, S = S01 * S2;
     int bad = 0;
+    // PG: sum_p lv_tot_i vm_j (row-major) and sum_p le . Q
+    float pa[kPGradTerms];
+#pragma unroll
+    for (int q = 0; q < kPGradTerms; ++q) pa[q] = 0.0f;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const int4 item = items[it];
         const int tile = item.x;
@@ -184,6 +189,7 @@ __global__ void __launch_bounds__(256, PIC_ADJ_MIN_BLOCKS) k_adj_push(Geom g, co
             float lv0 = lam.v[0][p] + dt * ly0;
             float lv1 = lam.v[1][p] + dt * ly1;
             float lv2 = lam.v[2][p] + dt * ly2;
+            const float lt0 = lv0, lt1 = lv1, lt2 = lv2;   // lv_tot (for PG)
             float le0, le1, le2;
             if (ab.mag) {
                 // lv <- R^T lv_tot, le = (c/2)(R^T lv_tot + lv_tot)
@@ -205,12 +211,41 @@ __global__ void __launch_bounds__(256, PIC_ADJ_MIN_BLOCKS) k_adj_push(Geom g, co
             int nd[8];
             corners(i, j, k, nx, ny, nz, nd);
             float sc[8];
+            float ex = 0.0f, ey = 0.0f, ez = 0.0f;   // E at y (PG)
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 float4 e0, e1;
                 ld_pair(E8 + 2 * nd[2 * r], e0, e1);
                 sc[2 * r] = le0 * e0.x + le1 * e0.y + le2 * e0.z;
                 sc[2 * r + 1] = le0 * e1.x + le1 * e1.y + le2 * e1.z;
+                if (PG) {
+                    // corners 2r, 2r + 1 share the (y, z) factor of their weights
+                    const float wyz = ((r & 1) ? fy : 1.0f - fy) * ((r & 2) ? fz : 1.0f - fz);
+                    const float w0 = (1.0f - fx) * wyz, w1 = fx * wyz;
+                    ex += w0 * e0.x + w1 * e1.x;
+                    ey += w0 * e0.y + w1 * e1.y;
+                    ez += w0 * e0.z + w1 * e1.z;
+                }
+            }
+            if (PG) {
+                // the quadrupole direction Q(y) = (-(x-c)/2, -(y-c)/2, (z-c)) as in
+                // the forward kick, vm = v + (c_kick / 2) (e + wz2 Q); sums of
+                // lv_tot_i vm_j and le . Q
+                float ux = (float)i - pg.half_n[0] + 0.5f + fx;
+                float uy = (float)j - pg.half_n[1] + 0.5f + fy;
+                float uz = (float)k - pg.half_n[2] + 0.5f + fz;
+                if (ux >= pg.half_n[0]) ux -= (float)nx;
+                if (uy >= pg.half_n[1]) uy -= (float)ny;
+                if (uz >= pg.half_n[2]) uz -= (float)nz;
+                const float Q0 = -0.5f * ux * pg.h[0], Q1 = -0.5f * uy * pg.h[1], Q2 = uz * pg.h[2];
+                const float hc = 0.5f * c_kick;
+                const float vm0 = pg.yv[0][p] + hc * (ex + wz2 * Q0);
+                const float vm1 = pg.yv[1][p] + hc * (ey + wz2 * Q1);
+                const float vm2 = pg.yv[2][p] + hc * (ez + wz2 * Q2);
+                pa[0] += lt0 * vm0; pa[1] += lt0 * vm1; pa[2] += lt0 * vm2;
+                pa[3] += lt1 * vm0; pa[4] += lt1 * vm1; pa[5] += lt1 * vm2;
+                pa[6] += lt2 * vm0; pa[7] += lt2 * vm1; pa[8] += lt2 * vm2;
+                pa[9] += le0 * Q0 + le1 * Q1 + le2 * Q2;
             }
             float dx, dy, dz;
             interp_grad(fx, fy, fz, sc, dx, dy, dz);
@@ -268,6 +303,41 @@ __global__ void __launch_bounds__(256, PIC_ADJ_MIN_BLOCKS) k_adj_push(Geom g, co
     max_to(&ctrl_w->adj_lv[ab.par], mlv);
     if (bad) atomicOr(&ctrl_w->flags, PIC_FLAG_BAD_CELL);
     if (nonfinite) atomicOr(&ctrl_w->flags, PIC_FLAG_NONFINITE);
+    if (PG) {
+        // block sums in FP64, fixed order: warp shuffles, then the 8 warps
+        __shared__ double red[kPGradTerms][8];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int q = 0; q < kPGradTerms; ++q) {
+            double t = (double)pa[q];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) red[q][wid] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < kPGradTerms) {
+            double t = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[threadIdx.x][q];
+            pg.part[(size_t)kPGradTerms * blockIdx.x + threadIdx.x] = t;
+        }
+    }
+}
+
+// acc[q] += sum over blocks of part[b][q]: strided per-thread sums, then a
+// fixed tree (one block of 256 threads)
+__global__ void k_pgrad_acc(const double *__restrict__ part, int blocks, double *acc) {
+    __shared__ double red[kPGradTerms][256];
+    double s[kPGradTerms];
+    for (int q = 0; q < kPGradTerms; ++q) s[q] = 0.0;
+    for (int b = threadIdx.x; b < blocks; b += blockDim.x)
+        for (int q = 0; q < kPGradTerms; ++q) s[q] += part[(size_t)kPGradTerms * b + q];
+    for (int q = 0; q < kPGradTerms; ++q) red[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int q = 0; q < kPGradTerms; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if ((int)threadIdx.x < kPGradTerms) acc[threadIdx.x] += red[threadIdx.x][0];
 }
 
 // lrho^ = sum_d (+i g_d / |k|^2) lE^_d / N_g   (S^T, with the C2R 1/N_g folded in)
@@ -442,18 +512,32 @@ cudaError_t launch_adj_seed(int64_t ng, const float4 *E4, float4 *lE4, const dou
 cudaError_t launch_adj_push(const Geom &g, const Ctrl *ctrl, const int4 *items, int max_items,
                             const int32_t *ycell, const float *const yo[3], const float4 *E8,
                             float4 *lE4, float c_kick, float dt, float wz2, const AdjRhoTerm &rt,
-                            const AdjBound &ab, Ctrl *ctrl_w, cudaStream_t st) {
+                            const AdjBound &ab, const PGrad &pg, Ctrl *ctrl_w, cudaStream_t st) {
     const int S = (g.tile[0] + 2 * g.guard + 1) * (g.tile[1] + 2 * g.guard + 1) *
                   (g.tile[2] + 2 * g.guard + 1);
     const size_t smem = sizeof(int) * 3 * (size_t)S;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_adj_push, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    const int blocks = std::max(1, std::min(152 * PIC_ADJ_MIN_BLOCKS * 2, max_items));
-    k_adj_push<<<blocks, 256, smem, st>>>(g, ctrl, items, ycell, yo[0], yo[1], yo[2], E8, lE4,
-                                          c_kick, dt, wz2, rt, ab, ctrl_w);
+    const int blocks = std::max(1, std::min(kAdjPushMaxBlocks, max_items));
+#define PIC_ADJ(PGV)                                                                            \
+    do {                                                                                        \
+        if (smem > 48 * 1024) {                                                                 \
+            cudaError_t e = cudaFuncSetAttribute(k_adj_push<PGV>,                               \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                                 (int)smem);                                    \
+            if (e != cudaSuccess) return e;                                                     \
+        }                                                                                       \
+        k_adj_push<PGV><<<blocks, 256, smem, st>>>(g, ctrl, items, ycell, yo[0], yo[1], yo[2],  \
+                                                   E8, lE4, c_kick, dt, wz2, rt, ab, pg,        \
+                                                   ctrl_w);                                     \
+    } while (0)
+    if (pg.part) PIC_ADJ(true);
+    else PIC_ADJ(false);
+#undef PIC_ADJ
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pgrad_acc(const double *part, int max_items, double *acc, cudaStream_t st) {
+    const int blocks = std::max(1, std::min(kAdjPushMaxBlocks, max_items));
+    k_pgrad_acc<<<1, 256, 0, st>>>(part, blocks, acc);
     return cudaGetLastError();
 }
 

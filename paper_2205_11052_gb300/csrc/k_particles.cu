@@ -323,6 +323,11 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g,
                 __stcs(save.o[0] + p, fx);
                 __stcs(save.o[1] + p, fy);
                 __stcs(save.o[2] + p, fz);
+                if (save.v[0]) {
+                    __stcs(save.v[0] + p, vx);
+                    __stcs(save.v[1] + p, vy);
+                    __stcs(save.v[2] + p, vz);
+                }
             }
             pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E8, sparse, acc, t, rho, rho64, qscale, c, fx, fy,
                                           fz, vx, vy, vz, bad, strays, a);

@@ -95,6 +95,8 @@ struct pic_ctx {
         char *buf;
         int64_t step0;
         long long step0_dev;
+        double pgrad[4];    // dJ/dB_ext (3), dJ/d(wz2) of the last backward pass
+        bool pgrad_ready;
     } adj;
     // phase timers: a ring of event pairs per phase, drained when it wraps
     bool timing;
@@ -346,6 +348,7 @@ int do_solve(pic_ctx *c) {
 }
 
 bool uniform_move(const pic_ctx *c) { return (c->prm.options & PIC_OPT_UNIFORM_MOVE) != 0; }
+bool param_grads(const pic_ctx *c) { return (c->prm.options & PIC_OPT_ADJOINT_PARAMS) != 0; }
 
 int do_gather_push(pic_ctx *c, bool diag) {
     int r = timer_begin(c, PIC_PHASE_PUSH);
@@ -426,14 +429,16 @@ int do_push_deposit(pic_ctx *c, bool diag, const SaveY &save = SaveY{}) {
 // starts a new particle order; an "order record" keeps its pid array and work
 // items.  Buffer:
 //   checkpoints [n_ckpt]: cell, o[3], v[3], pid (order record 0), items, n_items
-//   per-step store [K]  : cell, o[3] and E4 of each step of the segment being
-//                         reversed
+//   per-step store [K]  : cell, o[3] (and, for parameter gradients, v[3]
+//                         before the kick) and E8 of each step of the segment
+//                         being reversed
 //   order records [nrec - 1]: pid, items, n_items of records 1.. of that segment
 //   multiplier backup   : ly[3], lv[3] while a segment is recomputed/permuted
+//   parameter gradients : per-block partials of a reverse step and the 10 sums
 struct AdjLayout {
     size_t arr, items, ckpt, segy, segE, rec, n_ckpt, off_items, off_nitems;
-    size_t off_segy, off_segE, off_rec, off_lam, total;
-    int R, nrec;
+    size_t off_segy, off_segE, off_rec, off_lam, off_pg, total;
+    int R, nrec, ny;   // ny: arrays per stored step (4, or 7 with velocities)
 };
 
 AdjLayout adj_layout(const pic_ctx *c, int n_steps, int K) {
@@ -443,7 +448,8 @@ AdjLayout adj_layout(const pic_ctx *c, int n_steps, int K) {
     L.off_items = 8 * L.arr;
     L.off_nitems = L.off_items + L.items;
     L.ckpt = L.off_nitems + kAlign;
-    L.segy = 4 * L.arr;                       // cell, o[3]
+    L.ny = param_grads(c) ? 7 : 4;
+    L.segy = (size_t)L.ny * L.arr;            // cell, o[3] (, v[3])
     L.segE = align_up((size_t)c->ng * 32);    // x-paired E of one step
     L.rec = L.arr + L.items + kAlign;         // pid, items, n_items
     L.R = std::max(1, std::min(c->prm.sort_period > 0 ? c->prm.sort_period : K, K));
@@ -454,7 +460,10 @@ AdjLayout adj_layout(const pic_ctx *c, int n_steps, int K) {
     L.off_segE = L.off_segy + (size_t)K * L.segy;
     L.off_rec = L.off_segE + (size_t)K * L.segE;
     L.off_lam = L.off_rec + (size_t)(L.nrec - 1) * L.rec;
-    L.total = L.off_lam + 6 * L.arr;
+    L.off_pg = L.off_lam + 6 * L.arr;
+    L.total = L.off_pg + (param_grads(c) ? align_up(sizeof(double) * kPGradTerms *
+                                                    ((size_t)kAdjPushMaxBlocks + 1))
+                                         : 0);
     return L;
 }
 
@@ -571,6 +580,38 @@ void boris_rotation(const pic_ctx *c, int *mag, float R[9]) {
     }
 }
 
+// M[k] (row-major 3 x 3) = dR/dB_k of the Boris rotation R v = v + (v + v x t) x s,
+// t = h B (h = dt q/m / 2), s = 2t / (1 + |t|^2): column j is
+// h [ (e_j x e_k) x s + (e_j + e_j x t) x (2 / (1 + |t|^2)) (e_k - t_k s) ]
+void boris_rotation_derivative(const pic_ctx *c, double M[3][9]) {
+    const double h = 0.5 * c->prm.dt * c->sp.q_over_m;
+    const double t[3] = {h * c->prm.B_ext[0], h * c->prm.B_ext[1], h * c->prm.B_ext[2]};
+    const double D = 1.0 + t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    const double sv[3] = {2.0 * t[0] / D, 2.0 * t[1] / D, 2.0 * t[2] / D};
+    auto cross = [](const double a[3], const double b[3], double o[3]) {
+        o[0] = a[1] * b[2] - a[2] * b[1];
+        o[1] = a[2] * b[0] - a[0] * b[2];
+        o[2] = a[0] * b[1] - a[1] * b[0];
+    };
+    for (int k = 0; k < 3; ++k) {
+        double ek[3] = {0.0, 0.0, 0.0};
+        ek[k] = 1.0;
+        double ds[3];
+        for (int d = 0; d < 3; ++d) ds[d] = (2.0 / D) * (ek[d] - t[k] * sv[d]);
+        for (int j = 0; j < 3; ++j) {
+            double ej[3] = {0.0, 0.0, 0.0};
+            ej[j] = 1.0;
+            double a[3], b[3], w[3], x[3], wt[3];
+            cross(ej, ek, a);
+            cross(a, sv, b);               // (e_j x e_k) x s
+            cross(ej, t, wt);
+            for (int d = 0; d < 3; ++d) w[d] = ej[d] + wt[d];
+            cross(w, ds, x);               // (e_j + e_j x t) x ds
+            for (int i = 0; i < 3; ++i) M[k][3 * i + j] = h * (b[i] + x[i]);
+        }
+    }
+}
+
 AdjBound step_bound(const AdjBound &ab, int par) {
     AdjBound b = ab;
     b.par = par;
@@ -652,11 +693,13 @@ int adj_keep_step(pic_ctx *c, const AdjLayout &L, int seg, int a0, int n, int *c
     if ((r = do_solve(c)) || (r = adj_keep_E(c, L, n - a0))) return r;
     if (c->np == 0) return do_push_deposit(c, false);
     // y_n is written by the push that reads it
-    char *y[4];
-    buf_arrays(c->adj.buf + L.off_segy + (size_t)(n - a0) * L.segy, L.arr, 4, y);
-    SaveY save;
+    char *y[7];
+    buf_arrays(c->adj.buf + L.off_segy + (size_t)(n - a0) * L.segy, L.arr, L.ny, y);
+    SaveY save{};
     save.cell = reinterpret_cast<int32_t *>(y[0]);
     for (int d = 0; d < 3; ++d) save.o[d] = reinterpret_cast<float *>(y[1 + d]);
+    if (L.ny == 7)
+        for (int d = 0; d < 3; ++d) save.v[d] = reinterpret_cast<float *>(y[4 + d]);
     return do_push_deposit(c, false, save);
 }
 
@@ -754,7 +797,7 @@ int pic_create(const pic_grid_t *grid, const pic_species_t *species, const pic_p
         return fail(PIC_ERR_ARG, "block must be 0 or a multiple of 32 in 32..256");
     if (params->chunk != 0 && (params->chunk < 32 || params->chunk > kMaxChunk))
         return fail(PIC_ERR_ARG, "chunk must be 0 or in 32..%d", kMaxChunk);
-    if (params->options & ~(PIC_OPT_FIXED_DEPOSIT | PIC_OPT_UNIFORM_MOVE))
+    if (params->options & ~(PIC_OPT_FIXED_DEPOSIT | PIC_OPT_UNIFORM_MOVE | PIC_OPT_ADJOINT_PARAMS))
         return fail(PIC_ERR_ARG, "unknown option bits");
 
     pic_ctx *c = new (std::nothrow) pic_ctx();
@@ -1230,6 +1273,11 @@ int pic_adjoint_backward(pic_handle_t c, double scale, double *gx, double *gv, i
     boris_rotation(c, &ab.mag, ab.R);
     float4 *lE4 = c->at<float4>(c->lay.adjE4);
     const float2 *lrho2 = c->at<float2>(c->lay.lrho2);
+    const bool pgrad = param_grads(c);
+    double *pg_part = reinterpret_cast<double *>(c->adj.buf + L.off_pg);
+    double *pg_acc = pg_part + (size_t)kPGradTerms * kAdjPushMaxBlocks;
+    c->adj.pgrad_ready = false;
+    if (pgrad) PIC_CUDA(cudaMemsetAsync(pg_acc, 0, sizeof(double) * kPGradTerms, c->st));
 
     // terminal: lE = 2 h^3 w E of the final field, then (dD/dy)^T S^T
     PIC_CUDA(cudaMemsetAsync(c->ctrl()->adj_ly, 0, sizeof(c->ctrl()->adj_ly) * 3, c->st));
@@ -1270,17 +1318,27 @@ int pic_adjoint_backward(pic_handle_t c, double scale, double *gx, double *gv, i
         if (b0 > a0 && (r = adj_use_items(c, L, s, rec))) return r;
         AdjRhoTerm rt{};
         for (int n = b0 - 1; n >= a0; --n) {
-            char *y[4];
-            buf_arrays(c->adj.buf + L.off_segy + (size_t)(n - a0) * L.segy, L.arr, 4, y);
+            char *y[7];
+            buf_arrays(c->adj.buf + L.off_segy + (size_t)(n - a0) * L.segy, L.arr, L.ny, y);
             const int32_t *ycell = reinterpret_cast<const int32_t *>(y[0]);
             const float *yo[3] = {reinterpret_cast<const float *>(y[1]),
                                   reinterpret_cast<const float *>(y[2]),
                                   reinterpret_cast<const float *>(y[3])};
             const float4 *En = reinterpret_cast<const float4 *>(c->adj.buf + L.off_segE +
                                                                 (size_t)(n - a0) * L.segE);
+            PGrad pg{};
+            if (pgrad) {
+                for (int d = 0; d < 3; ++d) {
+                    pg.yv[d] = reinterpret_cast<const float *>(y[4 + d]);
+                    pg.half_n[d] = 0.5f * (float)c->geom.n[d];
+                    pg.h[d] = (float)c->h[d];
+                }
+                pg.part = pg_part;
+            }
             PIC_CUDA(launch_adj_push(c->geom, c->ctrl(), c->at<int4>(c->lay.items),
                                      (int)c->max_items, ycell, yo, En, lE4, c_kick, dt, wz2, rt,
-                                     step_bound(ab, n & 1), c->ctrl(), c->st));
+                                     step_bound(ab, n & 1), pg, c->ctrl(), c->st));
+            if (pgrad) PIC_CUDA(launch_pgrad_acc(pg_part, (int)c->max_items, pg_acc, c->st));
             if ((r = adj_solve(c, n & 1))) return r;
             rt.cell = ycell;
             for (int d = 0; d < 3; ++d) rt.o[d] = yo[d];
@@ -1337,7 +1395,33 @@ int pic_adjoint_backward(pic_handle_t c, double scale, double *gx, double *gv, i
     c->adj.cur_end = cur;
     c->adj.ready = false;
     c->rho_current = false;
+    double acc[kPGradTerms];
+    if (pgrad)
+        PIC_CUDA(cudaMemcpyAsync(acc, pg_acc, sizeof(acc), cudaMemcpyDeviceToHost, c->st));
     PIC_CUDA(cudaStreamSynchronize(c->st));
+    if (pgrad) {
+        // dJ/dB_k = sum_ij (dR/dB_k)_ij A_ij, A_ij = sum lv_tot_i vm_j over
+        // particles and steps; dJ/d(wz2) = sum le . Q
+        double M[3][9];
+        boris_rotation_derivative(c, M);
+        for (int k = 0; k < 3; ++k) {
+            double g = 0.0;
+            for (int q = 0; q < 9; ++q) g += M[k][q] * acc[q];
+            c->adj.pgrad[k] = scale * g;
+        }
+        c->adj.pgrad[3] = scale * acc[9];
+        c->adj.pgrad_ready = true;
+    }
+    return PIC_OK;
+}
+
+int pic_adjoint_param_gradient(pic_handle_t c, double grad[4]) {
+    int r = check_ready(c);
+    if (r) return r;
+    if (!grad) return fail(PIC_ERR_ARG, "null output array");
+    if (!param_grads(c)) return fail(PIC_ERR_STATE, "created without PIC_OPT_ADJOINT_PARAMS");
+    if (!c->adj.pgrad_ready) return fail(PIC_ERR_STATE, "no pic_adjoint_backward since the last forward");
+    for (int q = 0; q < 4; ++q) grad[q] = c->adj.pgrad[q];
     return PIC_OK;
 }
 

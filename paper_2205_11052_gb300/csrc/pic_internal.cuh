@@ -212,6 +212,7 @@ cudaError_t push_deposit_prepare(const Geom &g);
 struct SaveY {
     int32_t *cell;
     float *o[3];
+    float *v[3];   // also the velocities before the kick (null: not saved)
 };
 // E8: the x-paired field (launch_pair_E), 2 float4 per node
 cudaError_t launch_push_deposit(const Geom &g, const PushConst &pc, bool diag, bool fixed,
@@ -266,10 +267,24 @@ struct AdjRhoTerm {
     const float2 *lrho2;   // x-paired lrho (launch_pair_scalar)
     float sx, sy, sz;
 };
+// Parameter-gradient sums of one reverse step (part == nullptr: off): per
+// block, A_ij = sum_p lv_tot_i vm_j (9, row-major) and sum_p le . Q(y_p)
+// (Q the quadrupole direction field), from the saved velocities yv before the
+// kick; half_n and h give the box centre in cells and the spacing.
+struct PGrad {
+    const float *yv[3];
+    double *part;   // kPGradTerms doubles per block
+    float half_n[3], h[3];
+};
+constexpr int kPGradTerms = 10;
+constexpr int kAdjPushMaxBlocks = kNumSMs * PIC_ADJ_MIN_BLOCKS * 2;
 cudaError_t launch_adj_push(const Geom &g, const Ctrl *ctrl, const int4 *items, int max_items,
                             const int32_t *ycell, const float *const yo[3], const float4 *E8,
                             float4 *lE4, float c_kick, float dt, float wz2, const AdjRhoTerm &rt,
-                            const AdjBound &ab, Ctrl *ctrl_w, cudaStream_t st);
+                            const AdjBound &ab, const PGrad &pg, Ctrl *ctrl_w, cudaStream_t st);
+// acc[q] += the fixed-order sum of the kPGradTerms partials of the blocks the
+// last launch_adj_push used (max_items caps them as there)
+cudaError_t launch_pgrad_acc(const double *part, int max_items, double *acc, cudaStream_t st);
 cudaError_t launch_green_adj(const Geom &g, const double *L_d, const float2 *lE_hat,
                              float2 *lrho_hat, int64_t nhalf, cudaStream_t st);
 // where k_adj_rho writes the updated multipliers (o[0] == nullptr: in place)

@@ -178,6 +178,11 @@ class Simulation:
         capi.pic_adjoint_backward(self.handle, float(scale), gx.ctypes.data, gv.ctypes.data, False)
         return gx, gv
 
+    def adjoint_param_gradient(self):
+        """(dJ/dB_x, dJ/dB_y, dJ/dB_z, dJ/d(wz2)) of the last adjoint_backward
+        (the run must be created with options including PIC_OPT_ADJOINT_PARAMS)."""
+        return capi.pic_adjoint_param_gradient(self.handle)
+
     def dot(self, a, b) -> float:
         """FP64 sum of a * b over two CUDA float64 tensors of equal size."""
         a = a.contiguous()

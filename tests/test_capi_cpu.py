@@ -58,7 +58,7 @@ def test_create_and_sizes_without_gpu(lib):
     dict(n_particles=-1), dict(n_particles=2 ** 31), dict(q_over_m=0.0),
     dict(mode=(9, 0, 0)), dict(mode_comp=3), dict(block=48), dict(block=512),
     dict(chunk=8), dict(chunk=4096), dict(guard=-1), dict(B=(0.0, float("nan"), 0.0)),
-    dict(options=4),
+    dict(options=8),
 ])
 def test_create_rejects_bad_configs(lib, kw):
     with pytest.raises(capi.PicError) as e:

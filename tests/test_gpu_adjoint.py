@@ -209,3 +209,74 @@ def test_directional_derivative_with_the_benchmark_settings():
     J0 = po.run_with_gradient(w.x, w.v, g, p, n_steps, weights)[0]
     assert J == pytest.approx(J0, rel=1e-4)
     assert ad == pytest.approx(fd, rel=1e-3)
+
+
+PARAMS = capi.PIC_OPT_ADJOINT_PARAMS
+
+
+@pytest.mark.parametrize("wz2,B", [(0.3, (0.0, 0.0, 5.0)), (0.0, (1.0, -2.0, 3.0)),
+                                   (0.3, (0.0, 0.0, 0.0))],
+                         ids=["penning", "oblique-B", "quadrupole-B0"])
+@pytest.mark.parametrize("every", [4, 5], ids=["checkpoints", "kept"])
+def test_parameter_gradient_matches_oracle(wz2, B, every):
+    """dJ/dB_ext and dJ/d(wz2) against the oracle's reverse sweep, with
+    recomputed segments and with the trajectory kept; the state gradients are
+    unchanged by the option."""
+    w = _small()
+    n_steps, weights = 6, (1.0, 1.0, 1.0)
+    sim = Simulation.from_workload(w, wz2=wz2, B=B, options=FIXED | PARAMS)
+    sim.adjoint_forward(n_steps, weights, checkpoint_every=every)
+    gx, gv = sim.adjoint_backward()
+    gp = np.asarray(sim.adjoint_param_gradient())
+    sim.close()
+    g = po.Grid(w.n, w.L)
+    p = po.Params(dt=w.dt, Q=w.Q, q_over_m=w.q_over_m, wz2=wz2, B=B)
+    _, gxo, gvo, gBo, gwo = po.run_with_gradient(w.x, w.v, g, p, n_steps, weights,
+                                                 param_grad=True)
+    assert np.max(np.abs(gx - gxo)) <= 1e-4 * np.max(np.abs(gxo))
+    assert np.max(np.abs(gv - gvo)) <= 1e-4 * np.max(np.abs(gvo))
+    ref = np.append(gBo, gwo)
+    assert np.max(np.abs(gp - ref)) <= 1e-4 * np.max(np.abs(ref)), (gp, ref)
+
+
+def test_penning_parameter_gradient_against_central_differences_of_the_oracle():
+    """A Penning bunch through 10 Boris steps: dJ/dB_z and dJ/d(wz2) from the
+    GPU against central differences of the oracle's J in B_z and wz2."""
+    w = pi.penning(n=16, n_particles=4096, L=20.0, seed=9)
+    n_steps, weights = 10, (1.0, 1.0, 1.0)
+    sim = Simulation.from_workload(w, options=FIXED | PARAMS)
+    sim.adjoint_forward(n_steps, weights, checkpoint_every=4)
+    sim.adjoint_backward()
+    gp = sim.adjoint_param_gradient()
+    sim.close()
+    g = po.Grid(w.n, w.L)
+    eps = 1e-5
+
+    def J(B, wz2):
+        p = po.Params(dt=w.dt, Q=w.Q, q_over_m=w.q_over_m, B=B, wz2=wz2)
+        return po.run_with_gradient(w.x, w.v, g, p, n_steps, weights)[0]
+
+    Bz = w.B[2]
+    fd_b = (J((w.B[0], w.B[1], Bz + eps), w.wz2) - J((w.B[0], w.B[1], Bz - eps), w.wz2)) / (2 * eps)
+    fd_w = (J(w.B, w.wz2 + eps) - J(w.B, w.wz2 - eps)) / (2 * eps)
+    assert gp[2] == pytest.approx(fd_b, rel=1e-3)
+    assert gp[3] == pytest.approx(fd_w, rel=1e-3)
+
+
+def test_parameter_gradient_needs_the_option_and_a_backward_pass():
+    w = _small()
+    sim = Simulation.from_workload(w, wz2=0.3, options=FIXED)
+    sim.adjoint_forward(3, (1.0, 1.0, 1.0))
+    sim.adjoint_backward()
+    with pytest.raises(capi.PicError):
+        sim.adjoint_param_gradient()
+    sim.close()
+    sim = Simulation.from_workload(w, wz2=0.3, options=FIXED | PARAMS)
+    with pytest.raises(capi.PicError):
+        sim.adjoint_param_gradient()
+    sim.adjoint_forward(3, (1.0, 1.0, 1.0))
+    with pytest.raises(capi.PicError):
+        sim.adjoint_param_gradient()
+    sim.adjoint_backward()
+    assert np.all(np.isfinite(sim.adjoint_param_gradient()))
+    sim.close()
