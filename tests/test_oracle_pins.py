@@ -231,27 +231,28 @@ def test_dispersion_root_for_landau_k_half():
 
 @pytest.mark.slow
 def test_landau_damping_rate_and_frequency():
-    """Weak Landau damping, k = 0.5, alpha = 0.05 (Section 4.1): the x mode of
-    E_x oscillates at Re(w) and decays at Im(w) of the kinetic dispersion
-    relation.  Quiet 1D lattice start on a 32 x 1 x 1 grid, t in [0, 10]."""
-    from scipy.optimize import curve_fit
+    """Weak Landau damping, k = 0.5 (Section 4.1, Eq. landau_f): the x mode
+    of E_x oscillates at Re(w) and decays at Im(w) of the kinetic dispersion
+    relation.  Quiet 1D lattice start (32 cells, 128 x 1024 particles) at
+    alpha = 0.01, small enough that the linear rate holds; the least damped
+    root is separated from the ballistic transient and the heavier roots by
+    a six-exponential matrix pencil on t in [4, 14].  The grid's CIC
+    smoothing alone moves the root by 0.7% at this resolution."""
+    from tests.fits import pencil
 
-    w = pi.landau_lattice_1d(nx=32, mx=32, mv=2048, n_steps=200)
+    w = pi.landau_lattice_1d(nx=32, mx=128, mv=1024, alpha=0.01, n_steps=300)
     grid = po.Grid(w.n, w.L)
     p = po.Params(dt=w.dt, Q=w.Q, q_over_m=w.q_over_m)
     _, _, hist = po.run(w.x, w.v, grid, p, w.n_steps)
     t = np.array([d["t_field"] for d in hist])
     c = np.array([d["mode"] for d in hist])
-    sig = (c * np.exp(-1j * np.angle(c[0]))).real
-
-    def model(tt, A, g, om, ph):
-        return A * np.exp(g * tt) * np.cos(om * tt + ph)
-
-    sel = t > 2.0
-    popt, _ = curve_fit(model, t[sel], sig[sel], p0=[sig[0], -0.15, 1.4, 0.0])
     root = dispersion.root(0.5, 1.4 - 0.15j)
-    assert popt[1] == pytest.approx(root.imag, rel=0.05)
-    assert popt[2] == pytest.approx(root.real, rel=0.01)
+    sel = (t >= 4.0) & (t <= 14.0)
+    s, a = pencil(c[sel], t[1] - t[0], 6)
+    near = [i for i in range(len(s)) if abs(abs(s[i].imag) - root.real) < 0.1]
+    i = max(near, key=lambda j: abs(a[j]))
+    assert s[i].real == pytest.approx(root.imag, rel=0.02)
+    assert abs(s[i].imag) == pytest.approx(root.real, rel=0.005)
     # charge is exact and the lattice start has zero net momentum
     assert hist[-1]["Q"] == pytest.approx(w.Q, rel=1e-13)
     assert abs(hist[-1]["Px"]) < 1e-9 * abs(w.Q)
@@ -336,6 +337,108 @@ def test_diagnostics_field_energy_of_a_known_field():
     assert d["Wy"] == pytest.approx(9.0 * 8.0, rel=1e-14)
     assert d["Wx"] == 0.0 and d["Wz"] == 0.0
     assert d["Q"] == pytest.approx(8.0, rel=1e-14)
+
+
+def test_diagnostics_momentum_and_kinetic_energy_of_two_particles():
+    """Two electrons of a species with Q_e = -3 and q/m = -2 (Section 3.2:
+    q_p = -1.5, m_p = q_p / (q/m) = 0.75) moving at (1, 2, 3) and (-3, 0, 1):
+    the total momentum is (-1.5, 1.5, 3) and the kinetic energy 9, worked
+    out by hand."""
+    grid = po.Grid((4, 4, 4), (2.0, 2.0, 2.0))
+    v = np.array([[1.0, 2.0, 3.0], [-3.0, 0.0, 1.0]])
+    E = np.zeros((3,) + grid.shape)
+    d = po.diagnostics(np.zeros(grid.shape), E, v, grid, po.Params(dt=0.1, Q=-3.0, q_over_m=-2.0), 2)
+    assert (d["Px"], d["Py"], d["Pz"]) == pytest.approx((-1.5, 1.5, 3.0), rel=1e-15)
+    assert d["K"] == pytest.approx(9.0, rel=1e-15)
+
+
+def _work_and_impulse_residuals(n_steps=6):
+    """Run a strongly driven Penning-like bunch (self field, quadrupole and
+    B) and return the largest residuals of the work-energy theorem
+    K_{n+1} - K_n = sum_p q_p e_p . (x_{n+1} - x_n) and of the Lorentz
+    impulse P_{n+1} - P_n = sum_p q_p (dt e_p + (x_{n+1} - x_n) x B),
+    relative to |K| and |P| scales.  Both hold exactly for the synchronised
+    Boris step: the rotation does no work and v_{n+1} - v_n solves
+    v1 = v0 + dt (q/m) [e + (v0 + v1)/2 x B] (Eq. momentum_eqn), while the
+    drift-kick-drift positions move by dt (v_n + v_{n+1}) / 2.  The field e_p
+    is the gathered self field plus the quadrupole at the half-step
+    position; displacements come from the positions alone (minimum image)."""
+    w = pi.landau(n=8, ppc=4, seed=11, alpha=0.4)
+    grid = po.Grid(w.n, w.L)
+    B = np.array([0.3, -0.2, 2.0])
+    p = po.Params(dt=0.1, Q=w.Q, q_over_m=-1.7, B=tuple(B), wz2=0.8)
+    L = np.asarray(w.L)
+    N = w.x.shape[0]
+    qp = p.Q / N
+    x, v = w.x.copy(), w.v.copy()
+    prev = None
+    res_k = res_p = 0.0
+    for _ in range(n_steps):
+        xh = po.wrap(x + 0.5 * p.dt * v, grid)
+        e = po.gather(xh, po.solve_field(po.deposit(xh, grid, qp), grid), grid)
+        e = e + po.external_field(xh, grid, p.wz2)
+        x1, v1, d = po.step(x, v, grid, p, with_diag=True)
+        dx = x1 - x
+        dx -= L * np.round(dx / L)
+        if prev is not None:
+            work = qp * float(np.sum(e * dx))
+            impulse = qp * (p.dt * e.sum(axis=0) + np.cross(dx, B).sum(axis=0))
+            dK = d["K"] - prev["K"]
+            dP = np.array([d["Px"] - prev["Px"], d["Py"] - prev["Py"], d["Pz"] - prev["Pz"]])
+            res_k = max(res_k, abs(dK - work) / abs(work))
+            res_p = max(res_p, float(np.max(np.abs(dP - impulse))) / float(np.max(np.abs(impulse))))
+        prev = d
+        x, v = x1, v1
+    return res_k, res_p
+
+
+def test_kinetic_energy_and_momentum_follow_work_and_impulse():
+    """K and P of the diagnostics change by exactly the work and the impulse
+    of the fields on the particles (see _work_and_impulse_residuals): this
+    fixes the 1/2 of K, m_p = q_p / (q/m) with its sign and the sums over
+    particles independently of how the diagnostics are written."""
+    res_k, res_p = _work_and_impulse_residuals()
+    assert res_k < 1e-9
+    assert res_p < 1e-9
+
+
+@pytest.mark.parametrize("mistake", ["K without 1/2", "m_p with the wrong sign", "P without m_p"])
+def test_work_and_impulse_pins_catch_planted_mistakes(monkeypatch, mistake):
+    """The pin above fails for each plausible slip in the oracle's K and P."""
+    good = po.diagnostics
+
+    def planted(rho, E, v_new, grid, params, n_particles, mode=(1, 0, 0), mode_comp=0):
+        d = good(rho, E, v_new, grid, params, n_particles, mode, mode_comp)
+        mp = params.Q / n_particles / params.q_over_m
+        if mistake == "K without 1/2":
+            d["K"] *= 2.0
+        elif mistake == "m_p with the wrong sign":
+            d["K"], d["Px"], d["Py"], d["Pz"] = -d["K"], -d["Px"], -d["Py"], -d["Pz"]
+        else:
+            d["Px"], d["Py"], d["Pz"] = d["Px"] / mp, d["Py"] / mp, d["Pz"] / mp
+        return d
+
+    monkeypatch.setattr(po, "diagnostics", planted)
+    res_k, res_p = _work_and_impulse_residuals(n_steps=3)
+    assert max(res_k, res_p) > 0.5
+
+
+def test_momentum_is_conserved_by_the_self_field():
+    """With B = E_ext = 0 only the self field acts, whose forces sum to zero
+    (CIC deposit and gather are transposes, the spectral gradient is odd), so
+    P stays at its nonzero initial value to rounding over 20 steps."""
+    w = pi.landau(n=8, ppc=8, seed=21, alpha=0.3)
+    grid = po.Grid(w.n, w.L)
+    p = po.Params(dt=0.1, Q=w.Q)
+    v0 = w.v + np.array([0.3, -0.2, 0.1])
+    mp = (w.Q / w.x.shape[0]) / p.q_over_m
+    P0 = mp * v0.sum(axis=0)
+    _, _, hist = po.run(w.x, v0, grid, p, 20)
+    scale = abs(mp) * float(np.sum(np.abs(v0)))
+    for d in hist:
+        P = np.array([d["Px"], d["Py"], d["Pz"]])
+        assert np.max(np.abs(P - P0)) < 1e-12 * scale
+    assert np.max(np.abs(P0)) > 1e-3 * scale
 
 
 @pytest.mark.parametrize("Bz", [0.0, 5.0])
