@@ -50,6 +50,9 @@ def parse():
                     help="steps between re-binnings (default 4; 2 for the Penning bunch, whose "
                          "particles cross cells faster on its 256^3 mesh)")
     ap.add_argument("--options", type=int, default=LAUNCH["options"])
+    ap.add_argument("--stray-rebin", type=float, default=0.0,
+                    help="re-bin on the device when the last push left more than this fraction "
+                         "of the particles outside their tile's guard (0: period only)")
     ap.add_argument("--diag-every", type=int, default=1)
     ap.add_argument("--dt", type=float, default=0.05,
                     help="time step (0.05: the Landau benchmark; the paper's scaling runs use "
@@ -465,7 +468,8 @@ def main():
     N = w.n_particles
     ng = args.grid ** 3
     sim = Simulation.from_workload(w, sort_period=args.sort_period, options=options,
-                                   diag_every=args.diag_every, guard=args.guard, seed=2022 + rank)
+                                   diag_every=args.diag_every, guard=args.guard, seed=2022 + rank,
+                                   stray_rebin=args.stray_rebin)
     stream = sim.stream
 
     def barrier():

@@ -91,6 +91,13 @@ typedef struct {
                               (default 4095)                                     */
     int32_t options;       /* PIC_OPT_* bits (default 0)                         */
     uint64_t seed;         /* random stream of PIC_OPT_UNIFORM_MOVE              */
+    double  stray_rebin;   /* stray-triggered re-binning in pic_step (default 0 =
+                              off): > 0 makes the device decide before every
+                              step whether to re-bin, doing so when the last
+                              push left more than stray_rebin x n_particles
+                              particles outside their tile's guard (any small
+                              positive value re-bins on the first stray), or
+                              when sort_period (> 0) pushes have passed       */
 } pic_params_t;
 
 /* options: accumulate the deposit in 2^-20 fixed point (u32 shared-memory
@@ -232,8 +239,22 @@ int pic_gather_push(pic_handle_t h);
 /* n full steps: [re-bin when due] deposit, solve, gather+push, and the FP64
  * diagnostic reductions every diag_every steps.  Only kernel launches, cuFFT
  * executions and memsets are enqueued (no host synchronisation), so the
- * sequence can be captured in a CUDA graph by the caller. */
+ * sequence can be captured in a CUDA graph by the caller.
+ * Re-binning is due every sort_period steps, counted on the host; with
+ * params.stray_rebin > 0 the decision is taken on the device instead, before
+ * each step, from the stray count of the previous push and the pushes since
+ * the last re-binning: the sort kernels are launched every step and return at
+ * once unless a re-binning is due, so a captured graph re-bins exactly when
+ * the run needs it. */
 int pic_step(pic_handle_t h, int n);
+
+/* Re-binning statistics since the last load (synchronising): re-binnings
+ * performed (the load's own binning included), and the "strays": particles
+ * deposited outside their tile's guard by the pushes since the last
+ * re-binning (with stray_rebin on: by the last push alone, as each decision
+ * clears the count).  Either pointer may be NULL.  (Not in the paper: the
+ * binning is this library's.) */
+int pic_rebin_stats(pic_handle_t h, int64_t *rebins, int64_t *strays);
 
 /* ------------------------------------------------------------ diagnostics */
 

@@ -49,7 +49,8 @@ class pic_params_t(C.Structure):
                 ("tile", C.c_int32 * 3), ("guard", C.c_int32), ("sort_period", C.c_int32),
                 ("diag_every", C.c_int32), ("diag_capacity", C.c_int32),
                 ("mode", C.c_int32 * 3), ("mode_comp", C.c_int32), ("block", C.c_int32),
-                ("chunk", C.c_int32), ("options", C.c_int32), ("seed", C.c_uint64)]
+                ("chunk", C.c_int32), ("options", C.c_int32), ("seed", C.c_uint64),
+                ("stray_rebin", C.c_double)]
 
 
 PIC_OPT_FIXED_DEPOSIT = 1
@@ -92,6 +93,7 @@ _SIGNATURES = {
     "pic_get_field": (C.c_int, [pic_handle_t, C.c_void_p, C.c_void_p, C.c_int]),
     "pic_set_rho": (C.c_int, [pic_handle_t, C.c_void_p, C.c_int]),
     "pic_get_counts": (C.c_int, [pic_handle_t, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "pic_rebin_stats": (C.c_int, [pic_handle_t, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "pic_sort": (C.c_int, [pic_handle_t]),
     "pic_deposit": (C.c_int, [pic_handle_t]),
     "pic_field_solve": (C.c_int, [pic_handle_t]),
@@ -232,6 +234,13 @@ def pic_get_counts(h):
     n, s = C.c_int64(), C.c_int64()
     check(_call("pic_get_counts", h, C.byref(n), C.byref(s)), "pic_get_counts")
     return n.value, s.value
+
+
+def pic_rebin_stats(h):
+    """(re-binnings since the load, strays since the last re-binning decision)."""
+    r, s = C.c_int64(), C.c_int64()
+    check(_call("pic_rebin_stats", h, C.byref(r), C.byref(s)), "pic_rebin_stats")
+    return int(r.value), int(s.value)
 
 
 def pic_sort(h) -> None:

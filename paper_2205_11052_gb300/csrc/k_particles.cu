@@ -20,6 +20,18 @@ namespace {
 
 __device__ __forceinline__ void raise_flag(Ctrl *ctrl, int bit) { atomicOr(&ctrl->flags, bit); }
 
+// Velocity moments (sum v, sum |v|^2) are summed per thread in FP32 over a
+// few particles (one work item's share, or one loop iteration) and then
+// added to the thread's FP64 totals, so no FP32 sum runs over more than a
+// few dozen terms.
+__device__ __forceinline__ void fold_moments(float (&a)[4], double (&d)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        d[q] += (double)a[q];
+        a[q] = 0.f;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // load: FP64 (x_0, v_0) -> x_{1/2} = x_0 + dt/2 v_0 -> (cell, offset, v)
 // ---------------------------------------------------------------------------
@@ -169,6 +181,7 @@ __global__ void __launch_bounds__(256, 3) k_gather_push(int64_t n, Geom g, PushC
                                                       double *__restrict__ part) {
     const ParticleSet ps = ctrl->sets[ctrl->cur];
     float a_vx = 0.f, a_vy = 0.f, a_vz = 0.f, a_v2 = 0.f;
+    double d_v[4] = {0.0, 0.0, 0.0, 0.0};
     int bad = 0;
     const int64_t ngroups = n >> 2;                      // full groups of 4
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -197,6 +210,11 @@ __global__ void __launch_bounds__(256, 3) k_gather_push(int64_t n, Geom g, PushC
             a_vz += (uz.x + uz.y) + (uz.z + uz.w);
             a_v2 += (ux.x * ux.x + uy.x * uy.x + uz.x * uz.x) + (ux.y * ux.y + uy.y * uy.y + uz.y * uz.y) +
                     (ux.z * ux.z + uy.z * uy.z + uz.z * uz.z) + (ux.w * ux.w + uy.w * uy.w + uz.w * uz.w);
+            d_v[0] += (double)a_vx;
+            d_v[1] += (double)a_vy;
+            d_v[2] += (double)a_vz;
+            d_v[3] += (double)a_v2;
+            a_vx = a_vy = a_vz = a_v2 = 0.f;
         }
     }
     // the n mod 4 particles after the last full group: first threads of block 0
@@ -222,9 +240,9 @@ __global__ void __launch_bounds__(256, 3) k_gather_push(int64_t n, Geom g, PushC
     }
     if (bad) raise_flag(ctrl, bad);
     if (DIAG) {
-        // per-thread FP32 partials (a few particles each) -> FP64 block sum in
-        // a fixed order -> one partial per block (deterministic)
-        double d[4] = {(double)a_vx, (double)a_vy, (double)a_vz, (double)a_v2};
+        // per-thread FP64 totals -> FP64 block sum in a fixed order -> one
+        // partial per block (deterministic)
+        double d[4] = {d_v[0] + a_vx, d_v[1] + a_vy, d_v[2] + a_vz, d_v[3] + a_v2};
         __shared__ double red[4][8];
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         for (int q = 0; q < 4; ++q) {
@@ -240,7 +258,10 @@ __global__ void __launch_bounds__(256, 3) k_gather_push(int64_t n, Geom g, PushC
             part[4 * blockIdx.x + threadIdx.x] = t;
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->step += 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->step += 1;
+        ctrl->since_sort += 1;
+    }
 }
 
 
@@ -278,7 +299,7 @@ __device__ __forceinline__ void pd_one(const Geom &g, const PushConst &pc, const
 }
 
 template <bool DIAG, bool EXT, bool MAG, bool FIXED>
-__global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g, PushConst pc, Ctrl *ctrl,
+__global__ void __launch_bounds__(PIC_PD_THREADS, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g, PushConst pc, Ctrl *ctrl,
                                                           const int4 *__restrict__ items,
                                                           const float4 *__restrict__ E8,
                                                           float *rho, unsigned long long *rho64,
@@ -289,6 +310,7 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g,
     const ParticleSet ps = ctrl->sets[ctrl->cur];
     const int n_items = ctrl->n_items;
     float a[4] = {0.f, 0.f, 0.f, 0.f};
+    double dm[4] = {0.0, 0.0, 0.0, 0.0};
     int bad = 0;
     unsigned long long strays = 0;
     // a contiguous run of work items per block (consecutive items share tiles)
@@ -313,11 +335,25 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g,
             cur_tile = item.x;
             tc = t;
         }
-        // one particle per thread and iteration (coalesced 4-byte streams)
-        for (int p = item.y + threadIdx.x; p < item.z; p += blockDim.x) {
-            int32_t c = __ldcs(ps.cell + p);
-            float fx = __ldcs(ps.o[0] + p), fy = __ldcs(ps.o[1] + p), fz = __ldcs(ps.o[2] + p);
-            float vx = __ldcs(ps.v[0] + p), vy = __ldcs(ps.v[1] + p), vz = __ldcs(ps.v[2] + p);
+        // one particle per thread and iteration (coalesced 4-byte streams);
+        // the next iteration's particle is loaded before this one is pushed
+        int p = item.y + threadIdx.x;
+        int32_t nc = 0;
+        float nfx = 0.f, nfy = 0.f, nfz = 0.f, nvx = 0.f, nvy = 0.f, nvz = 0.f;
+        if (p < item.z) {
+            nc = __ldcs(ps.cell + p);
+            nfx = __ldcs(ps.o[0] + p); nfy = __ldcs(ps.o[1] + p); nfz = __ldcs(ps.o[2] + p);
+            nvx = __ldcs(ps.v[0] + p); nvy = __ldcs(ps.v[1] + p); nvz = __ldcs(ps.v[2] + p);
+        }
+        for (; p < item.z; p += blockDim.x) {
+            int32_t c = nc;
+            float fx = nfx, fy = nfy, fz = nfz, vx = nvx, vy = nvy, vz = nvz;
+            const int pn = p + (int)blockDim.x;
+            if (pn < item.z) {
+                nc = __ldcs(ps.cell + pn);
+                nfx = __ldcs(ps.o[0] + pn); nfy = __ldcs(ps.o[1] + pn); nfz = __ldcs(ps.o[2] + pn);
+                nvx = __ldcs(ps.v[0] + pn); nvy = __ldcs(ps.v[1] + pn); nvz = __ldcs(ps.v[2] + pn);
+            }
             if (save.cell) {
                 __stcs(save.cell + p, c);
                 __stcs(save.o[0] + p, fx);
@@ -339,6 +375,7 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g,
             __stcs(ps.v[1] + p, vy);
             __stcs(ps.v[2] + p, vz);
         }
+        if (DIAG) fold_moments(a, dm);
         if (!sparse) {
             __syncthreads();
             cic::tile_fold<FIXED>(acc, sum, S);
@@ -347,10 +384,13 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g,
     }
     if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, tc, g, rho, rho64, qscale);
     if (bad) raise_flag(ctrl, bad);
-    if (strays) atomicAdd(&ctrl->stray, strays);
+    if (strays) {
+        atomicAdd(&ctrl->stray, strays);
+        atomicAdd(&ctrl->stray_step, strays);
+    }
     if (DIAG) {
-        double d[4] = {(double)a[0], (double)a[1], (double)a[2], (double)a[3]};
-        __shared__ double red[4][8];
+        const double *d = dm;
+        __shared__ double red[4][PIC_PD_THREADS / 32];
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         for (int q = 0; q < 4; ++q) {
             double tt = d[q];
@@ -364,8 +404,12 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g,
             part[4 * blockIdx.x + threadIdx.x] = tt;
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->step += 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->step += 1;
+        ctrl->since_sort += 1;
+    }
 }
+
 
 }  // namespace
 
@@ -488,9 +532,8 @@ __device__ __forceinline__ void move_one(const Geom &g, uint64_t seed, long long
 }
 
 template <bool DIAG>
-__device__ __forceinline__ void block_moments(const float (&a)[4], double *part) {
+__device__ __forceinline__ void block_moments(const double (&d)[4], double *part) {
     if (!DIAG) return;
-    double d[4] = {(double)a[0], (double)a[1], (double)a[2], (double)a[3]};
     __shared__ double red[4][8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int q = 0; q < 4; ++q) {
@@ -509,7 +552,7 @@ __device__ __forceinline__ void block_moments(const float (&a)[4], double *part)
 // the random move of every particle with the deposit of the new positions
 // (the work items and shared tiles of k_push_deposit); velocities untouched
 template <bool DIAG, bool FIXED>
-__global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_move_deposit(
+__global__ void __launch_bounds__(256, PIC_MV_MIN_BLOCKS) k_move_deposit(
     Geom g, uint64_t seed, Ctrl *ctrl, const int4 *__restrict__ items, float *rho,
     unsigned long long *rho64, float qscale, int sparse_below, double *__restrict__ part) {
     extern __shared__ __align__(16) uint32_t acc[];
@@ -517,6 +560,7 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_move_deposit(
     const int n_items = ctrl->n_items;
     const long long n = ctrl->step;   // advanced after this kernel (k_step_inc)
     float a[4] = {0.f, 0.f, 0.f, 0.f};
+    double dm[4] = {0.0, 0.0, 0.0, 0.0};
     int bad = 0;
     unsigned long long strays = 0;
     int it0, it1;
@@ -564,6 +608,7 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_move_deposit(
             __stcs(ps.o[1] + p, fy);
             __stcs(ps.o[2] + p, fz);
         }
+        if (DIAG) fold_moments(a, dm);
         if (!sparse) {
             __syncthreads();
             cic::tile_fold<FIXED>(acc, sum, S);
@@ -572,8 +617,11 @@ __global__ void __launch_bounds__(256, PIC_PD_MIN_BLOCKS) k_move_deposit(
     }
     if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, tc, g, rho, rho64, qscale);
     if (bad) raise_flag(ctrl, bad);
-    if (strays) atomicAdd(&ctrl->stray, strays);
-    block_moments<DIAG>(a, part);
+    if (strays) {
+        atomicAdd(&ctrl->stray, strays);
+        atomicAdd(&ctrl->stray_step, strays);
+    }
+    block_moments<DIAG>(dm, part);
 }
 
 // the random move alone (split calls: pic_gather_push)
@@ -583,6 +631,7 @@ __global__ void __launch_bounds__(256) k_move(int64_t np, Geom g, uint64_t seed,
     const ParticleSet ps = ctrl->sets[ctrl->cur];
     const long long n = ctrl->step;
     float a[4] = {0.f, 0.f, 0.f, 0.f};
+    double dm[4] = {0.0, 0.0, 0.0, 0.0};
     int bad = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += stride) {
@@ -599,13 +648,17 @@ __global__ void __launch_bounds__(256) k_move(int64_t np, Geom g, uint64_t seed,
             a[1] += vy;
             a[2] += vz;
             a[3] += vx * vx + vy * vy + vz * vz;
+            fold_moments(a, dm);
         }
     }
     if (bad) raise_flag(ctrl, bad);
-    block_moments<DIAG>(a, part);
+    block_moments<DIAG>(dm, part);
 }
 
-__global__ void k_step_inc(Ctrl *ctrl) { ctrl->step += 1; }
+__global__ void k_step_inc(Ctrl *ctrl) {
+    ctrl->step += 1;
+    ctrl->since_sort += 1;
+}
 
 cudaError_t launch_move(int64_t np, const Geom &g, uint64_t seed, bool diag, bool fixed, bool deposit,
                         Ctrl *ctrl, const int4 *items, int max_items, float *rho,
@@ -613,7 +666,7 @@ cudaError_t launch_move(int64_t np, const Geom &g, uint64_t seed, bool diag, boo
                         int blocks, cudaStream_t st) {
     const int nb = std::max(1, std::min(blocks, deposit ? max_items : blocks));
     if (deposit) {
-        const size_t smem = push_deposit_smem(g);
+        const size_t smem = tile_deposit_smem(g);
         const float qs = (float)qscale;
         if (diag) {
             if (fixed) k_move_deposit<true, true><<<nb, 256, smem, st>>>(g, seed, ctrl, items, rho, rho64, qs, sparse_below, part);
@@ -633,16 +686,28 @@ cudaError_t launch_move(int64_t np, const Geom &g, uint64_t seed, bool diag, boo
     return (deposit && fixed) ? launch_rho_finish(g, rho64, rho, qscale, st) : cudaSuccess;
 }
 
-size_t push_deposit_smem(const Geom &g) {
+// item tile + the block's tile sums
+size_t tile_deposit_smem(const Geom &g) {
     const cic::Tile t0 = cic::tile_of(g, 0);
-    return cic::sum_offset(t0.S) + 8 * (size_t)t0.S;   // item tile + the block's tile sums
+    return cic::sum_offset(t0.S) + 8 * (size_t)t0.S;
 }
+size_t push_deposit_smem(const Geom &g) { return tile_deposit_smem(g); }
 
-// Allow the fused kernel's shared memory (call outside any stream capture)
+// Allow the fused kernels' shared memory (call outside any stream capture)
 cudaError_t push_deposit_prepare(const Geom &g) {
+    cudaError_t e = cudaSuccess;
+    const size_t tsm = tile_deposit_smem(g);
+    if (tsm > 48 * 1024) {
+#define PIC_MVA(D, F)                                                                          \
+        if ((e = cudaFuncSetAttribute(k_move_deposit<D, F>,                                     \
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)) != \
+            cudaSuccess)                                                                        \
+            return e
+        PIC_MVA(false, false); PIC_MVA(false, true); PIC_MVA(true, false); PIC_MVA(true, true);
+#undef PIC_MVA
+    }
     const size_t smem = push_deposit_smem(g);
     if (smem <= 48 * 1024) return cudaSuccess;
-    cudaError_t e = cudaSuccess;
 #define PIC_PDA(D, X, M, F)                                                                   \
     if ((e = cudaFuncSetAttribute(k_push_deposit<D, X, M, F>,                                 \
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != \
@@ -672,8 +737,9 @@ cudaError_t launch_push_deposit(const Geom &g, const PushConst &pc, bool diag, b
     const float qs = (float)qscale;
     cudaError_t e = cudaSuccess;
 #define PIC_PD(D, X, M, F)                                                                      \
-    k_push_deposit<D, X, M, F><<<nb, 256, smem, st>>>(g, pc, ctrl, items, E8, rho, rho64, qs,   \
-                                                      sparse_below, part, save)
+    k_push_deposit<D, X, M, F><<<nb, PIC_PD_THREADS, smem, st>>>(g, pc, ctrl, items, E8, rho,    \
+                                                                 rho64, qs, sparse_below, part, \
+                                                                 save)
 #define PIC_PD_F(D, X, M) \
     do { if (fixed) PIC_PD(D, X, M, true); else PIC_PD(D, X, M, false); } while (0)
     if (diag) {

@@ -77,7 +77,9 @@ __device__ __forceinline__ int block_exclusive_scan(int val, int *total) {
     return r;
 }
 
-__global__ void k_scan_reduce(const int32_t *__restrict__ data, int64_t n, int32_t *sums) {
+__global__ void k_scan_reduce(const int32_t *__restrict__ data, int64_t n, int32_t *sums,
+                              const int32_t *gate) {
+    if (gate && !*gate) return;
     const int64_t seg0 = (int64_t)blockIdx.x * kScanSeg;
     int s = 0;
     for (int q = 0; q < kScanItems; ++q) {
@@ -96,7 +98,8 @@ __global__ void k_scan_reduce(const int32_t *__restrict__ data, int64_t n, int32
 }
 
 // single block: exclusive scan of the nb block sums, total to sums[nb]
-__global__ void k_scan_top(int32_t *sums, int nb) {
+__global__ void k_scan_top(int32_t *sums, int nb, const int32_t *gate) {
+    if (gate && !*gate) return;
     __shared__ int tot;
     int carry = 0;
     for (int base = 0; base < nb; base += kScanThreads) {
@@ -111,7 +114,9 @@ __global__ void k_scan_top(int32_t *sums, int nb) {
     if (threadIdx.x == 0) sums[nb] = carry;
 }
 
-__global__ void k_scan_apply(int32_t *data, int64_t n, const int32_t *sums, int nb) {
+__global__ void k_scan_apply(int32_t *data, int64_t n, const int32_t *sums, int nb,
+                             const int32_t *gate) {
+    if (gate && !*gate) return;
     __shared__ int tot;
     const int64_t seg0 = (int64_t)blockIdx.x * kScanSeg;
     const int64_t t0 = seg0 + (int64_t)threadIdx.x * kScanItems;   // contiguous per thread
@@ -131,21 +136,23 @@ __global__ void k_scan_apply(int32_t *data, int64_t n, const int32_t *sums, int 
     if (blockIdx.x == 0 && threadIdx.x == 0) data[n] = sums[nb];
 }
 
-cudaError_t exclusive_scan_impl(int32_t *data, int64_t n, int32_t *tmp, cudaStream_t st) {
+cudaError_t exclusive_scan_impl(int32_t *data, int64_t n, int32_t *tmp, cudaStream_t st,
+                                const int32_t *gate = nullptr) {
     const int nb = (int)((n + kScanSeg - 1) / kScanSeg);
     if (nb == 0) {
         return cudaMemsetAsync(data, 0, sizeof(int32_t), st);
     }
-    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(data, n, tmp);
-    k_scan_top<<<1, kScanThreads, 0, st>>>(tmp, nb);
-    k_scan_apply<<<nb, kScanThreads, 0, st>>>(data, n, tmp, nb);
+    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(data, n, tmp, gate);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(tmp, nb, gate);
+    k_scan_apply<<<nb, kScanThreads, 0, st>>>(data, n, tmp, nb, gate);
     return cudaGetLastError();
 }
 
 // ---- work list ----------------------------------------------------------------
 
 __global__ void k_tile_ranges(const int32_t *__restrict__ bin_end, int ntiles, int chunk,
-                              int32_t *tile_items, int2 *tile_range) {
+                              int32_t *tile_items, int2 *tile_range, const int32_t *gate) {
+    if (gate && !*gate) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
     const int s = (t == 0) ? 0 : bin_end[t - 1];
@@ -156,11 +163,16 @@ __global__ void k_tile_ranges(const int32_t *__restrict__ bin_end, int ntiles, i
 
 __global__ void k_fill_items(int ntiles, int chunk, const int32_t *__restrict__ item_off,
                              const int2 *__restrict__ tile_range, int4 *items, Ctrl *ctrl,
-                             int flip) {
+                             int flip, const int32_t *gate) {
+    if (gate && !*gate) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {
         ctrl->n_items = item_off[ntiles];
         if (flip) ctrl->cur = 1 - ctrl->cur;    // particles now live in the other set
+        // a re-binning: every particle is back inside its tile
+        ctrl->rebins += 1;
+        ctrl->since_sort = 0;
+        ctrl->stray_step = 0ull;
     }
     if (t >= ntiles) return;
     const int2 r = tile_range[t];
@@ -174,8 +186,23 @@ __global__ void k_flip(Ctrl *ctrl) { ctrl->cur = 1 - ctrl->cur; }
 
 }  // namespace
 
-cudaError_t exclusive_scan(int32_t *data, int64_t n, int32_t *tmp, cudaStream_t st) {
-    return exclusive_scan_impl(data, n, tmp, st);
+cudaError_t exclusive_scan(int32_t *data, int64_t n, int32_t *tmp, cudaStream_t st,
+                           const int32_t *gate) {
+    return exclusive_scan_impl(data, n, tmp, st, gate);
+}
+
+namespace {
+__global__ void k_rebin_decide(Ctrl *ctrl, long long max_strays, int period) {
+    const bool due = (period > 0 && ctrl->since_sort >= period) ||
+                     ctrl->stray_step > (unsigned long long)max_strays;
+    ctrl->rebin = due ? 1 : 0;
+    ctrl->stray_step = 0ull;
+}
+}  // namespace
+
+cudaError_t launch_rebin_decide(Ctrl *ctrl, long long max_strays, int period, cudaStream_t st) {
+    k_rebin_decide<<<1, 1, 0, st>>>(ctrl, max_strays < 0 ? 0 : max_strays, period);
+    return cudaGetLastError();
 }
 
 // per-tile ranges from the bin ends left by a scatter, then the work items
@@ -184,11 +211,12 @@ cudaError_t launch_worklist(const int32_t *bin_end, int ntiles, int chunk, int32
                             cudaStream_t st) {
     const int T = 256;
     const int tb = (ntiles + T - 1) / T;
-    k_tile_ranges<<<tb, T, 0, st>>>(bin_end, ntiles, chunk, tile_items, tile_range);
+    k_tile_ranges<<<tb, T, 0, st>>>(bin_end, ntiles, chunk, tile_items, tile_range, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if ((e = exclusive_scan_impl(tile_items, ntiles, scan_tmp, st)) != cudaSuccess) return e;
-    k_fill_items<<<tb, T, 0, st>>>(ntiles, chunk, tile_items, tile_range, items, ctrl, flip);
+    k_fill_items<<<tb, T, 0, st>>>(ntiles, chunk, tile_items, tile_range, items, ctrl, flip,
+                                   nullptr);
     return cudaGetLastError();
 }
 
@@ -199,8 +227,9 @@ cudaError_t sort_prepare() {
 
 // histogram, scan and staged scatter by tile key >> shift (nb keys)
 cudaError_t sort_pass(int64_t n, const Geom &g, int shift, int64_t nb, Ctrl *ctrl, int32_t *bins,
-                      int32_t *scan_tmp, cudaStream_t st, SortRange rg = SortRange{0, 0}) {
-    return staged_pass(n, TileKey{g, shift}, nb, ctrl, bins, scan_tmp, st, rg);
+                      int32_t *scan_tmp, cudaStream_t st, SortRange rg = SortRange{0, 0},
+                      const int32_t *gate = nullptr) {
+    return staged_pass(n, TileKey{g, shift}, nb, ctrl, bins, scan_tmp, st, rg, gate);
 }
 
 // Shifts of the coarse passes that precede the full-key pass for particles in
@@ -233,7 +262,8 @@ int sort_launches(int64_t n, int ntiles, bool presort) {
 
 cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t *bins,
                         int64_t nbins, int32_t *scan_tmp, int32_t *tile_items,
-                        int2 *tile_range, int4 *items, bool presort, cudaStream_t st) {
+                        int2 *tile_range, int4 *items, bool presort, cudaStream_t st,
+                        const int32_t *gate) {
     cudaError_t e;
     if (presort && n > 0) {
         const int nt = g.ntile[0] * g.ntile[1] * g.ntile[2];
@@ -246,15 +276,17 @@ cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }
-    if ((e = sort_pass(n, g, 0, nbins, ctrl, bins, scan_tmp, st)) != cudaSuccess) return e;
+    if ((e = sort_pass(n, g, 0, nbins, ctrl, bins, scan_tmp, st, SortRange{0, 0}, gate)) !=
+        cudaSuccess)
+        return e;
     const int T = 256;
     const int ntiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
     const int tb = (ntiles + T - 1) / T;
-    k_tile_ranges<<<tb, T, 0, st>>>(bins, ntiles, chunk, tile_items, tile_range);
+    k_tile_ranges<<<tb, T, 0, st>>>(bins, ntiles, chunk, tile_items, tile_range, gate);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = exclusive_scan_impl(tile_items, ntiles, scan_tmp, st)) != cudaSuccess) return e;
+    if ((e = exclusive_scan_impl(tile_items, ntiles, scan_tmp, st, gate)) != cudaSuccess) return e;
     k_fill_items<<<tb, T, 0, st>>>(ntiles, chunk, tile_items, tile_range, items, ctrl,
-                                   n > 0 ? 1 : 0);
+                                   n > 0 ? 1 : 0, gate);
     return cudaGetLastError();
 }
 

@@ -316,6 +316,20 @@ int do_sort(pic_ctx *c, bool presort = false) {
     return timer_end(c, PIC_PHASE_SORT, sort_launches(c->np, (int)c->ntiles, presort));
 }
 
+// stray-triggered re-binning: the device decides (from the last push's strays
+// and the pushes since the last re-binning) and the sort kernels follow the gate
+int do_sort_gated(pic_ctx *c) {
+    int r = timer_begin(c, PIC_PHASE_SORT);
+    if (r) return r;
+    const long long max_strays = (long long)floor(c->prm.stray_rebin * (double)c->np);
+    PIC_CUDA(launch_rebin_decide(c->ctrl(), max_strays, c->prm.sort_period, c->st));
+    PIC_CUDA(launch_sort(c->np, c->geom, c->chunk, c->ctrl(), c->at<int32_t>(c->lay.bins),
+                         c->nbins, c->at<int32_t>(c->lay.scan_tmp),
+                         c->at<int32_t>(c->lay.tile_items), c->at<int2>(c->lay.tile_range),
+                         c->at<int4>(c->lay.items), false, c->st, &c->ctrl()->rebin));
+    return timer_end(c, PIC_PHASE_SORT, 1 + sort_launches(c->np, (int)c->ntiles, false));
+}
+
 int do_deposit(pic_ctx *c) {
     // the fixed-point path overwrites every node of rho (and re-zeroes the
     // integer grid); the FP32 path accumulates into a cleared rho
@@ -386,8 +400,8 @@ int do_diag_finalize(pic_ctx *c, int push_blocks) {
 }
 
 int fused_blocks_of(const pic_ctx *c) {
-    return (int)std::max<int64_t>(
-        1, std::min<int64_t>(c->max_items, std::min(kMaxPushBlocks, 152 * PIC_PD_MIN_BLOCKS * 2)));
+    const int per = uniform_move(c) ? PIC_MV_MIN_BLOCKS * 2 : PIC_PD_MIN_BLOCKS * PIC_PD_WAVES;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(c->max_items, std::min(kMaxPushBlocks, 152 * per)));
 }
 
 // gather + push + deposit of the new positions in one kernel (pic_step)
@@ -799,6 +813,8 @@ int pic_create(const pic_grid_t *grid, const pic_species_t *species, const pic_p
         return fail(PIC_ERR_ARG, "chunk must be 0 or in 32..%d", kMaxChunk);
     if (params->options & ~(PIC_OPT_FIXED_DEPOSIT | PIC_OPT_UNIFORM_MOVE | PIC_OPT_ADJOINT_PARAMS))
         return fail(PIC_ERR_ARG, "unknown option bits");
+    if (!isfinite(params->stray_rebin) || params->stray_rebin < 0.0)
+        return fail(PIC_ERR_ARG, "stray_rebin must be finite and >= 0");
 
     pic_ctx *c = new (std::nothrow) pic_ctx();
     if (!c) return fail(PIC_ERR_ARG, "out of host memory");
@@ -835,10 +851,10 @@ int pic_create(const pic_grid_t *grid, const pic_species_t *species, const pic_p
     c->dV = c->h[0] * c->h[1] * c->h[2];
     c->ntiles = nt;
     c->nbins = nt;    // the binning key is the deposit tile
-    if (push_deposit_smem(g) > kMaxSmemPerBlock) {
+    if (tile_deposit_smem(g) > kMaxSmemPerBlock) {
         delete c;
         return fail(PIC_ERR_ARG, "deposit tile plus guard too large for shared memory "
-                                 "(%zu bytes > %d)", push_deposit_smem(g), kMaxSmemPerBlock);
+                                 "(%zu bytes > %d)", tile_deposit_smem(g), kMaxSmemPerBlock);
     }
     if (c->nbins > 2147483647LL - 1) {
         delete c;
@@ -1141,7 +1157,9 @@ int pic_step(pic_handle_t c, int n) {
     // [field diagnostics, before rho is replaced] -> fused gather + push +
     // deposit of the new positions -> [particle diagnostics]
     for (int s = 0; s < n; ++s) {
-        if (c->prm.sort_period > 0 && c->since_sort >= c->prm.sort_period) {
+        if (c->prm.stray_rebin > 0.0 && c->np > 0) {
+            if ((r = do_sort_gated(c))) return r;
+        } else if (c->prm.sort_period > 0 && c->since_sort >= c->prm.sort_period) {
             if ((r = do_sort(c))) return r;
         }
         if (!c->rho_current && (r = do_deposit(c))) return r;
@@ -1174,6 +1192,17 @@ int pic_diagnostics(pic_handle_t c, pic_diag_t *out, int max_records, int *n_out
     }
     if (n_out) *n_out = (int)want;
     if (h.flags) return fail(PIC_ERR_DEVICE_FLAG, "device error flags 0x%x", h.flags);
+    return PIC_OK;
+}
+
+int pic_rebin_stats(pic_handle_t c, int64_t *rebins, int64_t *strays) {
+    int r = check_ready(c);
+    if (r) return r;
+    PIC_CUDA(cudaStreamSynchronize(c->st));
+    Ctrl h;
+    PIC_CUDA(cudaMemcpy(&h, c->ctrl(), sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    if (rebins) *rebins = h.rebins;
+    if (strays) *strays = (int64_t)h.stray_step;
     return PIC_OK;
 }
 

@@ -41,6 +41,14 @@ struct Ctrl {
     // the bits orders them), double-buffered by step parity: |ly|, |lv| of
     // the multipliers and |lrho| of the last adjoint solve
     unsigned int adj_ly[2], adj_lv[2], adj_lrho[2];
+    // stray-triggered re-binning: strays of the last push (summed by the push
+    // kernels, cleared by each re-binning decision and each re-binning), the
+    // pushes since the last re-binning, re-binnings since the load, and the
+    // gate the decision sets for the sort kernels of the current step
+    unsigned long long stray_step;
+    long long rebins;
+    int32_t since_sort;
+    int32_t rebin;
     int32_t cur;            // which ParticleSet holds the particles
     int32_t pad0;
     ParticleSet sets[2];
@@ -93,7 +101,19 @@ constexpr int kMaxPushBlocks = kNumSMs * 8;
 constexpr int kMaxSmemPerBlock = 227 * 1024;   // opt-in shared memory per block
 // resident blocks per SM the fused push + deposit kernel is compiled for
 #ifndef PIC_PD_MIN_BLOCKS
-#define PIC_PD_MIN_BLOCKS 4
+#define PIC_PD_MIN_BLOCKS 3
+#endif
+// threads per block of the fused push + deposit, and its grid in waves of
+// PIC_PD_MIN_BLOCKS blocks per SM
+#ifndef PIC_PD_THREADS
+#define PIC_PD_THREADS 256
+#endif
+#ifndef PIC_PD_WAVES
+#define PIC_PD_WAVES 2
+#endif
+// resident blocks per SM of the uniform-plasma move + deposit
+#ifndef PIC_MV_MIN_BLOCKS
+#define PIC_MV_MIN_BLOCKS 4
 #endif
 // read and write page-locked host particle arrays in place (no staging copies)
 #ifndef PIC_ZERO_COPY
@@ -170,16 +190,23 @@ cudaError_t launch_unload(int64_t o0, int64_t m, const int32_t *inv, const Geom 
                           const double *h_d, const double *L_d, double dt, const Ctrl *ctrl,
                           double *x, double *v, cudaStream_t st);
 
-cudaError_t exclusive_scan(int32_t *data, int64_t n, int32_t *tmp, cudaStream_t st);
+cudaError_t exclusive_scan(int32_t *data, int64_t n, int32_t *tmp, cudaStream_t st,
+                           const int32_t *gate = nullptr);
 cudaError_t sort_prepare();   // kernel attributes; call once per device outside capture
 cudaError_t launch_worklist(const int32_t *bin_end, int ntiles, int chunk, int32_t *tile_items,
                             int2 *tile_range, int4 *items, int32_t *scan_tmp, Ctrl *ctrl, int flip,
                             cudaStream_t st);
 // presort: the particles are in arbitrary order (just loaded); coarse passes
 // by tile key >> shift run first so that no slice overflows the staged table
+// gate != nullptr: every kernel of the sort returns at once unless *gate is
+// nonzero on the device (the stray-triggered re-binning of pic_step)
 cudaError_t launch_sort(int64_t n, const Geom &g, int chunk, Ctrl *ctrl, int32_t *bins,
                         int64_t nbins, int32_t *scan_tmp, int32_t *tile_items,
-                        int2 *tile_range, int4 *items, bool presort, cudaStream_t st);
+                        int2 *tile_range, int4 *items, bool presort, cudaStream_t st,
+                        const int32_t *gate = nullptr);
+// ctrl->rebin = (period > 0 and ctrl->since_sort >= period) or
+// ctrl->stray_step > max_strays; clears ctrl->stray_step
+cudaError_t launch_rebin_decide(Ctrl *ctrl, long long max_strays, int period, cudaStream_t st);
 // kernels launch_sort issues
 int sort_launches(int64_t n, int ntiles, bool presort);
 // coarse passes + full-key pass over particles [o, o + n) of the current set
@@ -206,6 +233,7 @@ cudaError_t launch_move(int64_t np, const Geom &g, uint64_t seed, bool diag, boo
 // dynamic shared memory of the fused push + deposit kernel for geometry g,
 // and the one-time attribute setting it needs above 48 KiB
 size_t push_deposit_smem(const Geom &g);
+size_t tile_deposit_smem(const Geom &g);   // the deposit tiles alone (unstaged kernels)
 cudaError_t push_deposit_prepare(const Geom &g);
 // Optional copy of the positions a push starts from (cell, o[3]), written by
 // the fused kernel as it reads them (the adjoint keeps each step's y).

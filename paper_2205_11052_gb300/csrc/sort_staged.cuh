@@ -10,6 +10,7 @@
 #include <algorithm>
 
 #include "pic_internal.cuh"
+#include "tma.cuh"
 
 namespace pic {
 
@@ -63,50 +64,6 @@ constexpr int kPerThread = kStage / 256;   // the staged kernels run 256 threads
 constexpr int kHistStage = PIC_HIST_STAGE;   // particles per histogram slice
 constexpr int kHistPer = kHistStage / 256;
 
-// ---- bulk asynchronous copies (TMA) into shared memory, mbarrier completion ----
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-// bounded wait for the phase of the given parity; false if it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 22); ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 // Block-staged scatter.  A block takes kStage consecutive particles into
 // shared memory, finds the slice's distinct destination tiles with a small
 // shared hash table (a slice comes from one or two tiles plus strays into
@@ -157,7 +114,9 @@ struct SortRange {
 
 template <class Key>
 __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Key key_param, Ctrl *ctrl,
-                                                         int32_t *bins, SortRange rg) {
+                                                         int32_t *bins, SortRange rg,
+                                                         const int32_t *gate) {
+    if (gate && !*gate) return;
     Key key_of = key_param;   // a per-thread copy (functors may cache lookups)
     extern __shared__ __align__(128) unsigned char smem[];
     uint32_t *buf0 = reinterpret_cast<uint32_t *>(smem);
@@ -338,7 +297,9 @@ __global__ void __launch_bounds__(256) k_scatter_staged(int64_t n, Key key_param
 // slice (per-warp aggregated atomics when the table overflows).
 template <class Key>
 __global__ void __launch_bounds__(256) k_histogram_staged(int64_t n, Key key_param, Ctrl *ctrl,
-                                                           int32_t *bins, SortRange rg) {
+                                                           int32_t *bins, SortRange rg,
+                                                           const int32_t *gate) {
+    if (gate && !*gate) return;
     Key key_of = key_param;   // a per-thread copy (functors may cache lookups)
     __shared__ int32_t hkey[kHash];
     __shared__ int32_t hcnt[kHash];
@@ -386,22 +347,23 @@ __global__ void __launch_bounds__(256) k_histogram_staged(int64_t n, Key key_par
 // into the same range of the other set; nb keys (bins holds nb + 1 ints).
 template <class Key>
 cudaError_t staged_pass(int64_t n, const Key &key_of, int64_t nb, Ctrl *ctrl, int32_t *bins,
-                        int32_t *scan_tmp, cudaStream_t st, SortRange rg = SortRange{0, 0}) {
+                        int32_t *scan_tmp, cudaStream_t st, SortRange rg = SortRange{0, 0},
+                        const int32_t *gate = nullptr) {
     cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(int32_t) * (size_t)(nb + 1), st);
     if (e != cudaSuccess) return e;
     const int T = 256;
     if (n > 0) {
         const int hblocks = (int)std::min<int64_t>((n + kHistStage - 1) / kHistStage, 152 * 8);
-        k_histogram_staged<Key><<<hblocks, T, 0, st>>>(n, key_of, ctrl, bins, rg);
+        k_histogram_staged<Key><<<hblocks, T, 0, st>>>(n, key_of, ctrl, bins, rg, gate);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if ((e = exclusive_scan(bins, nb, scan_tmp, st)) != cudaSuccess) return e;
+    if ((e = exclusive_scan(bins, nb, scan_tmp, st, gate)) != cudaSuccess) return e;
     if (n > 0) {
         // resident blocks per SM as the staging buffer allows (228 KB per SM)
         const int per_sm =
             (int)std::max<size_t>(1, std::min<size_t>(8, (228 * 1024) / (kStageSmem + 1024)));
         const int sblocks = (int)std::min<int64_t>((n + kStage - 1) / kStage, 152 * per_sm);
-        k_scatter_staged<Key><<<sblocks, T, kStageSmem, st>>>(n, key_of, ctrl, bins, rg);
+        k_scatter_staged<Key><<<sblocks, T, kStageSmem, st>>>(n, key_of, ctrl, bins, rg, gate);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -28,13 +28,14 @@ def _d3(v):
 
 def make_structs(n, L, n_particles, dt, q_over_m=-1.0, Q=-1.0, B=(0.0, 0.0, 0.0), wz2=0.0,
                  tile=(0, 0, 0), guard=0, sort_period=0, diag_every=0, diag_capacity=0,
-                 mode=(1, 0, 0), mode_comp=0, block=0, chunk=0, options=0, seed=0):
+                 mode=(1, 0, 0), mode_comp=0, block=0, chunk=0, options=0, seed=0,
+                 stray_rebin=0.0):
     grid = capi.pic_grid_t(_i3(n), _d3(L))
     species = capi.pic_species_t(float(q_over_m), float(Q), int(n_particles))
     params = capi.pic_params_t(float(dt), _d3(B), float(wz2), _i3(tile), int(guard),
                                int(sort_period), int(diag_every), int(diag_capacity),
                                _i3(mode), int(mode_comp), int(block), int(chunk), int(options),
-                               int(seed))
+                               int(seed), float(stray_rebin))
     return grid, species, params
 
 
@@ -44,7 +45,7 @@ class Simulation:
     def __init__(self, n, L, n_particles, dt, q_over_m=-1.0, Q=-1.0, B=(0.0, 0.0, 0.0),
                  wz2=0.0, tile=(0, 0, 0), guard=0, sort_period=0, diag_every=0,
                  diag_capacity=0, mode=(1, 0, 0), mode_comp=0, block=0, chunk=0, options=0,
-                 seed=0, device=None, stream=None):
+                 seed=0, stray_rebin=0.0, device=None, stream=None):
         import torch
 
         self.n = tuple(int(a) for a in (n if np.ndim(n) else (n, n, n)))
@@ -53,7 +54,8 @@ class Simulation:
         self.dt = float(dt)
         grid, species, params = make_structs(self.n, self.L, n_particles, dt, q_over_m, Q, B, wz2,
                                              tile, guard, sort_period, diag_every, diag_capacity,
-                                             mode, mode_comp, block, chunk, options, seed)
+                                             mode, mode_comp, block, chunk, options, seed,
+                                             stray_rebin)
         self.handle = capi.pic_create(grid, species, params)
         self._closed = False
         self.sizes = capi.pic_buffer_sizes(self.handle)
@@ -140,6 +142,10 @@ class Simulation:
 
     def counts(self):
         return capi.pic_get_counts(self.handle)
+
+    def rebin_stats(self):
+        """(re-binnings since the load, strays since the last re-binning decision)."""
+        return capi.pic_rebin_stats(self.handle)
 
     def diagnostics(self, max_records: int = 1 << 16):
         recs = capi.pic_diagnostics(self.handle, max_records)

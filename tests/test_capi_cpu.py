@@ -58,7 +58,7 @@ def test_create_and_sizes_without_gpu(lib):
     dict(n_particles=-1), dict(n_particles=2 ** 31), dict(q_over_m=0.0),
     dict(mode=(9, 0, 0)), dict(mode_comp=3), dict(block=48), dict(block=512),
     dict(chunk=8), dict(chunk=4096), dict(guard=-1), dict(B=(0.0, float("nan"), 0.0)),
-    dict(options=8),
+    dict(options=8), dict(stray_rebin=-1e-3), dict(stray_rebin=float("nan")),
 ])
 def test_create_rejects_bad_configs(lib, kw):
     with pytest.raises(capi.PicError) as e:
@@ -74,6 +74,9 @@ def test_calls_before_binding_are_state_errors(lib):
     assert e.value.code == capi.PIC_ERR_STATE
     with pytest.raises(capi.PicError) as e:
         capi.pic_deposit(h)
+    assert e.value.code == capi.PIC_ERR_STATE
+    with pytest.raises(capi.PicError) as e:
+        capi.pic_rebin_stats(h)
     assert e.value.code == capi.PIC_ERR_STATE
     capi.pic_destroy(h)
 
