@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--grid", type=int, default=128)
+    ap.add_argument("--grid", type=int, default=None,
+                    help="grid nodes per axis (default 128; 256 for the Penning bunch)")
     ap.add_argument("--ppc", type=int, default=64)
     ap.add_argument("--sort-period", type=int, default=None,
                     help="steps between re-binnings (default 4; 2 for the Penning bunch, whose "
@@ -66,6 +67,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the side measurements of the default run (split-call deposit "
+                         "roofline, FP32-deposit line, Penning line)")
+    ap.add_argument("--side-steps", type=int, default=10,
+                    help="timed steps of each side measurement")
     ap.add_argument("--workload", default="landau",
                     choices=["landau", "uniform", "penning", "ensemble", "adjoint"],
                     help="landau: the benchmark step; uniform: the uniform plasma test (random "
@@ -80,6 +86,8 @@ def parse():
                          "then exit")
     args = ap.parse_args()
     penning = args.workload == "penning"
+    if args.grid is None:
+        args.grid = 256 if penning else 128
     if args.sort_period is None:
         args.sort_period = 2 if penning else LAUNCH["sort_period"]
     if args.guard is None:
@@ -231,6 +239,128 @@ def time_oracle(w, steps, warmup=0, uniform=False):
     return w.n_particles * steps / dt, dt
 
 
+# The all-core oracle figure: the oracle's own functions (deposit, solve_field,
+# gather, boris_kick, wrap, in the order of its step) driven over particle
+# chunks by a process pool; the chunks' density grids are summed in a fixed
+# order and the field solve runs once per step in the parent process.
+_ORC = {}
+
+
+def _orc_init(shm_names, shapes, grid_n, grid_L, params):
+    from multiprocessing import shared_memory
+
+    import numpy as np
+
+    from oracle import pic_oracle as po
+
+    _ORC["shm"] = [shared_memory.SharedMemory(name=nm) for nm in shm_names]
+    _ORC["arr"] = [np.ndarray(sh, dtype=np.float64, buffer=s.buf)
+                   for s, sh in zip(_ORC["shm"], shapes)]
+    _ORC["grid"] = po.Grid(grid_n, grid_L)
+    _ORC["params"] = po.Params(**params)
+
+
+def _orc_deposit(job):
+    from oracle import pic_oracle as po
+
+    i, s, e, N = job
+    x, v, xh, rho_parts, _ = _ORC["arr"]
+    g, p = _ORC["grid"], _ORC["params"]
+    xh[s:e] = po.wrap(x[s:e] + 0.5 * p.dt * v[s:e], g)
+    rho_parts[i] = po.deposit(xh[s:e], g, p.Q / N).ravel()
+    return i
+
+
+def _orc_push(job):
+    import numpy as np
+
+    from oracle import pic_oracle as po
+
+    i, s, e, N = job
+    x, v, xh, _, E = _ORC["arr"]
+    g, p = _ORC["grid"], _ORC["params"]
+    e_p = po.gather(xh[s:e], E.reshape((3,) + g.shape), g)
+    if p.wz2 != 0.0:
+        e_p = e_p + po.external_field(xh[s:e], g, p.wz2)
+    v1 = po.boris_kick(v[s:e], e_p, p.q_over_m, p.B, p.dt)
+    x[s:e] = po.wrap(xh[s:e] + 0.5 * p.dt * v1, g)
+    v[s:e] = v1
+    return np.concatenate([v1.sum(axis=0), [float(np.sum(v1 * v1))]])
+
+
+def time_oracle_parallel(w, steps, workers, return_state=False):
+    """Particle-steps/s of the oracle over `workers` processes (spawned);
+    with return_state, also the final (x, v)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+
+    import numpy as np
+
+    from oracle import pic_oracle as po
+
+    N = w.n_particles
+    g = po.Grid(w.n, w.L)
+    chunks = max(1, workers)
+    shapes = [(N, 3), (N, 3), (N, 3), (chunks, g.n_nodes), (3 * g.n_nodes,)]
+    shms, arrs = [], []
+    try:
+        for sh in shapes:
+            s = shared_memory.SharedMemory(create=True, size=int(np.prod(sh)) * 8)
+            shms.append(s)
+            arrs.append(np.ndarray(sh, dtype=np.float64, buffer=s.buf))
+        arrs[0][:] = w.x
+        arrs[1][:] = w.v
+        params = dict(dt=w.dt, q_over_m=w.q_over_m, Q=w.Q, B=tuple(w.B), wz2=w.wz2)
+        bounds = np.linspace(0, N, chunks + 1).astype(np.int64)
+        jobs = [(i, int(bounds[i]), int(bounds[i + 1]), N) for i in range(chunks)]
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(workers, initializer=_orc_init,
+                      initargs=([s.name for s in shms], shapes, w.n, w.L, params)) as pool:
+            pool.map(_orc_deposit, jobs[:1])          # workers up (imports done)
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                list(pool.map(_orc_deposit, jobs))
+                rho = np.zeros(g.n_nodes)
+                for i in range(chunks):               # fixed-order sum of the chunk grids
+                    rho += arrs[3][i]
+                arrs[4][:] = po.solve_field(rho.reshape(g.shape), g).ravel()
+                moments = pool.map(_orc_push, jobs)
+                _ = np.sum(moments, axis=0)
+            secs = time.perf_counter() - t0
+        state = (arrs[0].copy(), arrs[1].copy()) if return_state else None
+    finally:
+        del arrs
+        for s in shms:
+            s.close()
+            s.unlink()
+    if return_state:
+        return N * steps / secs, secs, state
+    return N * steps / secs, secs
+
+
+def cpu_baseline_figures(args, steps=2):
+    """Single-thread and all-core oracle throughput on a bounded sample of the
+    workload, with the core count of this host."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    ws = oracle_sample(args, args.cpu_sample)
+    one, secs1 = time_oracle(ws, steps, uniform=args.workload == "uniform")
+    out = {"value": one, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{ws.n_particles:,} particles of the workload on the full {args.grid}^3 "
+                     f"grid, {steps} oracle steps ({secs1:.1f} s, numpy FP64, single thread)",
+           "host_cores": cores}
+    if cores > 1 and args.workload != "uniform":
+        try:
+            allc, secs_a = time_oracle_parallel(ws, steps, cores)
+            out["all_cores"] = {"value": allc, "unit": UNIT, "cores": cores,
+                                "sample": f"the same sample and steps ({secs_a:.1f} s) over "
+                                          f"{cores} spawned processes, one particle chunk each; "
+                                          f"chunk grids summed in a fixed order, the FFT solve "
+                                          f"in the parent"}
+        except Exception as e:   # pragma: no cover - hosts without shared memory
+            out["all_cores"] = {"unavailable": str(e)[:200]}
+    return out
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -244,7 +374,9 @@ def run_reference(args, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": workload_name(args)},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample,
+                         "host_cores": len(os.sched_getaffinity(0))
+                         if hasattr(os, "sched_getaffinity") else os.cpu_count()},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -307,8 +439,20 @@ def measure_adjoint(n_steps=200, K=20, launch=None):
                                    torch.isfinite(gv).all().item())}
         sim._adj_buf = None
         torch.cuda.empty_cache()
-    # the adjoint of one step, without checkpoint recomputation
-    out["adjoint_step_over_forward"] = out["kept_trajectory"]["backward_over_forward"]
+    # headline: the backward pass with checkpoints every K steps (segment
+    # recomputation included) against the forward step
+    out["adjoint_step_over_forward"] = out["checkpoints"]["backward_over_forward"]
+    out["adjoint_step_over_forward_kept_trajectory"] = out["kept_trajectory"]["backward_over_forward"]
+    # dJ/dalpha = <dJ/dx0, dx0/dalpha> (FP64 dot on the device); the sample
+    # map's Jacobian comes from the input generator
+    sim.load(w.x, w.v)
+    sim.adjoint_forward(n_steps, (0.0, 0.0, 1.0), checkpoint_every=K)
+    gx, _ = sim.adjoint_backward(device=True)
+    dxa = torch.zeros_like(gx)
+    dxa[:, 2] = torch.from_numpy(pi.sample_cosine_density_dalpha(
+        w.x[:, 2], w.meta["alpha"], w.meta["k"])).to(gx.device)
+    out["dJ_dalpha"] = sim.dot(gx, dxa)
+    sim._adj_buf = None
     sim.close()
     return out
 
@@ -416,6 +560,98 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- side lines
+
+def timed_steps(sim, steps, gpu_index=0):
+    """Device time of `steps` pic_step calls with the phase timers on and the
+    SM clocks sampled; returns (ms, phases, launches, clocks)."""
+    import torch
+
+    from paper_2205_11052_gb300 import capi
+
+    capi.pic_enable_timers(sim.handle, True)
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(sim.stream)
+    for _ in range(steps):
+        sim.step(1)
+    ev1.record(sim.stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    phases, launches = capi.pic_read_timers(sim.handle)
+    capi.pic_enable_timers(sim.handle, False)
+    return ev0.elapsed_time(ev1), phases, launches, clk
+
+
+def push_roofline(phases, N, ng, peak, peak_kind):
+    """The fused push + deposit kernel against HBM: 56 B per particle (state
+    read and written once) + 20 B per node (E read, rho written)."""
+    avg_ms = phases["push"][0] / max(1, phases["push"][1])
+    achieved = (56.0 * N + 20.0 * ng) / (avg_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "k_push_deposit", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+            "ms_per_launch": avg_ms}
+
+
+def deposit_roofline(sim, N, ng, peak, peak_kind, launches=3):
+    """The split-call deposit kernel (k_deposit_tiles) at full size, right
+    after a re-binning: 16 B per particle (cell + offsets read) + 4 B per node."""
+    import torch
+
+    from paper_2205_11052_gb300 import capi
+
+    sim.sort()
+    sim.deposit()                       # warm-up
+    torch.cuda.synchronize()
+    capi.pic_enable_timers(sim.handle, True)
+    for _ in range(launches):
+        sim.deposit()
+    torch.cuda.synchronize()
+    phases, _ = capi.pic_read_timers(sim.handle)
+    capi.pic_enable_timers(sim.handle, False)
+    avg_ms = phases["deposit"][0] / max(1, phases["deposit"][1])
+    achieved = (16.0 * N + 4.0 * ng) / (avg_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "k_deposit_tiles", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+            "ms_per_launch": avg_ms, "particles_per_s": N / (avg_ms * 1e-3),
+            "what": f"pic_deposit (split call, fixed point) right after a re-binning, mean of "
+                    f"{launches} launches; 16 B per particle + 4 B per node"}
+
+
+def side_line(x, v, w_like, opts, warmup, steps, peak, peak_kind, ng, what):
+    """One more configuration on the same GPU: load, warm up, time `steps`."""
+    import torch
+
+    from paper_2205_11052_gb300.sim import Simulation
+
+    sim = Simulation(n=w_like.n, L=w_like.L, n_particles=x.shape[0], dt=w_like.dt,
+                     q_over_m=w_like.q_over_m, Q=w_like.Q, B=w_like.B, wz2=w_like.wz2,
+                     mode=w_like.mode, mode_comp=w_like.mode_comp, **opts)
+    sim.load(x, v)
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    r0, _ = sim.rebin_stats()
+    ms, phases, launches, clk = timed_steps(sim, steps)
+    r1, _ = sim.rebin_stats()
+    hist = sim.diagnostics()
+    flags = sim.flags()
+    N = x.shape[0]
+    out = {"workload": what, "value": N * steps / (ms * 1e-3), "unit": UNIT,
+           "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
+           "config": {k: (list(v) if isinstance(v, tuple) else v) for k, v in opts.items()},
+           "phases_ms": {k: round(p[0] / max(1, p[1]), 4) for k, p in phases.items()},
+           "roofline": push_roofline(phases, N, ng, peak, peak_kind),
+           "rebins": r1 - r0, "gpu_launches": launches, "clocks": clk, "device_flags": flags,
+           "diag_last": {k: hist[-1][k] for k in ("step", "Wx", "Wz", "Q", "K")} if hist else None}
+    sim.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- native arm
 
 def main():
@@ -481,6 +717,7 @@ def main():
     torch.cuda.synchronize()
 
     # ---- timed region: K steps, timers on, clocks sampled
+    rebins0, _ = sim.rebin_stats()
     capi.pic_enable_timers(sim.handle, True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -504,6 +741,7 @@ def main():
 
     hist = sim.diagnostics()
     flags = sim.flags()
+    rebins = sim.rebin_stats()[0] - rebins0
 
     # ---- roofline of the dominant kernel (CUDA events inside the timed region)
     peak, peak_kind = load_peaks()
@@ -538,12 +776,17 @@ def main():
             "peak_source": f"{peak_kind} hbm_gbs"}
     phase_ms = {k: (v[0] / max(1, v[1]), v[1]) for k, v in phases.items()}
 
+    # ---- the split-call deposit kernel at full size (its own roofline line)
+    roof_dep = None
+    if rank == 0 and not args.no_extras and args.workload == "landau":
+        roof_dep = deposit_roofline(sim, N, ng, peak, peak_kind)
+
     # ---- end-to-end through the C ABI with pinned host buffers
     e2e = None
+    xh = vh = None
     if not args.no_e2e and args.e2e_steps > 0:
         xh = torch.from_numpy(w.x).pin_memory()
         vh = torch.from_numpy(w.v).pin_memory()
-        del w
         diag_buf = (capi.pic_diag_t * 1)()
         import ctypes as C
         lib = capi.load_library()
@@ -566,20 +809,42 @@ def main():
                "what": "per step: pic_load_particles from pinned host FP64 (x, v), "
                        "pic_step(1), pic_diagnostics readback"}
 
+    # ---- side lines on the same GPU: the FP32 tile-accumulation deposit on
+    # this workload, and the Penning-trap bunch (256^3, 1.3e8 particles)
+    fp32_line = penning_line = None
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == "landau":
+        sim.close()
+        sim = None
+        torch.cuda.empty_cache()
+        if xh is None:
+            xh, vh = w.x, w.v
+        opts = dict(sort_period=args.sort_period, options=args.options & ~capi.PIC_OPT_FIXED_DEPOSIT,
+                    diag_every=args.diag_every, guard=args.guard)
+        fp32_line = side_line(xh, vh, w, opts, 3, args.side_steps, peak, peak_kind, ng,
+                              workload_name(args) + "; FP32 tile accumulation (float shared "
+                              "atomics, float grid atomics)")
+        del xh, vh, w
+        wp = pi.penning(n=256, seed=1002, dt=0.05)
+        popts = dict(sort_period=2, guard=3, options=capi.PIC_OPT_FIXED_DEPOSIT,
+                     diag_every=args.diag_every)
+        penning_line = side_line(wp.x, wp.v, wp, popts, 3, args.side_steps, peak, peak_kind,
+                                 256 ** 3,
+                                 "penning_trap_3d: 256^3 grid on [0,20)^3, 130,000,000 particles "
+                                 "in a Gaussian bunch sigma=(1,1,2), Bz=5, axial frequency 1, "
+                                 f"Q=-1562.5, dt=0.05; {args.side_steps} of its 100 steps")
+        del wp
+
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        ws = oracle_sample(args, args.cpu_sample)
-        val, secs = time_oracle(ws, 2, uniform=args.workload == "uniform")
-        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{ws.n_particles:,} particles of the workload on the full "
-                         f"{args.grid}^3 grid, 2 oracle steps ({secs:.1f} s, numpy FP64, "
-                         f"single thread)"}
+        cpu = cpu_baseline_figures(args)
 
     # ---- adjoint step cost against the forward step (bump-on-tail, 64^3)
     adj = None
     if rank == 0 and not args.no_adjoint:
-        sim.close()
+        if sim is not None:
+            sim.close()
+            sim = None
         torch.cuda.empty_cache()
         adj = measure_adjoint()
 
@@ -597,7 +862,11 @@ def main():
                              f"vs {L2_BYTES / 2**20:.0f} MiB L2), no flush",
                        "parallelism": "replicas" if world > 1 else "single-gpu"},
             "roofline": roof,
+            "roofline_deposit": roof_dep,
             "phases_ms": {k: round(v[0], 4) for k, v in phase_ms.items()},
+            "rebins": rebins,
+            "fp32_deposit": fp32_line,
+            "penning": penning_line,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "adjoint": adj,
@@ -607,7 +876,8 @@ def main():
             "diag_last": {k: hist[-1][k] for k in ("step", "Wx", "Q", "K")} if hist else None,
         }
         print(json.dumps(line), flush=True)
-    sim.close()
+    if sim is not None:
+        sim.close()
     if dist is not None:
         dist.destroy_process_group()
 

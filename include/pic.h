@@ -412,9 +412,11 @@ int pic_batch_get_particles(pic_batch_t b, double *x, double *v, int dst_is_devi
  *          (the layout pic_get_field returns)
  *   out    device pointer to 4 doubles; the caller owns inputs and outputs
  *   stream cudaStream_t as void*, NULL = legacy default stream
- * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before capturing a stream into a CUDA graph.  All calls share the one
+ * Every call looks up the scratch array's device address
+ * (cudaGetSymbolAddress, which allocates nothing) on the device that is
+ * current, so a device reset between calls is harmless; the first call on
+ * each device also loads the library's device code there and does that
+ * set-up, so make it before any stream capture.  All calls share the one
  * scratch array, which keeps the last call's partials (every partial a call
  * reads is written by that same call, so nothing needs clearing); calls whose
  * kernels overlap on the GPU race on it and must be ordered by the caller.

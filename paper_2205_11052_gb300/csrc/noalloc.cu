@@ -19,8 +19,6 @@
 // race on it and must be serialised by the caller.
 #include <stdio.h>
 
-#include <mutex>
-
 #include "pic_internal.cuh"
 
 namespace {
@@ -32,11 +30,6 @@ static_assert((long long)kSpan * kMaxBlocks == PIC_NOALLOC_MAX_NODES, "size cont
 
 // 8192 blocks x 4 doubles = 256 KiB per device
 static __device__ __align__(256) double g_noalloc_partials[kMaxBlocks * 4];
-
-// device address of g_noalloc_partials, looked up once per device
-constexpr int kMaxDevices = 64;
-double *g_scratch_ptr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mu;
 
 __global__ void __launch_bounds__(kThreads) k_energy_partials(const float *__restrict__ rho,
                                                               const float4 *__restrict__ E4,
@@ -90,22 +83,16 @@ int noalloc_fail(int code, const char *msg, cudaError_t e = cudaSuccess) {
                              e != cudaSuccess ? cudaGetErrorString(e) : "");
 }
 
-// Device address of the scratch array on the current device (set-up on the
-// first call per device).
+// Device address of the scratch array on the current device.  It is looked
+// up on every call (cudaGetSymbolAddress allocates nothing), so a context
+// that was reset or replaced since an earlier call is never handed a stale
+// address; the first lookup on a device also loads this library's device
+// code there.
 int scratch_for_current_device(double **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return noalloc_fail(PIC_ERR_CUDA, "cudaGetDevice failed", e);
-    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(PIC_ERR_ARG, "device index too large");
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        if (e != cudaSuccess || !p)
-            return noalloc_fail(PIC_ERR_CUDA, "cudaGetSymbolAddress failed", e);
-        g_scratch_ptr[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess || !p) return noalloc_fail(PIC_ERR_CUDA, "cudaGetSymbolAddress failed", e);
+    *out = static_cast<double *>(p);
     return PIC_OK;
 }
 

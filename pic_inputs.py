@@ -123,6 +123,15 @@ def sample_cosine_density(u: np.ndarray, L: float, alpha: float, k: float,
     return x
 
 
+def sample_cosine_density_dalpha(x: np.ndarray, alpha: float, k: float) -> np.ndarray:
+    """Derivative in alpha of the sample sample_cosine_density(u, L, alpha, k)
+    at fixed u, expressed through the sample x itself: differentiating
+    x + (alpha/k) sin(k x) = u L gives dx/dalpha = -(sin(k x)/k) / (1 + alpha cos(k x)).
+    The Jacobian of this input generator, for gradients of a run with respect
+    to the perturbation amplitude."""
+    return -(np.sin(k * x) / k) / (1.0 + alpha * np.cos(k * x))
+
+
 def _chunked(N: int, seed: int, chunk: int, fill, workers=None):
     """Run fill(rng, start, stop) over [0, N) in chunks, each with its own
     stream spawned from ``seed`` (deterministic for any worker count)."""

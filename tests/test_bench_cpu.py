@@ -30,3 +30,21 @@ def test_reference_arm_prints_one_contract_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_all_core_oracle_driver_reproduces_the_oracle_step():
+    """The all-core CPU baseline drives the oracle's own functions over
+    particle chunks; its state after two steps equals po.run's."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import pic_inputs as pi
+    from oracle import pic_oracle as po
+
+    w = pi.penning(n=8, n_particles=3000, L=20.0, seed=9)
+    val, secs, (x, v) = bench.time_oracle_parallel(w, 2, 2, return_state=True)
+    assert val > 0 and secs > 0
+    xo, vo, _ = po.run(w.x, w.v, po.Grid(w.n, w.L),
+                       po.Params(dt=w.dt, q_over_m=w.q_over_m, Q=w.Q, B=w.B, wz2=w.wz2), 2)
+    assert np.max(np.abs(x - xo)) < 1e-12 and np.max(np.abs(v - vo)) < 1e-12

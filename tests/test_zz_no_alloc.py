@@ -64,6 +64,35 @@ def test_noalloc_reduction_matches_step_diagnostics_on_two_calls():
             assert g == pytest.approx(e, rel=REL)
 
 
+def test_noalloc_calls_leave_device_memory_untouched():
+    """After a first call on the device (its one-time set-up), further calls
+    change neither the device's free memory nor torch's allocations, and
+    repeat the first result bit for bit."""
+    w = pi.landau(n=(32, 32, 24), ppc=2, seed=14, alpha=0.2)
+    sim = Simulation.from_workload(w)
+    sim.deposit()
+    sim.field_solve()
+    ng = int(np.prod(w.n))
+    rho = torch.empty(ng, dtype=torch.float32, device="cuda")
+    E = torch.empty(4 * ng, dtype=torch.float32, device="cuda")
+    capi.pic_get_field(sim.handle, rho.data_ptr(), E.data_ptr(), True)
+    outs = [torch.zeros(4, dtype=torch.float64, device="cuda") for _ in range(3)]
+    dV = float(np.prod(np.asarray(w.L) / np.asarray(w.n)))
+    st = sim.stream.cuda_stream
+    capi.pic_field_energy_noalloc(rho.data_ptr(), E.data_ptr(), ng, dV, outs[0].data_ptr(), st)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    torch_bytes0 = torch.cuda.memory_allocated()
+    for o in outs[1:]:
+        capi.pic_field_energy_noalloc(rho.data_ptr(), E.data_ptr(), ng, dV, o.data_ptr(), st)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == torch_bytes0
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    sim.close()
+
+
 def test_noalloc_rejects_oversized_and_bad_arguments():
     capi.load_library()
     x = torch.zeros(8, dtype=torch.float32, device="cuda")
