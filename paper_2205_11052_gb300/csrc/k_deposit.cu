@@ -5,13 +5,16 @@
 // q_p / h^3 * w_a(fx) w_b(fy) w_c(fz) to node (i + a, j + b, k + c), a, b, c
 // in {0, 1}, with w_0(f) = 1 - f and w_1(f) = f (periodic wrap).
 //
-// Tiled kernel: one CTA per work item (a range of binned particles whose
-// stencil base was inside one tile at the last sort).  The CTA accumulates
-// the unscaled weights in a shared-memory copy of the tile plus `guard`
-// cells on each side (plus the +1 stencil layer) and finally adds the tile
-// to the grid with one global atomic per touched node.  Particles that
-// drifted beyond the guard since the last sort go straight to the grid with
-// global atomics, so the result never depends on the sort cadence.
+// Tiled kernel: each CTA takes a contiguous run of work items (ranges of
+// binned particles whose stencil base was inside one tile at the last sort;
+// consecutive items share tiles) and accumulates the unscaled weights in a
+// shared-memory copy of the tile plus `guard` cells on each side (plus the +1
+// stencil layer).  After each item the tile is folded into per-tile sums
+// that go to the grid with one global atomic per touched node when the run
+// moves to another tile.  Particles that drifted beyond the guard since the
+// last sort go straight to the grid with global atomics, so the result never
+// depends on the sort cadence.  Each thread loads its next particle before
+// depositing the current one.
 //
 // Two accumulators:
 //  * FP32: float shared tile, float global atomics into rho.
@@ -33,18 +36,29 @@ namespace {
 using namespace cic;
 
 template <bool FIXED>
-__global__ void __launch_bounds__(256) k_deposit_tiles(Geom g, const Ctrl *__restrict__ ctrl,
-                                                        const int4 *__restrict__ items,
-                                                        float qscale, float *rho,
-                                                        unsigned long long *rho64, Ctrl *ctrl_w,
-                                                        int sparse_below) {
-    extern __shared__ uint32_t acc[];
+__global__ void __launch_bounds__(256, 3) k_deposit_tiles(Geom g, const Ctrl *__restrict__ ctrl,
+                                                           const int4 *__restrict__ items,
+                                                           float qscale, float *rho,
+                                                           unsigned long long *rho64, Ctrl *ctrl_w,
+                                                           int sparse_below) {
+    extern __shared__ __align__(16) uint32_t acc[];
     const ParticleSet ps = ctrl->sets[ctrl->cur];
     const int n_items = ctrl->n_items;
     unsigned long long strays = 0;
     int bad = 0;
-
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    int it0, it1;
+    item_run(items, n_items, it0, it1);
+    const int S = tile_of(g, 0).S;
+    void *sum = reinterpret_cast<char *>(acc) + sum_offset(S);
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        acc[s] = 0u;
+        if (FIXED) reinterpret_cast<unsigned long long *>(sum)[s] = 0ull;
+        else reinterpret_cast<float *>(sum)[s] = 0.0f;
+    }
+    __syncthreads();
+    int cur_tile = -1;
+    Tile tc = tile_of(g, 0);
+    for (int it = it0; it < it1; ++it) {
         const int4 item = items[it];
         if (item.z - item.y < sparse_below) {
             // few particles: skip the shared tile, add straight to the grid
@@ -59,18 +73,39 @@ __global__ void __launch_bounds__(256) k_deposit_tiles(Geom g, const Ctrl *__res
             continue;
         }
         const Tile t = tile_of(g, item.x);
-        for (int s = threadIdx.x; s < t.S; s += blockDim.x) acc[s] = 0u;
-        __syncthreads();
-        for (int p = item.y + threadIdx.x; p < item.z; p += blockDim.x) {
+        if (item.x != cur_tile) {
+            if (cur_tile >= 0) tile_flush_sum<FIXED>(sum, tc, g, rho, rho64, qscale);
+            cur_tile = item.x;
+            tc = t;
+        }
+        int p = item.y + threadIdx.x;
+        int32_t nc = 0;
+        float nfx = 0.f, nfy = 0.f, nfz = 0.f;
+        if (p < item.z) {
+            nc = __ldcs(ps.cell + p);
+            nfx = __ldcs(ps.o[0] + p);
+            nfy = __ldcs(ps.o[1] + p);
+            nfz = __ldcs(ps.o[2] + p);
+        }
+        for (; p < item.z; p += blockDim.x) {
+            const int32_t c = nc;
+            const float fx = nfx, fy = nfy, fz = nfz;
+            const int pn = p + (int)blockDim.x;
+            if (pn < item.z) {
+                nc = __ldcs(ps.cell + pn);
+                nfx = __ldcs(ps.o[0] + pn);
+                nfy = __ldcs(ps.o[1] + pn);
+                nfz = __ldcs(ps.o[2] + pn);
+            }
             int i, j, k;
-            if (!decode_cell(__ldcs(ps.cell + p), g, i, j, k)) bad = 1;
-            const float fx = __ldcs(ps.o[0] + p), fy = __ldcs(ps.o[1] + p), fz = __ldcs(ps.o[2] + p);
+            if (!decode_cell(c, g, i, j, k)) bad = 1;
             if (!tile_add<FIXED>(acc, t, g, i, j, k, fx, fy, fz, rho, rho64, qscale)) ++strays;
         }
         __syncthreads();
-        tile_flush<FIXED>(acc, t, g, rho, rho64, qscale);
+        tile_fold<FIXED>(acc, sum, S);
         __syncthreads();
     }
+    if (cur_tile >= 0) tile_flush_sum<FIXED>(sum, tc, g, rho, rho64, qscale);
     if (bad) atomicOr(&ctrl_w->flags, PIC_FLAG_BAD_CELL);
     if (strays) atomicAdd(&ctrl_w->stray, strays);
 }
@@ -102,9 +137,7 @@ cudaError_t launch_deposit(int64_t n, const Geom &g, const Ctrl *ctrl, const int
                            cudaStream_t st) {
     (void)n;
     const float qscale = (float)qscale_d;
-    const int S = (g.tile[0] + 2 * g.guard + 1) * (g.tile[1] + 2 * g.guard + 1) *
-                  (g.tile[2] + 2 * g.guard + 1);
-    const size_t smem = sizeof(uint32_t) * (size_t)S;
+    const size_t smem = tile_deposit_smem(g);   // item tile + the block's tile sums
     const int blocks = grid_blocks < max_items ? grid_blocks : (max_items > 0 ? max_items : 1);
     cudaError_t e;
     if (fixed) {
