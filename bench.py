@@ -41,7 +41,8 @@ L2_BYTES = 129 * 2 ** 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 20; 100 for the ensemble, as configured)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--grid", type=int, default=None,
@@ -79,6 +80,10 @@ def parse():
                          "bunch (256^3, 1.3e8 particles, Boris + quadrupole); ensemble: batched "
                          "instances vs per-instance launches; adjoint: only the adjoint cost")
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "particles"],
+                    help="with N > 1 GPUs: replicas (independent runs, the default) or "
+                         "particles (one run, particles split over the ranks, rho summed by an "
+                         "all-reduce each step, the field solved on every rank)")
     ap.add_argument("--ens-count", type=int, default=512, help="ensemble instances")
     ap.add_argument("--record-traffic", metavar="NCU_CSV",
                     help="write profiles/traffic.json from an ncu --csv capture of "
@@ -86,6 +91,8 @@ def parse():
                          "then exit")
     args = ap.parse_args()
     penning = args.workload == "penning"
+    if args.steps is None:
+        args.steps = 100 if args.workload == "ensemble" else 20
     if args.grid is None:
         args.grid = 256 if penning else 128
     if args.sort_period is None:
@@ -473,10 +480,12 @@ def ensemble_members(count, seed=1_000_000):
         ppc = int(rng.integers(8, 65))
         alpha = float(rng.uniform(0.01, 0.1))
         out.append((n, ppc, alpha, seed + i))
-    members = []
-    for n, ppc, alpha, s in out:
-        w = pi.landau(n=n, ppc=ppc, alpha=alpha, seed=s, chunk=1 << 18)
-        members.append(w)
+    # instances are independent (each from its own seed): draw them in parallel
+    import concurrent.futures as cf
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        members = list(ex.map(lambda a: pi.landau(n=a[0], ppc=a[1], alpha=a[2], seed=a[3],
+                                                  chunk=1 << 18), out))
     return members
 
 
@@ -503,6 +512,7 @@ def run_ensemble(args):
 
         t1 = time.perf_counter()
         best, table = tune_ensemble(members, 0.05, space={"tile": [(8, 8, 8), (4, 4, 4)],
+                                                          "block": [128, 256],
                                                           "sort_period": [2, 4], "options": [1]})
         opts = {k: tuple(v) if isinstance(v, list) else v for k, v in best.items()}
         tuned = {"best": best, "table": table, "seconds": round(time.perf_counter() - t1, 1)}
@@ -526,7 +536,8 @@ def run_ensemble(args):
     ens.close()
     del ens
     torch.cuda.empty_cache()
-    sims = [Simulation.from_workload(w, **opts) for w in ws]
+    single_opts = {k: v for k, v in opts.items() if k != "block"}
+    sims = [Simulation.from_workload(w, **single_opts) for w in ws]
     for s in sims:
         s.step(args.warmup)
     torch.cuda.synchronize()
@@ -538,10 +549,32 @@ def run_ensemble(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_single = e0.elapsed_time(e1)
+    # (b) one CUDA graph of all the steps per instance, replayed one after the other
+    gs = torch.cuda.Stream()
+    gs.wait_stream(stream)
+    graphs = []
+    for s in sims:
+        capi.pic_set_stream(s.handle, gs.cuda_stream)
+        with torch.cuda.stream(gs):
+            s.step(1)
+        gs.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=gs):
+            s.step(args.steps)
+        graphs.append(g)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for g in graphs:
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_graphs = e0.elapsed_time(e1)
+    del graphs
     for s in sims:
         s.close()
     v_batch = N * args.steps / (ms_batch * 1e-3)
     v_single = N * args.steps / (ms_single * 1e-3)
+    v_graphs = N * args.steps / (ms_graphs * 1e-3)
     line = {
         "metric": "ensemble particle-steps/s (batched launch vs one launch sequence per instance)",
         "value": v_batch, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -553,8 +586,12 @@ def run_ensemble(args):
                    "generation_s": round(gen_s, 1),
                    **{k: list(v) if isinstance(v, tuple) else v for k, v in opts.items()}},
         "per_instance_launches": {"value": v_single, "ms_per_step": ms_single / args.steps},
+        "per_instance_graphs": {"value": v_graphs, "ms_per_step": ms_graphs / args.steps,
+                                "what": f"one CUDA graph of {args.steps} steps per instance, the "
+                                        f"{len(ws)} graphs replayed in turn"},
         "autotune": tuned,
         "speedup": ms_single / ms_batch,
+        "speedup_vs_graphs": ms_graphs / ms_batch,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -652,6 +689,57 @@ def side_line(x, v, w_like, opts, warmup, steps, peak, peak_kind, ng, what):
     return out
 
 
+# ---------------------------------------------------------------- particle sharding
+
+def run_sharded(args, dist, rank, world):
+    """One Landau run with its particles split over the ranks: per step each
+    rank deposits its share (pic_deposit), an all-reduce sums rho, and each
+    rank solves and pushes (pic_field_solve, pic_gather_push).  Total work is
+    fixed, so this is strong scaling."""
+    import torch
+
+    import pic_inputs as pi
+    from paper_2205_11052_gb300.shard import sharded_simulation
+
+    w = pi.landau(n=args.grid, ppc=args.ppc, seed=1001, n_steps=args.steps, dt=args.dt)
+    N = w.n_particles
+    sim, stepper, (s0, s1) = sharded_simulation(
+        w, rank, world, dist if world > 1 else None, sort_period=args.sort_period,
+        options=args.options, guard=args.guard, diag_every=0)
+    del w
+    stepper.step(args.warmup)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(sim.stream)
+    stepper.step(args.steps)
+    ev1.record(sim.stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+    flags = sim.flags()
+    sim.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": N * args.steps / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(args), "n_particles": N,
+                       "parallelism": f"particles split over {world} rank(s); rho summed by an "
+                                      f"all-reduce every step; field solved on every rank",
+                       "path": "split calls: pic_deposit, all-reduce, pic_set_rho, "
+                               "pic_field_solve, pic_gather_push",
+                       "l2": "inputs larger than L2, no flush"},
+            "clocks": clk, "device_flags": flags}), flush=True)
+
+
 # ---------------------------------------------------------------- native arm
 
 def main():
@@ -690,6 +778,11 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build()
+    if args.shard == "particles":
+        run_sharded(args, dist, rank, world)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     # ---- inputs: seeded synthetic Landau damping (per-rank seed offset)
     options = args.options

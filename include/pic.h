@@ -86,7 +86,9 @@ typedef struct {
     int32_t diag_capacity; /* diagnostic records kept on the device (default 1024) */
     int32_t mode[3];       /* Fourier mode tracked by the diagnostics            */
     int32_t mode_comp;     /* component of E for that mode: 0 = x, 1 = y, 2 = z  */
-    int32_t block;         /* threads per block of the particle kernels (256)    */
+    int32_t block;         /* threads per block of the particle kernels (256);
+                              ensembles: of the batched push + deposit, a
+                              multiple of 32 in 64..256 (autotuned)          */
     int32_t chunk;         /* max particles per deposit work item, 32..4095
                               (default 4095)                                     */
     int32_t options;       /* PIC_OPT_* bits (default 0)                         */

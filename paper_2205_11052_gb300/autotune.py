@@ -1,7 +1,8 @@
 """Autotuner for the launch configuration of the PIC step.
 
 Times a few candidate settings of the tuning knobs of ``pic_params_t`` --
-deposit tile, guard layers, re-binning period, deposit accumulator -- on the
+deposit tile, guard layers, re-binning period, deposit accumulator, and for
+ensembles the thread-block size of the batched push -- on the
 caller's own particles with CUDA events (a few warm-up steps, then a few
 timed steps each) and returns the fastest.  Results are cached by the shape
 of the workload (grid, particles per cell, external fields), in memory and
@@ -91,6 +92,7 @@ class Autotuner:
 
 ENSEMBLE_SPACE = {
     "tile": [(8, 8, 8), (4, 4, 4), (8, 8, 4)],
+    "block": [128, 256],
     "sort_period": [2, 4],
     "options": [1, 0],
 }
@@ -104,7 +106,7 @@ def ensemble_key(members) -> str:
 
 def tune_ensemble(members, dt, space=None, warmup=2, steps=4, cache=None, **fixed):
     """Fastest ensemble setting among the candidates of `space` (a dict of
-    lists over tile / sort_period / options / guard), each timed on the
+    lists over tile / block / sort_period / options / guard), each timed on the
     device over `steps` steps of the whole ensemble after `warmup` steps.
     Returns (best setting, table of (setting, ms per step))."""
     import torch

@@ -21,7 +21,7 @@ from .sim import _d3, _i3, make_structs
 class Ensemble:
     def __init__(self, members, dt, q_over_m=-1.0, B=(0.0, 0.0, 0.0), wz2=0.0, tile=(0, 0, 0),
                  guard=0, sort_period=0, diag_every=0, diag_capacity=0, mode=(1, 0, 0),
-                 mode_comp=0, chunk=0, options=0, device=None, stream=None):
+                 mode_comp=0, chunk=0, options=0, block=0, device=None, stream=None):
         """members: sequence of (n, L, x, v, Q) with x, v (N_i, 3) float64 arrays."""
         import torch
 
@@ -32,7 +32,7 @@ class Ensemble:
         self.counts = [int(np.asarray(m[2]).shape[0]) for m in self.members]
         _, _, params = make_structs((2, 1, 1), (1.0, 1.0, 1.0), 0, dt, q_over_m, 0.0, B, wz2, tile,
                                     guard, sort_period, diag_every, diag_capacity, mode, mode_comp,
-                                    0, chunk, options)
+                                    block, chunk, options)
         self.handle = capi.pic_batch_create(insts, q_over_m, params)
         self._closed = False
         self.sizes = capi.pic_batch_buffer_sizes(self.handle)

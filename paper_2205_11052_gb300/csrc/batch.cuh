@@ -39,7 +39,7 @@ cudaError_t batch_sort_prepare();   // kernel attributes; once per device outsid
 size_t batch_push_smem(int max_S);
 cudaError_t launch_b_push_deposit(bool push, bool diag, bool ext, bool mag, bool fixed,
                                   const InstDesc *desc, const int32_t *tile_inst, Ctrl *ctrl,
-                                  const int4 *items, int blocks, int max_S, const float4 *E8,
+                                  const int4 *items, int blocks, int threads, int max_S, const float4 *E8,
                                   float *rho, unsigned long long *rho64, int sparse_below,
                                   double *part, cudaStream_t st);
 cudaError_t launch_b_rho_finish(int64_t ng, const InstDesc *desc, const long long *g0, int n_inst,

@@ -56,7 +56,7 @@ struct pic_batch {
     std::vector<int32_t> tile_inst;
     std::vector<SizeClass> cls;
     int64_t np, ng, nhalf_tot;
-    int ntiles, max_items, chunk, sparse_below, fused_blocks;
+    int ntiles, max_items, chunk, sparse_below, fused_blocks, block;
     int max_S;                 // largest tile (plus guard) of any instance, in nodes
     size_t fft_reserve;
     int64_t staging;
@@ -190,7 +190,7 @@ int b_deposit_pass(pic_batch *b, bool push, bool diag) {
     if (!b_fixed(b)) B_CUDA(cudaMemsetAsync(b->at<float>(b->o_rho), 0, (size_t)b->ng * 4, b->st));
     B_CUDA(launch_b_push_deposit(push, diag, b_ext(b), b_mag(b), b_fixed(b), b->at<InstDesc>(b->o_desc),
                                  b->at<int32_t>(b->o_tinst), b->ctrl(), b->at<int4>(b->o_items),
-                                 b->fused_blocks, b->max_S, b->at<float4>(b->o_E8),
+                                 b->fused_blocks, b->block, b->max_S, b->at<float4>(b->o_E8),
                                  b->at<float>(b->o_rho), b->at<unsigned long long>(b->o_rho64),
                                  b->sparse_below, b->at<double>(b->o_ppart), b->st));
     if (b_fixed(b))
@@ -239,6 +239,8 @@ int pic_batch_create(const pic_instance_t *inst, int n_inst, double q_over_m,
     if (!(isfinite(params->dt) && params->dt > 0.0)) return record_error(PIC_ERR_ARG, "dt must be finite and > 0");
     if (params->chunk != 0 && (params->chunk < 32 || params->chunk > kMaxChunk))
         return record_error(PIC_ERR_ARG, "chunk must be 0 or in 32..%d", kMaxChunk);
+    if (params->block != 0 && (params->block < 64 || params->block > 256 || params->block % 32))
+        return record_error(PIC_ERR_ARG, "block must be 0 or a multiple of 32 in 64..256");
     if (params->guard < 0 || params->guard > 8) return record_error(PIC_ERR_ARG, "guard outside 0..8");
     if (params->diag_every < 0 || params->diag_capacity < 0) return record_error(PIC_ERR_ARG, "negative diagnostic setting");
     if (params->mode_comp < 0 || params->mode_comp > 2) return record_error(PIC_ERR_ARG, "mode_comp must be 0, 1 or 2");
@@ -272,6 +274,7 @@ int pic_batch_create(const pic_instance_t *inst, int n_inst, double q_over_m,
     b->qm = q_over_m;
     b->inst.assign(inst, inst + n_inst);
     b->chunk = b->prm.chunk ? b->prm.chunk : kMaxChunk;
+    b->block = b->prm.block ? b->prm.block : 256;
     b->sparse_below = 64;
     b->np = np;
 
@@ -385,8 +388,13 @@ int pic_batch_create(const pic_instance_t *inst, int n_inst, double q_over_m,
         delete b;
         return record_error(PIC_ERR_ARG, "deposit tile plus guard too large for shared memory");
     }
+    // two waves of the blocks that fit on an SM (the kernel's register budget
+    // is sized for PIC_BATCH_PD_MIN_BLOCKS blocks of 256 threads)
+    const int64_t per_sm = std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)PIC_BATCH_PD_MIN_BLOCKS * 256 / b->block,
+                             (int64_t)kMaxSmemPerBlock / std::max<size_t>(1, batch_push_smem(max_S))));
     b->fused_blocks = (int)std::max<int64_t>(
-        1, std::min<int64_t>(b->max_items, (int64_t)kNumSMs * PIC_BATCH_PD_MIN_BLOCKS * 2));
+        1, std::min<int64_t>(b->max_items, (int64_t)kNumSMs * per_sm * 2));
     b->staging = std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)1 << 22));
     size_t ws = 0;
     size_t bound = (size_t)b->nhalf_tot * 8 * 3 + ((size_t)4 << 20);

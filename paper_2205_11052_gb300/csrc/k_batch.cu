@@ -413,7 +413,8 @@ size_t batch_push_smem(int max_S) { return cic::sum_offset(max_S) + 8 * (size_t)
 
 cudaError_t launch_b_push_deposit(bool push, bool diag, bool ext, bool mag, bool fixed,
                                   const InstDesc *desc, const int32_t *tile_inst, Ctrl *ctrl,
-                                  const int4 *items, int blocks, int max_S, const float4 *E8,
+                                  const int4 *items, int blocks, int threads, int max_S,
+                                  const float4 *E8,
                                   float *rho, unsigned long long *rho64, int sparse_below,
                                   double *part, cudaStream_t st) {
     const size_t smem = batch_push_smem(max_S);
@@ -425,7 +426,7 @@ cudaError_t launch_b_push_deposit(bool push, bool diag, bool ext, bool mag, bool
             (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                                       (int)smem)) != cudaSuccess)                               \
             return e;                                                                           \
-        kern<<<blocks, 256, smem, st>>>(desc, tile_inst, ctrl, items, E8, rho, rho64,          \
+        kern<<<blocks, threads, smem, st>>>(desc, tile_inst, ctrl, items, E8, rho, rho64,      \
                                         sparse_below, max_S, part);                             \
     } while (0)
 #define PIC_BPD_F(P, D, X, M) \

@@ -119,3 +119,53 @@ def test_autotuner_picks_the_fastest_measured_setting():
                       warmup=1, steps=2)
     cfg = tuner.tune(ws[0])
     assert cfg in [r["cfg"] for r in next(iter(tuner.cache.values()))["table"]]
+
+
+@pytest.mark.parametrize("block", [128, 256])
+def test_block_size_does_not_change_the_result(block):
+    """The batched push's thread-block size is a tuning knob only: with the
+    fixed-point deposit every block size gives the same bits."""
+    ws = _members()
+    out = []
+    for blk in (block, 256):
+        ens = Ensemble([(w.n, w.L, w.x, w.v, w.Q) for w in ws], dt=0.05, sort_period=2,
+                       options=capi.PIC_OPT_FIXED_DEPOSIT, block=blk)
+        ens.step(3)
+        out.append(ens.particles())
+        ens.close()
+    for a, b in zip(out[0][0] + out[0][1], out[1][0] + out[1][1]):
+        assert np.array_equal(a, b)
+
+
+def test_sample_of_the_512_instance_ensemble_follows_the_oracle():
+    """The 512-instance Landau ensemble of the benchmark (grids U{16,24,32,48}^3,
+    8-64 particles per cell, alpha U[0.01, 0.1], seeds 10^6 + i) advanced
+    by a captured CUDA graph with 128-thread blocks, 4^3 tiles and re-binning
+    every 2 steps: one instance of each grid size, drawn with a fixed seed
+    among the lighter ones, against its own oracle run."""
+    import bench
+
+    ws = bench.ensemble_members(512)
+    ens = Ensemble([(w.n, w.L, w.x, w.v, w.Q) for w in ws], dt=0.05, diag_every=1,
+                   tile=(4, 4, 4), sort_period=2, block=128,
+                   options=capi.PIC_OPT_FIXED_DEPOSIT)
+    g = ens.capture(3)            # one eager step, then the captured three
+    g.replay()
+    torch.cuda.synchronize()
+    xs, vs = ens.particles()
+    hist = ens.diagnostics()
+    ens.close()
+    rng = np.random.default_rng(2024)
+    picks = []
+    for n in (16, 24, 32, 48):
+        cand = [i for i, w in enumerate(ws) if w.n[0] == n and w.n_particles <= 16 * n ** 3]
+        picks.append(int(rng.choice(cand)))
+    for i in picks:
+        w = ws[i]
+        gr = po.Grid(w.n, w.L)
+        p = po.Params(dt=0.05, Q=w.Q, q_over_m=w.q_over_m)
+        xo, vo, ho = po.run(w.x, w.v, gr, p, 4)
+        assert _pos_err(xs[i], xo, w) <= 1e-4, i
+        assert np.max(np.abs(vs[i] - vo)) <= 1e-4 * np.max(np.abs(vo)), i
+        assert hist[-1][i]["Wx"] == pytest.approx(ho[-1]["Wx"], rel=1e-4)
+        assert hist[-1][i]["Q"] == pytest.approx(ho[-1]["Q"], rel=1e-6)
