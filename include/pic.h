@@ -262,11 +262,23 @@ int pic_rebin_stats(pic_handle_t h, int64_t *rebins, int64_t *strays);
 
 /* Copy up to max_records diagnostic records (oldest first; at most the last
  * diag_capacity are kept) to host memory and report how many were written.
- * Synchronises, then returns PIC_ERR_DEVICE_FLAG if a kernel raised a flag. */
+ * Synchronises, then returns PIC_ERR_TIMEOUT if a kernel's bounded wait gave
+ * up, or PIC_ERR_DEVICE_FLAG if a kernel raised another flag. */
 int pic_diagnostics(pic_handle_t h, pic_diag_t *out, int max_records, int *n_out);
 
 /* Read (synchronising) and optionally clear the device error flag word. */
 int pic_device_flags(pic_handle_t h, int32_t *flags, int clear);
+
+/* Exercise the failure path of the kernels' bounded waits without a fault
+ * (not in the paper; failure detection of this library).  The staged sort
+ * waits on mbarriers for its bulk copies with a time limit; this call runs one
+ * kernel whose wait has nothing to wait for (an mbarrier no thread arrives on,
+ * no copy in flight), so the wait gives up after that limit (two seconds of
+ * the GPU's clock), the kernel raises PIC_FLAG_TIMEOUT in the flag word and returns, and
+ * the context stays usable.  Synchronises; returns PIC_ERR_TIMEOUT when the
+ * flag was raised (the expected result) and leaves the flag set, so that
+ * pic_diagnostics and pic_device_flags report it until it is cleared. */
+int pic_selftest_timeout(pic_handle_t h);
 
 /* ------------------------------------------------------------ timers */
 

@@ -94,6 +94,7 @@ _SIGNATURES = {
     "pic_set_rho": (C.c_int, [pic_handle_t, C.c_void_p, C.c_int]),
     "pic_get_counts": (C.c_int, [pic_handle_t, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "pic_rebin_stats": (C.c_int, [pic_handle_t, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "pic_selftest_timeout": (C.c_int, [pic_handle_t]),
     "pic_sort": (C.c_int, [pic_handle_t]),
     "pic_deposit": (C.c_int, [pic_handle_t]),
     "pic_field_solve": (C.c_int, [pic_handle_t]),
@@ -234,6 +235,11 @@ def pic_get_counts(h):
     n, s = C.c_int64(), C.c_int64()
     check(_call("pic_get_counts", h, C.byref(n), C.byref(s)), "pic_get_counts")
     return n.value, s.value
+
+
+def pic_selftest_timeout(h) -> int:
+    """Status of one bounded device wait that is left to run out (PIC_ERR_TIMEOUT expected)."""
+    return int(_call("pic_selftest_timeout", h))
 
 
 def pic_rebin_stats(h):

@@ -555,7 +555,9 @@ int pic_batch_diagnostics(pic_batch_t b, pic_diag_t *out, int max_records, int *
         }
     }
     if (n_out) *n_out = (int)want;
-    if (h.flags) return record_error(PIC_ERR_DEVICE_FLAG, "device error flags 0x%x", h.flags);
+    if (h.flags)
+        return record_error((h.flags & PIC_FLAG_TIMEOUT) ? PIC_ERR_TIMEOUT : PIC_ERR_DEVICE_FLAG,
+                            "device error flags 0x%x", h.flags);
     return PIC_OK;
 }
 

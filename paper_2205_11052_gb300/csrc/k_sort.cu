@@ -316,6 +316,26 @@ cudaError_t launch_sort_range(int64_t n, int64_t o, const Geom &g, Ctrl *ctrl, i
     return cudaSuccess;
 }
 
+namespace {
+// The failure path of the bounded waits, on purpose and without a fault: an
+// mbarrier that no thread arrives on and no copy completes is waited for with
+// the same bounded wait the staged kernels use; the wait gives up after its
+// poll limit, the kernel raises PIC_FLAG_TIMEOUT and returns.  Nothing is in
+// flight, so the block can leave at once.
+__global__ void k_timeout_selftest(Ctrl *ctrl) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    if (!mbar_wait(&bar, 0u)) atomicOr(&ctrl->flags, PIC_FLAG_TIMEOUT);
+}
+}  // namespace
+
+cudaError_t launch_timeout_selftest(Ctrl *ctrl, cudaStream_t st) {
+    k_timeout_selftest<<<1, 32, 0, st>>>(ctrl);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_flip(Ctrl *ctrl, cudaStream_t st) {
     k_flip<<<1, 1, 0, st>>>(ctrl);
     return cudaGetLastError();

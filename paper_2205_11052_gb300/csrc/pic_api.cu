@@ -762,6 +762,12 @@ const void *mapped_host(const void *p, size_t bytes) {
 }
 
 // Reset the resettable head of the control block (everything before `cur`).
+// a raised device flag as a status: a bounded wait that gave up is reported
+// as such, every other flag as PIC_ERR_DEVICE_FLAG
+int flag_error(int32_t flags) {
+    return (flags & PIC_FLAG_TIMEOUT) ? PIC_ERR_TIMEOUT : PIC_ERR_DEVICE_FLAG;
+}
+
 int reset_ctrl(pic_ctx *c) {
     PIC_CUDA(cudaMemsetAsync(c->ctrl(), 0, offsetof(Ctrl, cur), c->st));
     return PIC_OK;
@@ -1191,7 +1197,7 @@ int pic_diagnostics(pic_handle_t c, pic_diag_t *out, int max_records, int *n_out
         for (long long q = 0; q < want; ++q) out[q] = all[(size_t)((first + q) % cap)];
     }
     if (n_out) *n_out = (int)want;
-    if (h.flags) return fail(PIC_ERR_DEVICE_FLAG, "device error flags 0x%x", h.flags);
+    if (h.flags) return fail(flag_error(h.flags), "device error flags 0x%x", h.flags);
     return PIC_OK;
 }
 
@@ -1204,6 +1210,17 @@ int pic_rebin_stats(pic_handle_t c, int64_t *rebins, int64_t *strays) {
     if (rebins) *rebins = h.rebins;
     if (strays) *strays = (int64_t)h.stray_step;
     return PIC_OK;
+}
+
+int pic_selftest_timeout(pic_handle_t c) {
+    int r = check_ready(c);
+    if (r) return r;
+    PIC_CUDA(launch_timeout_selftest(c->ctrl(), c->st));
+    PIC_CUDA(cudaStreamSynchronize(c->st));
+    int32_t f = 0;
+    PIC_CUDA(cudaMemcpy(&f, c->ctrl(), sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (f & PIC_FLAG_TIMEOUT) return fail(PIC_ERR_TIMEOUT, "bounded device wait gave up (flags 0x%x)", f);
+    return fail(PIC_ERR_STATE, "the self-test wait completed, which it must not");
 }
 
 int pic_device_flags(pic_handle_t c, int32_t *flags, int clear) {

@@ -215,6 +215,8 @@ cudaError_t launch_sort_range(int64_t n, int64_t o, const Geom &g, Ctrl *ctrl, i
                               int64_t nbins, int32_t *scan_tmp, int *passes, int *kernels,
                               cudaStream_t st);
 cudaError_t launch_flip(Ctrl *ctrl, cudaStream_t st);   // ctrl->cur = 1 - ctrl->cur
+// one bounded wait that nothing completes: raises PIC_FLAG_TIMEOUT (pic_selftest_timeout)
+cudaError_t launch_timeout_selftest(Ctrl *ctrl, cudaStream_t st);
 
 cudaError_t launch_deposit(int64_t n, const Geom &g, const Ctrl *ctrl, const int4 *items,
                            int max_items, double qscale, float *rho, unsigned long long *rho64,

@@ -1,7 +1,7 @@
 // Bulk asynchronous copies (TMA, cp.async.bulk) from global into shared
 // memory with mbarrier completion, shared by the staged sort passes and the
-// staged push.  Every wait is bounded: mbar_wait gives up after a fixed
-// number of polls and the caller raises PIC_FLAG_TIMEOUT.
+// self-test of the bounded wait.  Every wait is bounded: mbar_wait gives up
+// after two seconds (or 2^24 polls) and the caller raises PIC_FLAG_TIMEOUT.
 #pragma once
 
 #include <stdint.h>
@@ -34,10 +34,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-// bounded wait for the phase of the given parity; false if it gave up
+// nanoseconds of the GPU's global timer
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// longest a bounded wait waits before it gives up (copies of a few KB take
+// microseconds; this is the bound of a wait that would otherwise never end)
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+// bounded wait for the phase of the given parity; false if it gave up.
+// Bounded in wall time (each try_wait may suspend the thread for a short,
+// system-dependent time) and in the number of polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 22); ++it)
+    const uint64_t t0 = global_ns();
+    for (int it = 0; it < (1 << 24); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
     return false;
 }
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {

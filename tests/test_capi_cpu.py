@@ -78,6 +78,7 @@ def test_calls_before_binding_are_state_errors(lib):
     with pytest.raises(capi.PicError) as e:
         capi.pic_rebin_stats(h)
     assert e.value.code == capi.PIC_ERR_STATE
+    assert capi.pic_selftest_timeout(h) == capi.PIC_ERR_STATE
     capi.pic_destroy(h)
 
 
