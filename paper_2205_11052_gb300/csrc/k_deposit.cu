@@ -110,14 +110,25 @@ __global__ void __launch_bounds__(256, 3) k_deposit_tiles(Geom g, const Ctrl *__
     if (strays) atomicAdd(&ctrl_w->stray, strays);
 }
 
-// integer grid -> charge density, and clear the integer grid for next time
-__global__ void k_rho_finish(int64_t ng, unsigned long long *__restrict__ rho64,
-                             float *__restrict__ rho, double scale) {
+// integer grid -> charge density, and clear the integer grid for next time;
+// two nodes per thread and iteration (16-byte loads and stores of the 8-byte
+// words, 8-byte stores of the densities), the odd last node by thread 0
+__global__ void __launch_bounds__(256) k_rho_finish(int64_t ng, unsigned long long *__restrict__ rho64,
+                                                    float *__restrict__ rho, double scale) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gidx < ng; gidx += stride) {
-        const long long v = (long long)rho64[gidx];
-        rho[gidx] = (float)((double)v * scale);
-        rho64[gidx] = 0ull;
+    const int64_t n2 = ng >> 1;
+    ulonglong2 *r2 = reinterpret_cast<ulonglong2 *>(rho64);
+    float2 *f2 = reinterpret_cast<float2 *>(rho);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += stride) {
+        const ulonglong2 v = __ldcs(r2 + q);
+        __stcs(f2 + q, make_float2((float)((double)(long long)v.x * scale),
+                                   (float)((double)(long long)v.y * scale)));
+        __stcs(r2 + q, make_ulonglong2(0ull, 0ull));
+    }
+    if ((ng & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const long long v = (long long)rho64[ng - 1];
+        rho[ng - 1] = (float)((double)v * scale);
+        rho64[ng - 1] = 0ull;
     }
 }
 
@@ -126,7 +137,7 @@ __global__ void k_rho_finish(int64_t ng, unsigned long long *__restrict__ rho64,
 cudaError_t launch_rho_finish(const Geom &g, unsigned long long *rho64, float *rho, double qscale,
                               cudaStream_t st) {
     const int64_t ng = (int64_t)g.n[0] * g.n[1] * g.n[2];
-    const int fb = (int)std::min<int64_t>((ng + 255) / 256, 152 * 8);
+    const int fb = (int)std::max<int64_t>(1, std::min<int64_t>((ng / 2 + 255) / 256, 152 * 8));
     k_rho_finish<<<fb, 256, 0, st>>>(ng, rho64, rho, qscale / (double)kFixOne);
     return cudaGetLastError();
 }

@@ -20,19 +20,21 @@ namespace pic {
 
 namespace {
 
-__global__ void k_green(int nx, int ny, int nz, int nh, double tpx, double tpy, double tpz,
-                        double inv_ng, const float2 *__restrict__ rho_hat,
-                        float2 *__restrict__ E_hat, int64_t nhalf, int mi, int mj, int mk,
-                        int mode_comp, int mode_conj, Ctrl *ctrl) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nhalf) return;
-    const int a = (int)(q % nh);
-    const int64_t r = q / nh;
-    const int b = (int)(r % ny);
-    const int c = (int)(r / ny);
-    const int my = (b <= ny / 2) ? b : b - ny;
-    const int mz = (c <= nz / 2) ? c : c - nz;
-    const float kx = (float)(tpx * a), ky = (float)(tpy * my), kz = (float)(tpz * mz);
+// One thread per coefficient of an x-row (a) of the half spectrum; the row
+// (b, c) comes from the block's y and z indices, so no index is divided.
+// ktab holds the FP32 wavenumbers of every FFT index per axis (x: nh
+// entries, then y: ny, then z: nz), rounded once from FP64 on the host.
+__global__ void __launch_bounds__(128) k_green(int nx, int ny, int nz, int nh,
+                                               const float *__restrict__ ktab, float inv_ng,
+                                               const float2 *__restrict__ rho_hat,
+                                               float2 *__restrict__ E_hat, int64_t nhalf, int mi,
+                                               int mj, int mk, int mode_comp, int mode_conj,
+                                               Ctrl *ctrl) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nh) return;
+    const int b = blockIdx.y, c = blockIdx.z;
+    const int64_t q = ((int64_t)c * ny + b) * nh + a;
+    const float kx = ktab[a], ky = ktab[nh + b], kz = ktab[nh + ny + c];
     const float gx = ((nx & 1) == 0 && a == nx / 2) ? 0.0f : kx;
     const float gy = ((ny & 1) == 0 && b == ny / 2) ? 0.0f : ky;
     const float gz = ((nz & 1) == 0 && c == nz / 2) ? 0.0f : kz;
@@ -40,7 +42,7 @@ __global__ void k_green(int nx, int ny, int nz, int nh, double tpx, double tpy, 
     float2 ex = make_float2(0.f, 0.f), ey = ex, ez = ex;
     if (q != 0) {
         const float2 rh = rho_hat[q];
-        const float sc = (float)inv_ng / k2;
+        const float sc = inv_ng / k2;
         // -i * g * rh = g * (rh.y, -rh.x)
         ex = make_float2(gx * sc * rh.y, -gx * sc * rh.x);
         ey = make_float2(gy * sc * rh.y, -gy * sc * rh.x);
@@ -84,7 +86,21 @@ __global__ void __launch_bounds__(256) k_diag_field(int64_t ng, const float *__r
                                                      const float4 *__restrict__ E4, double *part) {
     float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += stride) {
+    // two nodes per iteration, both loaded before either is summed
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; g + stride < ng; g += 2 * stride) {
+        const float4 e = __ldcs(E4 + g), e2 = __ldcs(E4 + g + stride);
+        const float r = __ldcs(rho + g), r2 = __ldcs(rho + g + stride);
+        ff_add_sq(hi[0], lo[0], e.x);
+        ff_add_sq(hi[1], lo[1], e.y);
+        ff_add_sq(hi[2], lo[2], e.z);
+        ff_add(hi[3], lo[3], r);
+        ff_add_sq(hi[0], lo[0], e2.x);
+        ff_add_sq(hi[1], lo[1], e2.y);
+        ff_add_sq(hi[2], lo[2], e2.z);
+        ff_add(hi[3], lo[3], r2);
+    }
+    if (g < ng) {
         const float4 e = E4[g];
         ff_add_sq(hi[0], lo[0], e.x);
         ff_add_sq(hi[1], lo[1], e.y);
@@ -168,15 +184,29 @@ cudaError_t launch_pair_E(const Geom &g, const float4 *E4, float4 *E8, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_green(const Geom &g, const double *L_d, const float2 *rho_hat, float2 *E_hat,
+void green_table(const Geom &g, const double *L_d, float *ktab) {
+    const double two_pi = 6.283185307179586476925286766559;
+    int o = 0;
+    for (int a = 0; a < g.nh; ++a) ktab[o++] = (float)(two_pi / L_d[0] * a);
+    for (int b = 0; b < g.n[1]; ++b) {
+        const int m = (b <= g.n[1] / 2) ? b : b - g.n[1];
+        ktab[o++] = (float)(two_pi / L_d[1] * m);
+    }
+    for (int c = 0; c < g.n[2]; ++c) {
+        const int m = (c <= g.n[2] / 2) ? c : c - g.n[2];
+        ktab[o++] = (float)(two_pi / L_d[2] * m);
+    }
+}
+
+cudaError_t launch_green(const Geom &g, const float *ktab, const float2 *rho_hat, float2 *E_hat,
                          int64_t nhalf, const int *mode_idx, int mode_comp, int mode_conj,
                          Ctrl *ctrl, cudaStream_t st) {
-    const double two_pi = 6.283185307179586476925286766559;
     const double ng = (double)g.n[0] * g.n[1] * g.n[2];
-    const int T = 256;
-    k_green<<<(unsigned)((nhalf + T - 1) / T), T, 0, st>>>(
-        g.n[0], g.n[1], g.n[2], g.nh, two_pi / L_d[0], two_pi / L_d[1], two_pi / L_d[2], 1.0 / ng,
-        rho_hat, E_hat, nhalf, mode_idx[0], mode_idx[1], mode_idx[2], mode_comp, mode_conj, ctrl);
+    const int T = 128;
+    const dim3 grid((unsigned)((g.nh + T - 1) / T), (unsigned)g.n[1], (unsigned)g.n[2]);
+    k_green<<<grid, T, 0, st>>>(g.n[0], g.n[1], g.n[2], g.nh, ktab, (float)(1.0 / ng), rho_hat,
+                                E_hat, nhalf, mode_idx[0], mode_idx[1], mode_idx[2], mode_comp,
+                                mode_conj, ctrl);
     return cudaGetLastError();
 }
 

@@ -49,7 +49,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // Byte offsets of every device buffer inside the caller's arena.
 struct Layout {
     size_t ctrl, sets, rho, rho64, rho_hat, E_hat, E4, E8, lrho2, bins, scan_tmp, tile_items, tile_range,
-        items, fpart, ppart, ring, inv, stage_x, stage_v, adjE4, fft, total;
+        items, fpart, ppart, ring, inv, stage_x, stage_v, adjE4, ktab, fft, total;
     size_t set_stride;   // bytes of one per-particle array
 };
 
@@ -221,6 +221,7 @@ void compute_layout(pic_ctx *c) {
     L.stage_v = take((size_t)c->staging * 24);
     L.adjE4 = take((size_t)c->ng * 16);
     L.lrho2 = take((size_t)c->ng * 8);
+    L.ktab = take((size_t)(c->geom.nh + c->grid.n[1] + c->grid.n[2]) * 4);
     L.fft = take(c->fft_reserve);
     L.total = o;
 }
@@ -354,7 +355,7 @@ int do_solve(pic_ctx *c) {
     int r = timer_begin(c, PIC_PHASE_SOLVE);
     if (r) return r;
     PIC_CUFFT(cufftExecR2C(c->r2c, c->at<cufftReal>(c->lay.rho), c->at<cufftComplex>(c->lay.rho_hat)));
-    PIC_CUDA(launch_green(c->geom, c->L, c->at<float2>(c->lay.rho_hat), c->at<float2>(c->lay.E_hat),
+    PIC_CUDA(launch_green(c->geom, c->at<float>(c->lay.ktab), c->at<float2>(c->lay.rho_hat), c->at<float2>(c->lay.E_hat),
                           c->nhalf, c->mode_idx, c->prm.mode_comp, c->mode_conj, c->ctrl(), c->st));
     PIC_CUFFT(cufftExecC2R(c->c2r, c->at<cufftComplex>(c->lay.E_hat), c->at<cufftReal>(c->lay.E4)));
     PIC_CUDA(launch_pair_E(c->geom, c->at<float4>(c->lay.E4), c->at<float4>(c->lay.E8), c->st));
@@ -948,6 +949,10 @@ int pic_bind_workspace(pic_handle_t c, void *arena, size_t bytes, void *stream) 
     c->hsets[0] = h.sets[0];
     c->hsets[1] = h.sets[1];
     PIC_CUDA(cudaMemcpyAsync(c->ctrl(), &h, sizeof(h), cudaMemcpyHostToDevice, c->st));
+    std::vector<float> ktab((size_t)(c->geom.nh + c->grid.n[1] + c->grid.n[2]));
+    green_table(c->geom, c->L, ktab.data());
+    PIC_CUDA(cudaMemcpyAsync(c->at<float>(c->lay.ktab), ktab.data(), ktab.size() * 4,
+                             cudaMemcpyHostToDevice, c->st));
     PIC_CUDA(cudaMemsetAsync(c->at<char>(c->lay.E4), 0, (size_t)c->ng * 16, c->st));
     PIC_CUDA(cudaMemsetAsync(c->at<char>(c->lay.rho), 0, (size_t)c->ng * 4, c->st));
     PIC_CUDA(cudaMemsetAsync(c->at<char>(c->lay.rho64), 0, (size_t)c->ng * 8, c->st));

@@ -256,7 +256,9 @@ cudaError_t launch_gather_push(int64_t n, const Geom &g, const PushConst &pc, bo
 // E8[2q] = E4[q], E8[2q + 1] = E4[q + x (periodic)]
 cudaError_t launch_pair_E(const Geom &g, const float4 *E4, float4 *E8, cudaStream_t st);
 
-cudaError_t launch_green(const Geom &g, const double *L_d, const float2 *rho_hat,
+// FP32 wavenumbers of every FFT index per axis (x: nh, y: ny, z: nz entries)
+void green_table(const Geom &g, const double *L_d, float *ktab);
+cudaError_t launch_green(const Geom &g, const float *ktab, const float2 *rho_hat,
                          float2 *E_hat, int64_t nhalf, const int *mode_idx, int mode_comp,
                          int mode_conj, Ctrl *ctrl, cudaStream_t st);
 cudaError_t launch_diag_field(const Geom &g, const float *rho, const float4 *E4,
