@@ -169,10 +169,33 @@ __global__ void __launch_bounds__(256, PIC_ADJ_MIN_BLOCKS) k_adj_push(Geom g, co
         const cic::Tile tb = cic::tile_of(g, tile);
         for (int q = threadIdx.x; q < 3 * S; q += blockDim.x) acc[q] = 0;
         __syncthreads();
-        for (int p = item.y + threadIdx.x; p < item.z; p += blockDim.x) {
+        // the next particle's position and multipliers are loaded before the
+        // current one is reversed
+        int p = item.y + threadIdx.x;
+        int32_t nyc = 0;
+        float nly0 = 0.f, nly1 = 0.f, nly2 = 0.f, nfx = 0.f, nfy = 0.f, nfz = 0.f;
+        float nlv0 = 0.f, nlv1 = 0.f, nlv2 = 0.f;
+        if (p < item.z) {
+            nyc = ycell[p];
+            nly0 = lam.o[0][p]; nly1 = lam.o[1][p]; nly2 = lam.o[2][p];
+            nfx = yo0[p]; nfy = yo1[p]; nfz = yo2[p];
+            nlv0 = lam.v[0][p]; nlv1 = lam.v[1][p]; nlv2 = lam.v[2][p];
+        }
+        for (; p < item.z; p += blockDim.x) {
             int i, j, k;
-            if (!decode(ycell[p], g, i, j, k)) bad = 1;
-            float ly0 = lam.o[0][p], ly1 = lam.o[1][p], ly2 = lam.o[2][p];
+            if (!decode(nyc, g, i, j, k)) bad = 1;
+            float ly0 = nly0, ly1 = nly1, ly2 = nly2;
+            const float fx = nfx, fy = nfy, fz = nfz;
+            const float plv0 = nlv0, plv1 = nlv1, plv2 = nlv2;
+            {
+                const int pn = p + (int)blockDim.x;
+                if (pn < item.z) {
+                    nyc = ycell[pn];
+                    nly0 = lam.o[0][pn]; nly1 = lam.o[1][pn]; nly2 = lam.o[2][pn];
+                    nfx = yo0[pn]; nfy = yo1[pn]; nfz = yo2[pn];
+                    nlv0 = lam.v[0][pn]; nlv1 = lam.v[1][pn]; nlv2 = lam.v[2][pn];
+                }
+            }
             if (rt.cell) {
                 // the deposit term (dD/dy)^T lrho of the step after this one
                 int ri, rj, rk;
@@ -185,10 +208,9 @@ __global__ void __launch_bounds__(256, PIC_ADJ_MIN_BLOCKS) k_adj_push(Geom g, co
                 ly1 += rt.sy * ry;
                 ly2 += rt.sz * rz;
             }
-            const float fx = yo0[p], fy = yo1[p], fz = yo2[p];
-            float lv0 = lam.v[0][p] + dt * ly0;
-            float lv1 = lam.v[1][p] + dt * ly1;
-            float lv2 = lam.v[2][p] + dt * ly2;
+            float lv0 = plv0 + dt * ly0;
+            float lv1 = plv1 + dt * ly1;
+            float lv2 = plv2 + dt * ly2;
             const float lt0 = lv0, lt1 = lv1, lt2 = lv2;   // lv_tot (for PG)
             float le0, le1, le2;
             if (ab.mag) {

@@ -121,7 +121,7 @@ constexpr int kMaxSmemPerBlock = 227 * 1024;   // opt-in shared memory per block
 #endif
 // resident blocks per SM the reverse push is compiled for
 #ifndef PIC_ADJ_MIN_BLOCKS
-#define PIC_ADJ_MIN_BLOCKS 4
+#define PIC_ADJ_MIN_BLOCKS 3
 #endif
 constexpr int kMaxChunk = 4095;   // fixed-point tile slots stay below 2^32
 
