@@ -8,7 +8,7 @@ namespace pic {
 
 // resident blocks per SM the batched push + deposit kernel is compiled for
 #ifndef PIC_BATCH_PD_MIN_BLOCKS
-#define PIC_BATCH_PD_MIN_BLOCKS 4
+#define PIC_BATCH_PD_MIN_BLOCKS 3
 #endif
 
 // One instance of an ensemble (device copy in the batch arena).

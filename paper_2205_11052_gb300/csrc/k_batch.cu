@@ -181,19 +181,42 @@ __global__ void __launch_bounds__(256, PIC_BATCH_PD_MIN_BLOCKS) k_b_push_deposit
             Dc = &D;
         }
         float a[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int p = item.y + threadIdx.x; p < item.z; p += blockDim.x) {
-            int32_t c = ps.cell[p];
-            float fx = ps.o[0][p], fy = ps.o[1][p], fz = ps.o[2][p];
+        // the next particle's streams are loaded before the current one is pushed
+        int p = item.y + threadIdx.x;
+        int32_t nc = 0;
+        float nfx = 0.f, nfy = 0.f, nfz = 0.f, nvx = 0.f, nvy = 0.f, nvz = 0.f;
+        if (p < item.z) {
+            nc = __ldcs(ps.cell + p);
+            nfx = __ldcs(ps.o[0] + p); nfy = __ldcs(ps.o[1] + p); nfz = __ldcs(ps.o[2] + p);
             if (PUSH) {
-                float vx = ps.v[0][p], vy = ps.v[1][p], vz = ps.v[2][p];
+                nvx = __ldcs(ps.v[0] + p); nvy = __ldcs(ps.v[1] + p); nvz = __ldcs(ps.v[2] + p);
+            }
+        }
+        for (; p < item.z; p += blockDim.x) {
+            int32_t c = nc;
+            float fx = nfx, fy = nfy, fz = nfz;
+            const float cvx = nvx, cvy = nvy, cvz = nvz;
+            {
+                const int pn = p + (int)blockDim.x;
+                if (pn < item.z) {
+                    nc = __ldcs(ps.cell + pn);
+                    nfx = __ldcs(ps.o[0] + pn); nfy = __ldcs(ps.o[1] + pn); nfz = __ldcs(ps.o[2] + pn);
+                    if (PUSH) {
+                        nvx = __ldcs(ps.v[0] + pn); nvy = __ldcs(ps.v[1] + pn);
+                        nvz = __ldcs(ps.v[2] + pn);
+                    }
+                }
+            }
+            if (PUSH) {
+                float vx = cvx, vy = cvy, vz = cvz;
                 push_one_pairs<EXT, MAG>(g, pc, Ei, c, fx, fy, fz, vx, vy, vz, bad);
-                ps.cell[p] = c;
-                ps.o[0][p] = fx;
-                ps.o[1][p] = fy;
-                ps.o[2][p] = fz;
-                ps.v[0][p] = vx;
-                ps.v[1][p] = vy;
-                ps.v[2][p] = vz;
+                __stcs(ps.cell + p, c);
+                __stcs(ps.o[0] + p, fx);
+                __stcs(ps.o[1] + p, fy);
+                __stcs(ps.o[2] + p, fz);
+                __stcs(ps.v[0] + p, vx);
+                __stcs(ps.v[1] + p, vy);
+                __stcs(ps.v[2] + p, vz);
                 if (DIAG) {
                     a[0] += vx;
                     a[1] += vy;
