@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the side measurements of the default run (split-call deposit "
-                         "roofline, FP32-deposit line, Penning line)")
+                         "roofline, FP32-deposit line, Penning line, 512-instance ensemble)")
     ap.add_argument("--side-steps", type=int, default=10,
                     help="timed steps of each side measurement")
     ap.add_argument("--workload", default="landau",
@@ -489,25 +489,29 @@ def ensemble_members(count, seed=1_000_000):
     return members
 
 
-def run_ensemble(args):
-    """Batched ensemble vs the same instances stepped one launch sequence
-    per instance; both timed on the device over the same steps."""
+# the autotuner's choice for the 512-instance ensemble on a GB300
+# (profiles/ensemble512_bench.md), used when the default run times it
+ENSEMBLE_TUNED = dict(tile=(8, 8, 8), block=256, sort_period=4, options=1)
+
+
+def measure_ensemble(count, steps, warmup, tune=True, sort_period=4, options=1):
+    """Batched ensemble vs the same instances stepped (a) one launch sequence
+    per instance and (b) one CUDA graph per instance, all timed on the device
+    over the same steps.  Returns the measurement as a dict."""
     import torch
 
     from paper_2205_11052_gb300 import capi
     from paper_2205_11052_gb300.batch import Ensemble
-    from paper_2205_11052_gb300.build import build
     from paper_2205_11052_gb300.sim import Simulation
 
-    build()
     t0 = time.perf_counter()
-    ws = ensemble_members(args.ens_count)
+    ws = ensemble_members(count)
     gen_s = time.perf_counter() - t0
     N = sum(w.n_particles for w in ws)
-    opts = dict(sort_period=args.sort_period, options=args.options)
+    opts = dict(sort_period=sort_period, options=options)
     members = [(w.n, w.L, w.x, w.v, w.Q) for w in ws]
     tuned = None
-    if not args.no_tune:
+    if tune:
         from paper_2205_11052_gb300.autotune import tune_ensemble
 
         t1 = time.perf_counter()
@@ -516,10 +520,12 @@ def run_ensemble(args):
                                                           "sort_period": [2, 4], "options": [1]})
         opts = {k: tuple(v) if isinstance(v, list) else v for k, v in best.items()}
         tuned = {"best": best, "table": table, "seconds": round(time.perf_counter() - t1, 1)}
+    else:
+        opts = dict(ENSEMBLE_TUNED)
     ens = Ensemble(members, dt=0.05, **opts)
     # all instances, all K steps: one CUDA graph, replayed once per timing
-    graph = ens.capture(args.steps)
-    for _ in range(max(1, args.warmup // max(1, args.steps))):
+    graph = ens.capture(steps)
+    for _ in range(max(1, warmup // max(1, steps))):
         graph.replay()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -539,11 +545,11 @@ def run_ensemble(args):
     single_opts = {k: v for k, v in opts.items() if k != "block"}
     sims = [Simulation.from_workload(w, **single_opts) for w in ws]
     for s in sims:
-        s.step(args.warmup)
+        s.step(warmup)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         for s in sims:
             s.step(1)
     e1.record(stream)
@@ -560,7 +566,7 @@ def run_ensemble(args):
         gs.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=gs):
-            s.step(args.steps)
+            s.step(steps)
         graphs.append(g)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -572,27 +578,42 @@ def run_ensemble(args):
     del graphs
     for s in sims:
         s.close()
-    v_batch = N * args.steps / (ms_batch * 1e-3)
-    v_single = N * args.steps / (ms_single * 1e-3)
-    v_graphs = N * args.steps / (ms_graphs * 1e-3)
-    line = {
-        "metric": "ensemble particle-steps/s (batched launch vs one launch sequence per instance)",
-        "value": v_batch, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_batch / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"ensemble of {len(ws)} Landau instances, grids U{{16,24,32,48}}^3, "
-                               f"8-64 particles/cell, alpha U[0.01,0.1], {N:,} particles; "
-                               f"batched steps captured in one CUDA graph",
-                   "generation_s": round(gen_s, 1),
-                   **{k: list(v) if isinstance(v, tuple) else v for k, v in opts.items()}},
-        "per_instance_launches": {"value": v_single, "ms_per_step": ms_single / args.steps},
-        "per_instance_graphs": {"value": v_graphs, "ms_per_step": ms_graphs / args.steps,
-                                "what": f"one CUDA graph of {args.steps} steps per instance, the "
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"ensemble of {len(ws)} Landau instances, grids U{{16,24,32,48}}^3, "
+                    f"8-64 particles/cell, alpha U[0.01,0.1], {N:,} particles; {steps} batched "
+                    f"steps captured in one CUDA graph",
+        "value": N * steps / (ms_batch * 1e-3), "unit": UNIT, "ms_per_step": ms_batch / steps,
+        "steps": steps, "warmup": warmup, "generation_s": round(gen_s, 1),
+        "config": {k: list(v) if isinstance(v, tuple) else v for k, v in opts.items()},
+        "per_instance_launches": {"value": N * steps / (ms_single * 1e-3),
+                                  "ms_per_step": ms_single / steps},
+        "per_instance_graphs": {"value": N * steps / (ms_graphs * 1e-3),
+                                "ms_per_step": ms_graphs / steps,
+                                "what": f"one CUDA graph of {steps} steps per instance, the "
                                         f"{len(ws)} graphs replayed in turn"},
         "autotune": tuned,
         "speedup": ms_single / ms_batch,
         "speedup_vs_graphs": ms_graphs / ms_batch,
         "clocks": clk,
+    }
+
+
+def run_ensemble(args):
+    """The batched-ensemble line (`--workload ensemble`)."""
+    from paper_2205_11052_gb300.build import build
+
+    build()
+    m = measure_ensemble(args.ens_count, args.steps, args.warmup, tune=not args.no_tune,
+                         sort_period=args.sort_period, options=args.options)
+    line = {
+        "metric": "ensemble particle-steps/s (batched launch vs one launch sequence per instance)",
+        "value": m["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload=m["workload"], generation_s=m["generation_s"], **m["config"]),
+        **{k: m[k] for k in ("per_instance_launches", "per_instance_graphs", "autotune",
+                             "speedup", "speedup_vs_graphs", "clocks")},
     }
     print(json.dumps(line), flush=True)
 
@@ -903,8 +924,9 @@ def main():
                        "pic_step(1), pic_diagnostics readback"}
 
     # ---- side lines on the same GPU: the FP32 tile-accumulation deposit on
-    # this workload, and the Penning-trap bunch (256^3, 1.3e8 particles)
-    fp32_line = penning_line = None
+    # this workload, the Penning-trap bunch (256^3, 1.3e8 particles) and the
+    # 512-instance batched ensemble
+    fp32_line = penning_line = ens_line = None
     if rank == 0 and world == 1 and not args.no_extras and args.workload == "landau":
         sim.close()
         sim = None
@@ -926,6 +948,9 @@ def main():
                                  "in a Gaussian bunch sigma=(1,1,2), Bz=5, axial frequency 1, "
                                  f"Q=-1562.5, dt=0.05; {args.side_steps} of its 100 steps")
         del wp
+        # the 512-instance batched ensemble, its configured 100 steps in one graph
+        # (the autotuner's setting, fixed), against per-instance launches and graphs
+        ens_line = measure_ensemble(args.ens_count, 100, 3, tune=False)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -960,6 +985,7 @@ def main():
             "rebins": rebins,
             "fp32_deposit": fp32_line,
             "penning": penning_line,
+            "ensemble": ens_line,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "adjoint": adj,
