@@ -48,6 +48,17 @@ __device__ __forceinline__ void weights(float fx, float fy, float fz, float w[8]
     w[6] = x0 * d; w[7] = fx * d;
 }
 
+// CIC weights from per-axis weight pairs (x0, x1) = (1 - fx, fx) etc., with
+// the same products in the same order as weights()
+__device__ __forceinline__ void weights_pairs(float x0, float x1, float y0, float y1, float z0,
+                                              float z1, float w[8]) {
+    const float a = y0 * z0, b = y1 * z0, c = y0 * z1, d = y1 * z1;
+    w[0] = x0 * a; w[1] = x1 * a;
+    w[2] = x0 * b; w[3] = x1 * b;
+    w[4] = x0 * c; w[5] = x1 * c;
+    w[6] = x0 * d; w[7] = x1 * d;
+}
+
 // fixed-point weights: all eight rounded to multiples of 2^-20, then the
 // heaviest corner (weight >= 1/8, picked by which half of the cell each
 // offset lies in) absorbs the rounding remainder, so the corners sum to
@@ -144,33 +155,58 @@ __host__ __device__ __forceinline__ Tile tile_of(const Geom &g, int tile) {
     return t;
 }
 
+// slot of axis index a (0 <= a < n) in the box of the tile with origin o
+// grown by G cells on each side: (a - o + G) mod n, valid below T + 2G (on a
+// periodic axis shorter than the box, slots alias nodes, which the flush maps
+// back to the same node)
+__device__ __forceinline__ int box_slot(int a, int o, int n, int G) {
+    int s = a - o + G;
+    if (s < 0) s += n;
+    if (s >= n) s -= n;
+    return s;
+}
+
 // returns true if the particle went to the shared tile, false if to the grid
 template <bool FIXED>
 __device__ __forceinline__ bool tile_add(uint32_t *acc, const Tile &t, const Geom &g, int i, int j,
                                          int k, float fx, float fy, float fz, float *rho,
                                          unsigned long long *rho64, float qscale) {
-    float w[8];
-    weights(fx, fy, fz, w);
     const int G = g.guard;
-    const int si = tile_slot(i, t.ox, g.n[0], g.tile[0], G);
-    const int sj = tile_slot(j, t.oy, g.n[1], g.tile[1], G);
-    const int sk = tile_slot(k, t.oz, g.n[2], g.tile[2], G);
-    if (si >= 0 && sj >= 0 && sk >= 0) {
+    const int si = box_slot(i, t.ox, g.n[0], G);
+    const int sj = box_slot(j, t.oy, g.n[1], G);
+    const int sk = box_slot(k, t.oz, g.n[2], G);
+    if ((unsigned)si < (unsigned)(t.S0 - 1) && (unsigned)sj < (unsigned)(g.tile[1] + 2 * G) &&
+        (unsigned)sk < (unsigned)(g.tile[2] + 2 * G)) {
         const int s = si + t.S0 * sj + t.S01 * sk;
         const int off[8] = {0, 1, t.S0, t.S0 + 1, t.S01, t.S01 + 1, t.S01 + t.S0,
                             t.S01 + t.S0 + 1};
         if (FIXED) {
+            // the x weights carry the 2^20 fixed-point scale: scaling by a power
+            // of two is exact, so these are bit for bit the scaled weights
+            float w[8];
+            weights_pairs(kFixScale * (1.0f - fx), kFixScale * fx, 1.0f - fy, fy, 1.0f - fz, fz, w);
             uint32_t q[8];
-            fixed_weights(w, fx, fy, fz, q);
+            uint32_t sum = 0;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) atomicAdd(acc + s + off[c], q[c]);
+            for (int c = 0; c < 8; ++c) {
+                q[c] = __float2uint_rn(w[c]);
+                sum += q[c];
+            }
+            const int big = (fx >= 0.5f ? 1 : 0) | (fy >= 0.5f ? 2 : 0) | (fz >= 0.5f ? 4 : 0);
+            const uint32_t adj = kFixOne - sum;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) atomicAdd(acc + s + off[c], q[c] + (c == big ? adj : 0u));
         } else {
+            float w[8];
+            weights(fx, fy, fz, w);
             float *accf = reinterpret_cast<float *>(acc);
 #pragma unroll
             for (int c = 0; c < 8; ++c) atomicAdd(accf + s + off[c], w[c]);
         }
         return true;
     }
+    float w[8];
+    weights(fx, fy, fz, w);
     deposit_global<FIXED>(rho, rho64, g, i, j, k, w, fx, fy, fz, qscale);
     return false;
 }

@@ -281,8 +281,8 @@ __device__ __forceinline__ void pd_one(const Geom &g, const PushConst &pc, const
                                        float &fx, float &fy, float &fz, float &vx, float &vy,
                                        float &vz, int &bad, unsigned long long &strays,
                                        float (&a)[4]) {
-    push_one_pairs<EXT, MAG>(g, pc, E8, c, fx, fy, fz, vx, vy, vz, bad);
-    const int i = cell_i(c), j = cell_j(c), k = cell_k(c);
+    int i, j, k;
+    push_one_pairs<EXT, MAG>(g, pc, E8, c, fx, fy, fz, vx, vy, vz, bad, i, j, k);
     if (sparse) {
         float w[8];
         cic::weights(fx, fy, fz, w);

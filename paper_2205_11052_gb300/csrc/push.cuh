@@ -12,8 +12,8 @@
 
 namespace pic {
 
-__device__ __forceinline__ void advance_cells(const Geom &g, float sx, float sy, float sz, int i,
-                                              int j, int k, int32_t &c, float &fx, float &fy,
+__device__ __forceinline__ void advance_cells(const Geom &g, float sx, float sy, float sz, int &i,
+                                              int &j, int &k, int32_t &c, float &fx, float &fy,
                                               float &fz, int &bad);
 
 // CIC interpolation of the eight corner values (corner bits a | b<<1 | c<<2)
@@ -82,10 +82,10 @@ __device__ __forceinline__ void gather_E_pairs(const Geom &g, const float4 *__re
 
 // Boris kick with the interpolated field (plus the external quadrupole), then
 // a full drift in cell units carried into the cell index and wrapped; (i, j, k)
-// is the particle's stencil base before the step
+// is the particle's stencil base before the step and after it
 template <bool EXT, bool MAG>
 __device__ __forceinline__ void kick_drift(const Geom &g, const PushConst &pc, float ex, float ey,
-                                           float ez, int i, int j, int k, int32_t &c, float &fx,
+                                           float ez, int &i, int &j, int &k, int32_t &c, float &fx,
                                            float &fy, float &fz, float &vx, float &vy, float &vz,
                                            int &bad) {
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -126,9 +126,9 @@ __device__ __forceinline__ void kick_drift(const Geom &g, const PushConst &pc, f
 
 // New in-cell offsets s (in cell units, relative to the stencil base
 // (i, j, k)): carry floor(s) into the cell index, keep the fraction, wrap
-// periodically, repack the cell
-__device__ __forceinline__ void advance_cells(const Geom &g, float sx, float sy, float sz, int i,
-                                              int j, int k, int32_t &c, float &fx, float &fy,
+// periodically, repack the cell; (i, j, k) become the new stencil base
+__device__ __forceinline__ void advance_cells(const Geom &g, float sx, float sy, float sz, int &i,
+                                              int &j, int &k, int32_t &c, float &fx, float &fy,
                                               float &fz, int &bad) {
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     float flx = floorf(sx), fly = floorf(sy), flz = floorf(sz);
@@ -177,17 +177,27 @@ __device__ __forceinline__ void push_one(const Geom &g, const PushConst &pc,
     kick_drift<EXT, MAG>(g, pc, ex, ey, ez, i, j, k, c, fx, fy, fz, vx, vy, vz, bad);
 }
 
-// gather from the x-paired grid + kick + drift
+// gather from the x-paired grid + kick + drift; (i, j, k) receives the new
+// stencil base (the fields of the new packed cell c)
+template <bool EXT, bool MAG>
+__device__ __forceinline__ void push_one_pairs(const Geom &g, const PushConst &pc,
+                                               const float4 *__restrict__ E8, int32_t &c,
+                                               float &fx, float &fy, float &fz, float &vx,
+                                               float &vy, float &vz, int &bad, int &i, int &j,
+                                               int &k) {
+    decode_base(g, c, i, j, k, bad);
+    float ex, ey, ez;
+    gather_E_pairs(g, E8, i, j, k, fx, fy, fz, ex, ey, ez);
+    kick_drift<EXT, MAG>(g, pc, ex, ey, ez, i, j, k, c, fx, fy, fz, vx, vy, vz, bad);
+}
+
 template <bool EXT, bool MAG>
 __device__ __forceinline__ void push_one_pairs(const Geom &g, const PushConst &pc,
                                                const float4 *__restrict__ E8, int32_t &c,
                                                float &fx, float &fy, float &fz, float &vx,
                                                float &vy, float &vz, int &bad) {
     int i, j, k;
-    decode_base(g, c, i, j, k, bad);
-    float ex, ey, ez;
-    gather_E_pairs(g, E8, i, j, k, fx, fy, fz, ex, ey, ez);
-    kick_drift<EXT, MAG>(g, pc, ex, ey, ez, i, j, k, c, fx, fy, fz, vx, vy, vz, bad);
+    push_one_pairs<EXT, MAG>(g, pc, E8, c, fx, fy, fz, vx, vy, vz, bad, i, j, k);
 }
 
 }  // namespace pic
