@@ -36,7 +36,7 @@ namespace {
 using namespace cic;
 
 template <bool FIXED>
-__global__ void __launch_bounds__(256, 3) k_deposit_tiles(Geom g, const Ctrl *__restrict__ ctrl,
+__global__ void __launch_bounds__(256, PIC_DEP_MIN_BLOCKS) k_deposit_tiles(Geom g, const Ctrl *__restrict__ ctrl,
                                                            const int4 *__restrict__ items,
                                                            float qscale, float *rho,
                                                            unsigned long long *rho64, Ctrl *ctrl_w,

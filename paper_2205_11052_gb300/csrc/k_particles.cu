@@ -584,10 +584,26 @@ __global__ void __launch_bounds__(256, PIC_MV_MIN_BLOCKS) k_move_deposit(
             cur_tile = item.x;
             tc = t;
         }
-        for (int p = item.y + threadIdx.x; p < item.z; p += blockDim.x) {
-            int32_t c = __ldcs(ps.cell + p);
-            float fx = __ldcs(ps.o[0] + p), fy = __ldcs(ps.o[1] + p), fz = __ldcs(ps.o[2] + p);
-            move_one(g, seed, n, ps.pid[p], c, fx, fy, fz, bad);
+        // the next particle's streams are loaded before the current one moves
+        int p = item.y + threadIdx.x;
+        int32_t nc = 0, npid = 0;
+        float nfx = 0.f, nfy = 0.f, nfz = 0.f;
+        if (p < item.z) {
+            nc = __ldcs(ps.cell + p);
+            nfx = __ldcs(ps.o[0] + p); nfy = __ldcs(ps.o[1] + p); nfz = __ldcs(ps.o[2] + p);
+            npid = ps.pid[p];
+        }
+        for (; p < item.z; p += blockDim.x) {
+            int32_t c = nc;
+            float fx = nfx, fy = nfy, fz = nfz;
+            const int32_t pid = npid;
+            const int pn = p + (int)blockDim.x;
+            if (pn < item.z) {
+                nc = __ldcs(ps.cell + pn);
+                nfx = __ldcs(ps.o[0] + pn); nfy = __ldcs(ps.o[1] + pn); nfz = __ldcs(ps.o[2] + pn);
+                npid = ps.pid[pn];
+            }
+            move_one(g, seed, n, pid, c, fx, fy, fz, bad);
             const int i = cell_i(c), j = cell_j(c), k = cell_k(c);
             if (sparse) {
                 float w[8];

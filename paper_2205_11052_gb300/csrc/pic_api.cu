@@ -873,7 +873,7 @@ int pic_create(const pic_grid_t *grid, const pic_species_t *species, const pic_p
     c->max_items = c->ntiles + (c->cap + c->chunk - 1) / c->chunk + 1;
     c->staging = std::max<int64_t>(1, std::min<int64_t>(c->cap, (int64_t)1 << 22));
     c->sparse_below = 64;
-    c->deposit_blocks = 152 * 3 * 2;   // two waves of the 3 resident blocks per SM
+    c->deposit_blocks = 152 * PIC_DEP_MIN_BLOCKS * 2;   // two waves of the resident blocks
 
     int m[3] = {p.mode[0], p.mode[1], p.mode[2]};
     c->mode_conj = 0;
