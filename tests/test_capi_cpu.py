@@ -125,7 +125,7 @@ def test_batch_create_validates_and_sizes_without_gpu(lib):
 def test_adjoint_buffer_with_parameter_gradients_without_gpu(lib):
     """PIC_OPT_ADJOINT_PARAMS adds each stored step's velocities (3 arrays per
     step of the reversed segment) and the per-block partials of the parameter
-    sums (10 doubles for each of the 152 * 4 * 2 reverse-push blocks, plus 10)."""
+    sums (10 doubles for each of the 152 * 3 * 2 reverse-push blocks, plus 10)."""
     def align(b):
         return (b + 255) // 256 * 256
 
@@ -134,7 +134,7 @@ def test_adjoint_buffer_with_parameter_gradients_without_gpu(lib):
     b = _create(n_particles=n_p, options=capi.PIC_OPT_ADJOINT_PARAMS)
     sa = capi.pic_adjoint_buffer_bytes(a, n_steps, K)
     sb = capi.pic_adjoint_buffer_bytes(b, n_steps, K)
-    assert sb - sa == K * 3 * align(4 * n_p) + align(8 * 10 * (152 * 4 * 2 + 1))
+    assert sb - sa == K * 3 * align(4 * n_p) + align(8 * 10 * (152 * 3 * 2 + 1))
     with pytest.raises(capi.PicError) as e:
         capi.pic_adjoint_param_gradient(b)
     assert e.value.code == capi.PIC_ERR_STATE
