@@ -166,18 +166,25 @@ __device__ __forceinline__ int box_slot(int a, int o, int n, int G) {
     return s;
 }
 
+// slot s of stencil base (i, j, k) in the box of tile t; true if the whole
+// 2x2x2 stencil lies inside the box
+__device__ __forceinline__ bool box_base(const Tile &t, const Geom &g, int i, int j, int k, int &s) {
+    const int G = g.guard;
+    const int si = box_slot(i, t.ox, g.n[0], G);
+    const int sj = box_slot(j, t.oy, g.n[1], G);
+    const int sk = box_slot(k, t.oz, g.n[2], G);
+    s = si + t.S0 * sj + t.S01 * sk;
+    return (unsigned)si < (unsigned)(t.S0 - 1) && (unsigned)sj < (unsigned)(g.tile[1] + 2 * G) &&
+           (unsigned)sk < (unsigned)(g.tile[2] + 2 * G);
+}
+
 // returns true if the particle went to the shared tile, false if to the grid
 template <bool FIXED>
 __device__ __forceinline__ bool tile_add(uint32_t *acc, const Tile &t, const Geom &g, int i, int j,
                                          int k, float fx, float fy, float fz, float *rho,
                                          unsigned long long *rho64, float qscale) {
-    const int G = g.guard;
-    const int si = box_slot(i, t.ox, g.n[0], G);
-    const int sj = box_slot(j, t.oy, g.n[1], G);
-    const int sk = box_slot(k, t.oz, g.n[2], G);
-    if ((unsigned)si < (unsigned)(t.S0 - 1) && (unsigned)sj < (unsigned)(g.tile[1] + 2 * G) &&
-        (unsigned)sk < (unsigned)(g.tile[2] + 2 * G)) {
-        const int s = si + t.S0 * sj + t.S01 * sk;
+    int s;
+    if (box_base(t, g, i, j, k, s)) {
         const int off[8] = {0, 1, t.S0, t.S0 + 1, t.S01, t.S01 + 1, t.S01 + t.S0,
                             t.S01 + t.S0 + 1};
         if (FIXED) {

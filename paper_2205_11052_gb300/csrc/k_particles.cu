@@ -274,15 +274,27 @@ __global__ void __launch_bounds__(256, 3) k_gather_push(int64_t n, Geom g, PushC
 // it at the end: per step the particle store is read and written once (56
 // bytes per particle) instead of being read again by a separate deposit.
 // ---------------------------------------------------------------------------
+// When the block holds the field of its tile's box in shared memory (sE not
+// null, dense items), E of a particle whose stencil lies in the box is read
+// there (eight 16-byte shared loads, a few wavefronts per warp instead of one
+// L1 wavefront per particle and 32-byte global read); other particles read
+// the x-paired grid.
 template <bool DIAG, bool EXT, bool MAG, bool FIXED>
 __device__ __forceinline__ void pd_one(const Geom &g, const PushConst &pc, const float4 *E8,
-                                       bool sparse, uint32_t *acc, const cic::Tile &t, float *rho,
-                                       unsigned long long *rho64, float qscale, int32_t &c,
-                                       float &fx, float &fy, float &fz, float &vx, float &vy,
-                                       float &vz, int &bad, unsigned long long &strays,
-                                       float (&a)[4]) {
+                                       const float4 *sE, bool sparse, uint32_t *acc,
+                                       const cic::Tile &t, float *rho, unsigned long long *rho64,
+                                       float qscale, int32_t &c, float &fx, float &fy, float &fz,
+                                       float &vx, float &vy, float &vz, int &bad,
+                                       unsigned long long &strays, float (&a)[4]) {
     int i, j, k;
-    push_one_pairs<EXT, MAG>(g, pc, E8, c, fx, fy, fz, vx, vy, vz, bad, i, j, k);
+    decode_base(g, c, i, j, k, bad);
+    float ex, ey, ez;
+    int s0;
+    if (sE != nullptr && cic::box_base(t, g, i, j, k, s0))
+        gather_E_box(sE, s0, t.S0, t.S01, fx, fy, fz, ex, ey, ez);
+    else
+        gather_E_pairs(g, E8, i, j, k, fx, fy, fz, ex, ey, ez);
+    kick_drift<EXT, MAG>(g, pc, ex, ey, ez, i, j, k, c, fx, fy, fz, vx, vy, vz, bad);
     if (sparse) {
         float w[8];
         cic::weights(fx, fy, fz, w);
@@ -298,9 +310,33 @@ __device__ __forceinline__ void pd_one(const Geom &g, const PushConst &pc, const
     }
 }
 
+// the field on the box of tile t (the deposit tile's slots: the tile, G cells
+// on each side and the +1 stencil layer, periodic) into shared memory
+__device__ __forceinline__ void stage_E_box(float4 *sE, const float4 *__restrict__ E4,
+                                            const cic::Tile &t, const Geom &g) {
+    const int G = g.guard;
+    for (int s = threadIdx.x; s < t.S; s += blockDim.x) {
+        int a, b, cz;
+        cic::tile_pos(t, s, a, b, cz);
+        const int gi = cic::wrap_index(t.ox - G + a, g.n[0]);
+        const int gj = cic::wrap_index(t.oy - G + b, g.n[1]);
+        const int gk = cic::wrap_index(t.oz - G + cz, g.n[2]);
+        sE[s] = __ldg(E4 + gi + (int64_t)g.n[0] * (gj + (int64_t)g.n[1] * gk));
+    }
+}
+
+// byte offset of the staged field in the fused kernel's shared memory (after
+// the item tile and the tile sums)
+__host__ __device__ __forceinline__ size_t stage_offset(int S) {
+    return (cic::sum_offset(S) + 8 * (size_t)S + 15) & ~(size_t)15;
+}
+
+// E4 not null: the block copies its tile's box of E4 to shared memory at
+// each change of tile and gathers there (see pd_one)
 template <bool DIAG, bool EXT, bool MAG, bool FIXED>
 __global__ void __launch_bounds__(PIC_PD_THREADS, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g, PushConst pc, Ctrl *ctrl,
                                                           const int4 *__restrict__ items,
+                                                          const float4 *__restrict__ E4,
                                                           const float4 *__restrict__ E8,
                                                           float *rho, unsigned long long *rho64,
                                                           float qscale, int sparse_below,
@@ -318,6 +354,7 @@ __global__ void __launch_bounds__(PIC_PD_THREADS, PIC_PD_MIN_BLOCKS) k_push_depo
     item_run(items, n_items, it0, it1);
     const int S = cic::tile_of(g, 0).S;
     void *sum = reinterpret_cast<char *>(acc) + cic::sum_offset(S);
+    float4 *sE = reinterpret_cast<float4 *>(reinterpret_cast<char *>(acc) + stage_offset(S));
     for (int s = threadIdx.x; s < S; s += blockDim.x) {
         acc[s] = 0u;
         if (FIXED) reinterpret_cast<unsigned long long *>(sum)[s] = 0ull;
@@ -325,16 +362,21 @@ __global__ void __launch_bounds__(PIC_PD_THREADS, PIC_PD_MIN_BLOCKS) k_push_depo
     }
     __syncthreads();
     int cur_tile = -1;
-    cic::Tile tc = cic::tile_of(g, 0);
     for (int it = it0; it < it1; ++it) {
         const int4 item = items[it];
         const bool sparse = item.z - item.y < sparse_below;
         const cic::Tile t = cic::tile_of(g, item.x);
         if (!sparse && item.x != cur_tile) {
-            if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, tc, g, rho, rho64, qscale);
+            if (cur_tile >= 0)
+                cic::tile_flush_sum<FIXED>(sum, cic::tile_of(g, cur_tile), g, rho, rho64, qscale);
             cur_tile = item.x;
-            tc = t;
+            if (E4 != nullptr) {
+                // every read of the previous box ended at the item's last barrier
+                stage_E_box(sE, E4, t, g);
+                __syncthreads();
+            }
         }
+        const float4 *sEi = (E4 != nullptr && !sparse) ? sE : nullptr;
         // one particle per thread and iteration (coalesced 4-byte streams);
         // the next iteration's particle is loaded before this one is pushed
         int p = item.y + threadIdx.x;
@@ -365,8 +407,8 @@ __global__ void __launch_bounds__(PIC_PD_THREADS, PIC_PD_MIN_BLOCKS) k_push_depo
                     __stcs(save.v[2] + p, vz);
                 }
             }
-            pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E8, sparse, acc, t, rho, rho64, qscale, c, fx, fy,
-                                          fz, vx, vy, vz, bad, strays, a);
+            pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E8, sEi, sparse, acc, t, rho, rho64, qscale, c,
+                                          fx, fy, fz, vx, vy, vz, bad, strays, a);
             __stcs(ps.cell + p, c);
             __stcs(ps.o[0] + p, fx);
             __stcs(ps.o[1] + p, fy);
@@ -382,7 +424,7 @@ __global__ void __launch_bounds__(PIC_PD_THREADS, PIC_PD_MIN_BLOCKS) k_push_depo
             __syncthreads();
         }
     }
-    if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, tc, g, rho, rho64, qscale);
+    if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, cic::tile_of(g, cur_tile), g, rho, rho64, qscale);
     if (bad) raise_flag(ctrl, bad);
     if (strays) {
         atomicAdd(&ctrl->stray, strays);
@@ -707,7 +749,23 @@ size_t tile_deposit_smem(const Geom &g) {
     const cic::Tile t0 = cic::tile_of(g, 0);
     return cic::sum_offset(t0.S) + 8 * (size_t)t0.S;
 }
-size_t push_deposit_smem(const Geom &g) { return tile_deposit_smem(g); }
+// staged field: the box's float4 slots after the deposit tiles, if
+// PIC_PD_MIN_BLOCKS such blocks (plus the kernel's static shared memory and
+// the runtime's 1 KiB per block) fit in an SM's 228 KiB
+bool push_stages_E(const Geom &g) {
+#if PIC_PD_STAGE_E
+    const int S = cic::tile_of(g, 0).S;
+    const size_t per_block = stage_offset(S) + 16 * (size_t)S + 256 + 1024;
+    return per_block * PIC_PD_MIN_BLOCKS <= (size_t)228 * 1024;
+#else
+    (void)g;
+    return false;
+#endif
+}
+size_t push_deposit_smem(const Geom &g) {
+    const int S = cic::tile_of(g, 0).S;
+    return push_stages_E(g) ? stage_offset(S) + 16 * (size_t)S : tile_deposit_smem(g);
+}
 
 // Allow the fused kernels' shared memory (call outside any stream capture)
 cudaError_t push_deposit_prepare(const Geom &g) {
@@ -742,20 +800,21 @@ cudaError_t push_deposit_prepare(const Geom &g) {
 }
 
 cudaError_t launch_push_deposit(const Geom &g, const PushConst &pc, bool diag, bool fixed,
-                                Ctrl *ctrl, const int4 *items, int max_items, const float4 *E8,
-                                float *rho, unsigned long long *rho64, double qscale,
-                                int sparse_below, double *part, int blocks, const SaveY &save,
-                                cudaStream_t st) {
+                                Ctrl *ctrl, const int4 *items, int max_items, const float4 *E4,
+                                const float4 *E8, float *rho, unsigned long long *rho64,
+                                double qscale, int sparse_below, double *part, int blocks,
+                                const SaveY &save, cudaStream_t st) {
     const bool ext = pc.wz2 != 0.0f;
     const bool mag = pc.t[0] != 0.0f || pc.t[1] != 0.0f || pc.t[2] != 0.0f;
     const size_t smem = push_deposit_smem(g);
+    const float4 *E4s = push_stages_E(g) ? E4 : nullptr;
     const int nb = std::max(1, std::min(blocks, max_items));
     const float qs = (float)qscale;
     cudaError_t e = cudaSuccess;
 #define PIC_PD(D, X, M, F)                                                                      \
-    k_push_deposit<D, X, M, F><<<nb, PIC_PD_THREADS, smem, st>>>(g, pc, ctrl, items, E8, rho,    \
-                                                                 rho64, qs, sparse_below, part, \
-                                                                 save)
+    k_push_deposit<D, X, M, F><<<nb, PIC_PD_THREADS, smem, st>>>(g, pc, ctrl, items, E4s, E8,    \
+                                                                 rho, rho64, qs, sparse_below,  \
+                                                                 part, save)
 #define PIC_PD_F(D, X, M) \
     do { if (fixed) PIC_PD(D, X, M, true); else PIC_PD(D, X, M, false); } while (0)
     if (diag) {

@@ -421,7 +421,8 @@ int do_push_deposit(pic_ctx *c, bool diag, const SaveY &save = SaveY{}) {
     } else if (c->np > 0) {
         PIC_CUDA(launch_push_deposit(c->geom, push_const(c), diag, fixed, c->ctrl(),
                                      c->at<int4>(c->lay.items), (int)c->max_items,
-                                     c->at<float4>(c->lay.E8), c->at<float>(c->lay.rho),
+                                     c->at<float4>(c->lay.E4), c->at<float4>(c->lay.E8),
+                                     c->at<float>(c->lay.rho),
                                      c->at<unsigned long long>(c->lay.rho64), qscale_of(c),
                                      c->sparse_below, c->at<double>(c->lay.ppart),
                                      fused_blocks_of(c), save, c->st));

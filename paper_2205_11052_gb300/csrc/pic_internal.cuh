@@ -111,6 +111,11 @@ constexpr int kMaxSmemPerBlock = 227 * 1024;   // opt-in shared memory per block
 #ifndef PIC_PD_WAVES
 #define PIC_PD_WAVES 2
 #endif
+// the fused push + deposit gathers E from a shared-memory copy of its tile's
+// box when PIC_PD_MIN_BLOCKS blocks with that copy still fit on an SM
+#ifndef PIC_PD_STAGE_E
+#define PIC_PD_STAGE_E 1
+#endif
 // resident blocks per SM of the uniform-plasma move + deposit
 #ifndef PIC_MV_MIN_BLOCKS
 #define PIC_MV_MIN_BLOCKS 3
@@ -237,8 +242,10 @@ cudaError_t launch_move(int64_t np, const Geom &g, uint64_t seed, bool diag, boo
                         unsigned long long *rho64, double qscale, int sparse_below, double *part,
                         int blocks, cudaStream_t st);
 // dynamic shared memory of the fused push + deposit kernel for geometry g,
-// and the one-time attribute setting it needs above 48 KiB
+// whether it stages E in shared memory, and the one-time attribute setting it
+// needs above 48 KiB
 size_t push_deposit_smem(const Geom &g);
+bool push_stages_E(const Geom &g);
 size_t tile_deposit_smem(const Geom &g);   // the deposit tiles alone (unstaged kernels)
 cudaError_t push_deposit_prepare(const Geom &g);
 // Optional copy of the positions a push starts from (cell, o[3]), written by
@@ -248,10 +255,11 @@ struct SaveY {
     float *o[3];
     float *v[3];   // also the velocities before the kick (null: not saved)
 };
-// E8: the x-paired field (launch_pair_E), 2 float4 per node
+// E4: the field, one float4 per node; E8: the x-paired field (launch_pair_E),
+// 2 float4 per node
 cudaError_t launch_push_deposit(const Geom &g, const PushConst &pc, bool diag, bool fixed,
-                                Ctrl *ctrl, const int4 *items, int max_items, const float4 *E8,
-                                float *rho, unsigned long long *rho64, double qscale,
+                                Ctrl *ctrl, const int4 *items, int max_items, const float4 *E4,
+                                const float4 *E8, float *rho, unsigned long long *rho64, double qscale,
                                 int sparse_below, double *part, int blocks, const SaveY &save,
                                 cudaStream_t st);
 cudaError_t launch_gather_push(int64_t n, const Geom &g, const PushConst &pc, bool diag,

@@ -80,6 +80,24 @@ __device__ __forceinline__ void gather_E_pairs(const Geom &g, const float4 *__re
     interp_E(e, fx, fy, fz, ex, ey, ez);
 }
 
+// E at the particle from a copy of the field on a box in shared memory (one
+// float4 per slot; s0 is the stencil base's slot, rows S0 slots apart in y,
+// planes S01 apart in z)
+__device__ __forceinline__ void gather_E_box(const float4 *sE, int s0, int S0, int S01, float fx,
+                                             float fy, float fz, float &ex, float &ey,
+                                             float &ez) {
+    float4 e[8];
+    e[0] = sE[s0];
+    e[1] = sE[s0 + 1];
+    e[2] = sE[s0 + S0];
+    e[3] = sE[s0 + S0 + 1];
+    e[4] = sE[s0 + S01];
+    e[5] = sE[s0 + S01 + 1];
+    e[6] = sE[s0 + S01 + S0];
+    e[7] = sE[s0 + S01 + S0 + 1];
+    interp_E(e, fx, fy, fz, ex, ey, ez);
+}
+
 // Boris kick with the interpolated field (plus the external quadrupole), then
 // a full drift in cell units carried into the cell index and wrapped; (i, j, k)
 // is the particle's stencil base before the step and after it
