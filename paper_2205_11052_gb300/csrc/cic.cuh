@@ -48,33 +48,36 @@ __device__ __forceinline__ void weights(float fx, float fy, float fz, float w[8]
     w[6] = x0 * d; w[7] = fx * d;
 }
 
-// CIC weights from per-axis weight pairs (x0, x1) = (1 - fx, fx) etc., with
-// the same products in the same order as weights()
-__device__ __forceinline__ void weights_pairs(float x0, float x1, float y0, float y1, float z0,
-                                              float z1, float w[8]) {
-    const float a = y0 * z0, b = y1 * z0, c = y0 * z1, d = y1 * z1;
-    w[0] = x0 * a; w[1] = x1 * a;
-    w[2] = x0 * b; w[3] = x1 * b;
-    w[4] = x0 * c; w[5] = x1 * c;
-    w[6] = x0 * d; w[7] = x1 * d;
-}
-
-// fixed-point weights: all eight rounded to multiples of 2^-20, then the
-// heaviest corner (weight >= 1/8, picked by which half of the cell each
-// offset lies in) absorbs the rounding remainder, so the corners sum to
-// exactly 2^20 and none is negative
-__device__ __forceinline__ void fixed_weights(const float w[8], float fx, float fy, float fz,
-                                              uint32_t q[8]) {
-    uint32_t s = 0;
+// Fixed-point CIC weights by nested splitting: the particle's 2^20 units are
+// split between the two x corners, each x share between its two y corners
+// and each of those between its two z corners.  A split rounds the upper
+// share X f to the nearest integer and gives the lower corner the rest, so
+// the eight integers sum to exactly 2^20, none is negative, and each lies
+// within 1.5 units of 2^20 times the exact weight.  The rounding is FP32's
+// own: X f + 2^23 (one fused multiply-add, X f < 2^23) rounds to an integer
+// held in the mantissa bits, and subtracting 2^23 back is exact.
+__device__ __forceinline__ void fixed_split(float fx, float fy, float fz, uint32_t q[8]) {
+    constexpr float kMagic = 8388608.0f;         // 2^23
+    constexpr uint32_t kMagicBits = 0x4B000000u;  // its bit pattern
+    const float r = fmaf(kFixScale, fx, kMagic);
+    const uint32_t x1 = __float_as_uint(r) - kMagicBits;
+    const float x1f = r - kMagic;
+    const uint32_t xi[2] = {kFixOne - x1, x1};
+    const float xf[2] = {kFixScale - x1f, x1f};
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        q[c] = __float2uint_rn(w[c] * kFixScale);
-        s += q[c];
+    for (int a = 0; a < 2; ++a) {
+        const float ry = fmaf(xf[a], fy, kMagic);
+        const uint32_t y1 = __float_as_uint(ry) - kMagicBits;
+        const float y1f = ry - kMagic;
+        const uint32_t yi[2] = {xi[a] - y1, y1};
+        const float yf[2] = {xf[a] - y1f, y1f};
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const uint32_t z1 = __float_as_uint(fmaf(yf[b], fz, kMagic)) - kMagicBits;
+            q[a | b << 1 | 4] = z1;
+            q[a | b << 1] = yi[b] - z1;
+        }
     }
-    const int big = (fx >= 0.5f ? 1 : 0) | (fy >= 0.5f ? 2 : 0) | (fz >= 0.5f ? 4 : 0);
-    const uint32_t adj = kFixOne - s;   // a few units either way (mod 2^32)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) q[c] += (c == big) ? adj : 0u;
 }
 
 // the eight stencil node indices (periodic)
@@ -99,7 +102,7 @@ __device__ __forceinline__ void deposit_global(float *rho, unsigned long long *r
     nodes(g, i, j, k, nd);
     if (FIXED) {
         uint32_t q[8];
-        fixed_weights(w, fx, fy, fz, q);
+        fixed_split(fx, fy, fz, q);
 #pragma unroll
         for (int c = 0; c < 8; ++c) atomicAdd(rho64 + nd[c], (unsigned long long)q[c]);
     } else {
@@ -188,21 +191,10 @@ __device__ __forceinline__ bool tile_add(uint32_t *acc, const Tile &t, const Geo
         const int off[8] = {0, 1, t.S0, t.S0 + 1, t.S01, t.S01 + 1, t.S01 + t.S0,
                             t.S01 + t.S0 + 1};
         if (FIXED) {
-            // the x weights carry the 2^20 fixed-point scale: scaling by a power
-            // of two is exact, so these are bit for bit the scaled weights
-            float w[8];
-            weights_pairs(kFixScale * (1.0f - fx), kFixScale * fx, 1.0f - fy, fy, 1.0f - fz, fz, w);
             uint32_t q[8];
-            uint32_t sum = 0;
+            fixed_split(fx, fy, fz, q);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                q[c] = __float2uint_rn(w[c]);
-                sum += q[c];
-            }
-            const int big = (fx >= 0.5f ? 1 : 0) | (fy >= 0.5f ? 2 : 0) | (fz >= 0.5f ? 4 : 0);
-            const uint32_t adj = kFixOne - sum;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) atomicAdd(acc + s + off[c], q[c] + (c == big ? adj : 0u));
+            for (int c = 0; c < 8; ++c) atomicAdd(acc + s + off[c], q[c]);
         } else {
             float w[8];
             weights(fx, fy, fz, w);

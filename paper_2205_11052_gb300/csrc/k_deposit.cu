@@ -18,10 +18,10 @@
 //
 // Two accumulators:
 //  * FP32: float shared tile, float global atomics into rho.
-//  * fixed point: each weight rounded to a multiple of 2^-20 (the eight
-//    corners of a particle sum exactly to 2^20, none negative), u32 shared
-//    atomics (at most
-//    4095 particles per work item, so a slot cannot reach 2^32) and u64
+//  * fixed point: the particle's 2^20 units split over its eight corners by
+//    nested rounding (cic::fixed_split: they sum exactly to 2^20, none is
+//    negative), u32 shared atomics (at most 4095 particles per work item, so
+//    a slot cannot reach 2^32) and u64
 //    global atomics into an integer grid that k_rho_finish scales into rho.
 //    Integer addition is associative, so this deposit is deterministic and
 //    conserves the particles' total weight exactly.
@@ -56,8 +56,9 @@ __global__ void __launch_bounds__(256, PIC_DEP_MIN_BLOCKS) k_deposit_tiles(Geom 
         else reinterpret_cast<float *>(sum)[s] = 0.0f;
     }
     __syncthreads();
+    // t: the tile of the dense items (sparse items go straight to the grid)
     int cur_tile = -1;
-    Tile tc = tile_of(g, 0);
+    Tile t = tile_of(g, 0);
     for (int it = it0; it < it1; ++it) {
         const int4 item = items[it];
         if (item.z - item.y < sparse_below) {
@@ -72,11 +73,10 @@ __global__ void __launch_bounds__(256, PIC_DEP_MIN_BLOCKS) k_deposit_tiles(Geom 
             }
             continue;
         }
-        const Tile t = tile_of(g, item.x);
         if (item.x != cur_tile) {
-            if (cur_tile >= 0) tile_flush_sum<FIXED>(sum, tc, g, rho, rho64, qscale);
+            if (cur_tile >= 0) tile_flush_sum<FIXED>(sum, t, g, rho, rho64, qscale);
             cur_tile = item.x;
-            tc = t;
+            t = tile_of(g, item.x);
         }
         int p = item.y + threadIdx.x;
         int32_t nc = 0;
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256, PIC_DEP_MIN_BLOCKS) k_deposit_tiles(Geom 
         tile_fold<FIXED>(acc, sum, S);
         __syncthreads();
     }
-    if (cur_tile >= 0) tile_flush_sum<FIXED>(sum, tc, g, rho, rho64, qscale);
+    if (cur_tile >= 0) tile_flush_sum<FIXED>(sum, t, g, rho, rho64, qscale);
     if (bad) atomicOr(&ctrl_w->flags, PIC_FLAG_BAD_CELL);
     if (strays) atomicAdd(&ctrl_w->stray, strays);
 }

@@ -361,15 +361,16 @@ __global__ void __launch_bounds__(PIC_PD_THREADS, PIC_PD_MIN_BLOCKS) k_push_depo
         else reinterpret_cast<float *>(sum)[s] = 0.0f;
     }
     __syncthreads();
+    // t: the tile of the dense items (sparse items deposit and gather globally)
     int cur_tile = -1;
+    cic::Tile t = cic::tile_of(g, 0);
     for (int it = it0; it < it1; ++it) {
         const int4 item = items[it];
         const bool sparse = item.z - item.y < sparse_below;
-        const cic::Tile t = cic::tile_of(g, item.x);
         if (!sparse && item.x != cur_tile) {
-            if (cur_tile >= 0)
-                cic::tile_flush_sum<FIXED>(sum, cic::tile_of(g, cur_tile), g, rho, rho64, qscale);
+            if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, t, g, rho, rho64, qscale);
             cur_tile = item.x;
+            t = cic::tile_of(g, item.x);
             if (E4 != nullptr) {
                 // every read of the previous box ended at the item's last barrier
                 stage_E_box(sE, E4, t, g);
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(PIC_PD_THREADS, PIC_PD_MIN_BLOCKS) k_push_depo
             __syncthreads();
         }
     }
-    if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, cic::tile_of(g, cur_tile), g, rho, rho64, qscale);
+    if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, t, g, rho, rho64, qscale);
     if (bad) raise_flag(ctrl, bad);
     if (strays) {
         atomicAdd(&ctrl->stray, strays);
@@ -615,16 +616,16 @@ __global__ void __launch_bounds__(256, PIC_MV_MIN_BLOCKS) k_move_deposit(
         else reinterpret_cast<float *>(sum)[s] = 0.0f;
     }
     __syncthreads();
+    // t: the tile of the dense items (sparse items deposit globally)
     int cur_tile = -1;
-    cic::Tile tc = cic::tile_of(g, 0);
+    cic::Tile t = cic::tile_of(g, 0);
     for (int it = it0; it < it1; ++it) {
         const int4 item = items[it];
         const bool sparse = item.z - item.y < sparse_below;
-        const cic::Tile t = cic::tile_of(g, item.x);
         if (!sparse && item.x != cur_tile) {
-            if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, tc, g, rho, rho64, qscale);
+            if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, t, g, rho, rho64, qscale);
             cur_tile = item.x;
-            tc = t;
+            t = cic::tile_of(g, item.x);
         }
         // the next particle's streams are loaded before the current one moves
         int p = item.y + threadIdx.x;
@@ -673,7 +674,7 @@ __global__ void __launch_bounds__(256, PIC_MV_MIN_BLOCKS) k_move_deposit(
             __syncthreads();
         }
     }
-    if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, tc, g, rho, rho64, qscale);
+    if (cur_tile >= 0) cic::tile_flush_sum<FIXED>(sum, t, g, rho, rho64, qscale);
     if (bad) raise_flag(ctrl, bad);
     if (strays) {
         atomicAdd(&ctrl->stray, strays);
