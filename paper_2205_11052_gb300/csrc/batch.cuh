@@ -36,10 +36,17 @@ cudaError_t launch_b_sort(int64_t n, const InstDesc *desc, const long long *p0, 
                           int32_t *tile_items, int2 *tile_range, int4 *items, cudaStream_t st);
 cudaError_t batch_sort_prepare();   // kernel attributes; once per device outside capture
 // shared memory of the batched push + deposit: u32 tile slots + 64-bit per-tile sums
-size_t batch_push_smem(int max_S);
+// dynamic shared memory of the batched push + deposit for tiles of up to
+// max_S slots, without or with (staged) the copy of the field on the box
+size_t batch_push_smem(int max_S, bool staged = false);
+// whether blocks of `threads` threads stage the field: the resident blocks
+// per SM the kernel is sized for still fit with the staged box
+bool batch_stages_E(int max_S, int threads);
+// E4: the field, one float4 per node (null: no staging); E8: its x-paired copy
 cudaError_t launch_b_push_deposit(bool push, bool diag, bool ext, bool mag, bool fixed,
                                   const InstDesc *desc, const int32_t *tile_inst, Ctrl *ctrl,
-                                  const int4 *items, int blocks, int threads, int max_S, const float4 *E8,
+                                  const int4 *items, int blocks, int threads, int max_S,
+                                  const float4 *E4, const float4 *E8,
                                   float *rho, unsigned long long *rho64, int sparse_below,
                                   double *part, cudaStream_t st);
 cudaError_t launch_b_rho_finish(int64_t ng, const InstDesc *desc, const long long *g0, int n_inst,

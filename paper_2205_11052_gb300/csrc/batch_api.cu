@@ -57,6 +57,7 @@ struct pic_batch {
     std::vector<SizeClass> cls;
     int64_t np, ng, nhalf_tot;
     int ntiles, max_items, chunk, sparse_below, fused_blocks, block;
+    bool stage_E;   // the push stages each tile's box of E in shared memory
     int max_S;                 // largest tile (plus guard) of any instance, in nodes
     size_t fft_reserve;
     int64_t staging;
@@ -190,7 +191,9 @@ int b_deposit_pass(pic_batch *b, bool push, bool diag) {
     if (!b_fixed(b)) B_CUDA(cudaMemsetAsync(b->at<float>(b->o_rho), 0, (size_t)b->ng * 4, b->st));
     B_CUDA(launch_b_push_deposit(push, diag, b_ext(b), b_mag(b), b_fixed(b), b->at<InstDesc>(b->o_desc),
                                  b->at<int32_t>(b->o_tinst), b->ctrl(), b->at<int4>(b->o_items),
-                                 b->fused_blocks, b->block, b->max_S, b->at<float4>(b->o_E8),
+                                 b->fused_blocks, b->block, b->max_S,
+                                 b->stage_E ? b->at<float4>(b->o_E4) : nullptr,
+                                 b->at<float4>(b->o_E8),
                                  b->at<float>(b->o_rho), b->at<unsigned long long>(b->o_rho64),
                                  b->sparse_below, b->at<double>(b->o_ppart), b->st));
     if (b_fixed(b))
@@ -390,9 +393,11 @@ int pic_batch_create(const pic_instance_t *inst, int n_inst, double q_over_m,
     }
     // two waves of the blocks that fit on an SM (the kernel's register budget
     // is sized for PIC_BATCH_PD_MIN_BLOCKS blocks of 256 threads)
+    b->stage_E = batch_stages_E(max_S, b->block);
     const int64_t per_sm = std::max<int64_t>(
         1, std::min<int64_t>((int64_t)PIC_BATCH_PD_MIN_BLOCKS * 256 / b->block,
-                             (int64_t)kMaxSmemPerBlock / std::max<size_t>(1, batch_push_smem(max_S))));
+                             (int64_t)kMaxSmemPerBlock /
+                                 std::max<size_t>(1, batch_push_smem(max_S, b->stage_E))));
     b->fused_blocks = (int)std::max<int64_t>(
         1, std::min<int64_t>(b->max_items, (int64_t)kNumSMs * per_sm * 2));
     b->staging = std::max<int64_t>(1, std::min<int64_t>(np, (int64_t)1 << 22));

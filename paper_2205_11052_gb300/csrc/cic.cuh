@@ -275,5 +275,27 @@ __device__ __forceinline__ void tile_flush_sum(void *sum, const Tile &t, const G
 // the two shared tiles of a block: 32-bit item tile, then the 8-byte sums
 __host__ __device__ __forceinline__ size_t sum_offset(int S) { return ((size_t)S * 4 + 7) & ~(size_t)7; }
 
+// Copy of the field (one float4 per node) on the box of tile t -- the deposit
+// tile's slots: the tile, G cells on each side and the +1 stencil layer,
+// periodic -- into shared memory, one slot per thread and iteration.
+__device__ __forceinline__ void stage_box(float4 *sE, const float4 *__restrict__ E4, const Tile &t,
+                                          const Geom &g) {
+    const int G = g.guard;
+    for (int s = threadIdx.x; s < t.S; s += blockDim.x) {
+        int a, b, cz;
+        tile_pos(t, s, a, b, cz);
+        const int gi = wrap_index(t.ox - G + a, g.n[0]);
+        const int gj = wrap_index(t.oy - G + b, g.n[1]);
+        const int gk = wrap_index(t.oz - G + cz, g.n[2]);
+        sE[s] = __ldg(E4 + gi + (int64_t)g.n[0] * (gj + (int64_t)g.n[1] * gk));
+    }
+}
+
+// byte offset of a staged box of S slots in the push kernels' shared memory,
+// after the item tile and the tile sums
+__host__ __device__ __forceinline__ size_t stage_offset(int S) {
+    return (sum_offset(S) + 8 * (size_t)S + 15) & ~(size_t)15;
+}
+
 }  // namespace cic
 }  // namespace pic

@@ -143,11 +143,13 @@ struct BatchKey {
 template <bool PUSH, bool DIAG, bool EXT, bool MAG, bool FIXED>
 __global__ void __launch_bounds__(256, PIC_BATCH_PD_MIN_BLOCKS) k_b_push_deposit(
     const InstDesc *__restrict__ desc, const int32_t *__restrict__ tile_inst, Ctrl *ctrl,
-    const int4 *__restrict__ items, const float4 *__restrict__ E8, float *rho,
-    unsigned long long *rho64, int sparse_below, int max_S, double *__restrict__ part) {
+    const int4 *__restrict__ items, const float4 *__restrict__ E4, const float4 *__restrict__ E8,
+    float *rho, unsigned long long *rho64, int sparse_below, int max_S,
+    double *__restrict__ part) {
     extern __shared__ __align__(16) uint32_t acc[];
     __shared__ double red[4][8];
     void *sum = reinterpret_cast<char *>(acc) + cic::sum_offset(max_S);
+    float4 *sE = reinterpret_cast<float4 *>(reinterpret_cast<char *>(acc) + cic::stage_offset(max_S));
     const ParticleSet ps = ctrl->sets[ctrl->cur];
     const int n_items = ctrl->n_items;
     int it0, it1;
@@ -179,7 +181,13 @@ __global__ void __launch_bounds__(256, PIC_BATCH_PD_MIN_BLOCKS) k_b_push_deposit
             cur_tile = item.x;
             tc = t;
             Dc = &D;
+            if (PUSH && E4 != nullptr) {
+                // every read of the previous box ended at the item's last barrier
+                cic::stage_box(sE, E4 + D.g0, t, g);
+                __syncthreads();
+            }
         }
+        const float4 *sEi = (PUSH && E4 != nullptr && !sparse) ? sE : nullptr;
         float a[4] = {0.f, 0.f, 0.f, 0.f};
         // the next particle's streams are loaded before the current one is pushed
         int p = item.y + threadIdx.x;
@@ -207,9 +215,11 @@ __global__ void __launch_bounds__(256, PIC_BATCH_PD_MIN_BLOCKS) k_b_push_deposit
                     }
                 }
             }
+            int i, j, k;
             if (PUSH) {
                 float vx = cvx, vy = cvy, vz = cvz;
-                push_one_pairs<EXT, MAG>(g, pc, Ei, c, fx, fy, fz, vx, vy, vz, bad);
+                push_one_staged<EXT, MAG>(g, pc, Ei, sEi, t, c, fx, fy, fz, vx, vy, vz, bad, i, j,
+                                          k);
                 __stcs(ps.cell + p, c);
                 __stcs(ps.o[0] + p, fx);
                 __stcs(ps.o[1] + p, fy);
@@ -224,8 +234,7 @@ __global__ void __launch_bounds__(256, PIC_BATCH_PD_MIN_BLOCKS) k_b_push_deposit
                     a[3] += vx * vx + vy * vy + vz * vz;
                 }
             }
-            int i, j, k;
-            if (!cic::decode_cell(c, g, i, j, k)) bad |= PIC_FLAG_BAD_CELL;
+            if (!PUSH && !cic::decode_cell(c, g, i, j, k)) bad |= PIC_FLAG_BAD_CELL;
             if (sparse) {
                 float w[8];
                 cic::weights(fx, fy, fz, w);
@@ -432,15 +441,30 @@ cudaError_t launch_b_sort(int64_t n, const InstDesc *desc, const long long *p0, 
 
 cudaError_t batch_sort_prepare() { return staged_prepare<BatchKey>(); }
 
-size_t batch_push_smem(int max_S) { return cic::sum_offset(max_S) + 8 * (size_t)max_S; }
+size_t batch_push_smem(int max_S, bool staged) {
+    return staged ? cic::stage_offset(max_S) + 16 * (size_t)max_S
+                  : cic::sum_offset(max_S) + 8 * (size_t)max_S;
+}
+
+bool batch_stages_E(int max_S, int threads) {
+#if PIC_PD_STAGE_E
+    const int64_t per_sm = std::max(1, PIC_BATCH_PD_MIN_BLOCKS * 256 / std::max(1, threads));
+    const size_t per_block = batch_push_smem(max_S, true) + 256 + 1024;
+    return (size_t)per_sm * per_block <= (size_t)228 * 1024;
+#else
+    (void)max_S;
+    (void)threads;
+    return false;
+#endif
+}
 
 cudaError_t launch_b_push_deposit(bool push, bool diag, bool ext, bool mag, bool fixed,
                                   const InstDesc *desc, const int32_t *tile_inst, Ctrl *ctrl,
                                   const int4 *items, int blocks, int threads, int max_S,
-                                  const float4 *E8,
+                                  const float4 *E4, const float4 *E8,
                                   float *rho, unsigned long long *rho64, int sparse_below,
                                   double *part, cudaStream_t st) {
-    const size_t smem = batch_push_smem(max_S);
+    const size_t smem = batch_push_smem(max_S, E4 != nullptr && push);
     cudaError_t e = cudaSuccess;
 #define PIC_BPD(P, D, X, M, F)                                                                  \
     do {                                                                                        \
@@ -449,8 +473,8 @@ cudaError_t launch_b_push_deposit(bool push, bool diag, bool ext, bool mag, bool
             (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                                       (int)smem)) != cudaSuccess)                               \
             return e;                                                                           \
-        kern<<<blocks, threads, smem, st>>>(desc, tile_inst, ctrl, items, E8, rho, rho64,      \
-                                        sparse_below, max_S, part);                             \
+        kern<<<blocks, threads, smem, st>>>(desc, tile_inst, ctrl, items, push ? E4 : nullptr, \
+                                            E8, rho, rho64, sparse_below, max_S, part);         \
     } while (0)
 #define PIC_BPD_F(P, D, X, M) \
     do { if (fixed) PIC_BPD(P, D, X, M, true); else PIC_BPD(P, D, X, M, false); } while (0)

@@ -274,11 +274,8 @@ __global__ void __launch_bounds__(256, 3) k_gather_push(int64_t n, Geom g, PushC
 // it at the end: per step the particle store is read and written once (56
 // bytes per particle) instead of being read again by a separate deposit.
 // ---------------------------------------------------------------------------
-// When the block holds the field of its tile's box in shared memory (sE not
-// null, dense items), E of a particle whose stencil lies in the box is read
-// there (eight 16-byte shared loads, a few wavefronts per warp instead of one
-// L1 wavefront per particle and 32-byte global read); other particles read
-// the x-paired grid.
+// E from the block's shared copy of its tile's box when it holds one (see
+// push_one_staged), else from the x-paired grid.
 template <bool DIAG, bool EXT, bool MAG, bool FIXED>
 __device__ __forceinline__ void pd_one(const Geom &g, const PushConst &pc, const float4 *E8,
                                        const float4 *sE, bool sparse, uint32_t *acc,
@@ -287,14 +284,7 @@ __device__ __forceinline__ void pd_one(const Geom &g, const PushConst &pc, const
                                        float &vx, float &vy, float &vz, int &bad,
                                        unsigned long long &strays, float (&a)[4]) {
     int i, j, k;
-    decode_base(g, c, i, j, k, bad);
-    float ex, ey, ez;
-    int s0;
-    if (sE != nullptr && cic::box_base(t, g, i, j, k, s0))
-        gather_E_box(sE, s0, t.S0, t.S01, fx, fy, fz, ex, ey, ez);
-    else
-        gather_E_pairs(g, E8, i, j, k, fx, fy, fz, ex, ey, ez);
-    kick_drift<EXT, MAG>(g, pc, ex, ey, ez, i, j, k, c, fx, fy, fz, vx, vy, vz, bad);
+    push_one_staged<EXT, MAG>(g, pc, E8, sE, t, c, fx, fy, fz, vx, vy, vz, bad, i, j, k);
     if (sparse) {
         float w[8];
         cic::weights(fx, fy, fz, w);
@@ -308,27 +298,6 @@ __device__ __forceinline__ void pd_one(const Geom &g, const PushConst &pc, const
         a[2] += vz;
         a[3] += vx * vx + vy * vy + vz * vz;
     }
-}
-
-// the field on the box of tile t (the deposit tile's slots: the tile, G cells
-// on each side and the +1 stencil layer, periodic) into shared memory
-__device__ __forceinline__ void stage_E_box(float4 *sE, const float4 *__restrict__ E4,
-                                            const cic::Tile &t, const Geom &g) {
-    const int G = g.guard;
-    for (int s = threadIdx.x; s < t.S; s += blockDim.x) {
-        int a, b, cz;
-        cic::tile_pos(t, s, a, b, cz);
-        const int gi = cic::wrap_index(t.ox - G + a, g.n[0]);
-        const int gj = cic::wrap_index(t.oy - G + b, g.n[1]);
-        const int gk = cic::wrap_index(t.oz - G + cz, g.n[2]);
-        sE[s] = __ldg(E4 + gi + (int64_t)g.n[0] * (gj + (int64_t)g.n[1] * gk));
-    }
-}
-
-// byte offset of the staged field in the fused kernel's shared memory (after
-// the item tile and the tile sums)
-__host__ __device__ __forceinline__ size_t stage_offset(int S) {
-    return (cic::sum_offset(S) + 8 * (size_t)S + 15) & ~(size_t)15;
 }
 
 // E4 not null: the block copies its tile's box of E4 to shared memory at
@@ -354,7 +323,7 @@ __global__ void __launch_bounds__(PIC_PD_THREADS, PIC_PD_MIN_BLOCKS) k_push_depo
     item_run(items, n_items, it0, it1);
     const int S = cic::tile_of(g, 0).S;
     void *sum = reinterpret_cast<char *>(acc) + cic::sum_offset(S);
-    float4 *sE = reinterpret_cast<float4 *>(reinterpret_cast<char *>(acc) + stage_offset(S));
+    float4 *sE = reinterpret_cast<float4 *>(reinterpret_cast<char *>(acc) + cic::stage_offset(S));
     for (int s = threadIdx.x; s < S; s += blockDim.x) {
         acc[s] = 0u;
         if (FIXED) reinterpret_cast<unsigned long long *>(sum)[s] = 0ull;
@@ -373,7 +342,7 @@ __global__ void __launch_bounds__(PIC_PD_THREADS, PIC_PD_MIN_BLOCKS) k_push_depo
             t = cic::tile_of(g, item.x);
             if (E4 != nullptr) {
                 // every read of the previous box ended at the item's last barrier
-                stage_E_box(sE, E4, t, g);
+                cic::stage_box(sE, E4, t, g);
                 __syncthreads();
             }
         }
@@ -756,7 +725,7 @@ size_t tile_deposit_smem(const Geom &g) {
 bool push_stages_E(const Geom &g) {
 #if PIC_PD_STAGE_E
     const int S = cic::tile_of(g, 0).S;
-    const size_t per_block = stage_offset(S) + 16 * (size_t)S + 256 + 1024;
+    const size_t per_block = cic::stage_offset(S) + 16 * (size_t)S + 256 + 1024;
     return per_block * PIC_PD_MIN_BLOCKS <= (size_t)228 * 1024;
 #else
     (void)g;
@@ -765,7 +734,7 @@ bool push_stages_E(const Geom &g) {
 }
 size_t push_deposit_smem(const Geom &g) {
     const int S = cic::tile_of(g, 0).S;
-    return push_stages_E(g) ? stage_offset(S) + 16 * (size_t)S : tile_deposit_smem(g);
+    return push_stages_E(g) ? cic::stage_offset(S) + 16 * (size_t)S : tile_deposit_smem(g);
 }
 
 // Allow the fused kernels' shared memory (call outside any stream capture)

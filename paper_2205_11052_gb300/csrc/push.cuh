@@ -8,6 +8,7 @@
 // step in cell units, carried into the cell index and wrapped periodically.
 #pragma once
 
+#include "cic.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -216,6 +217,28 @@ __device__ __forceinline__ void push_one_pairs(const Geom &g, const PushConst &p
                                                float &vy, float &vz, int &bad) {
     int i, j, k;
     push_one_pairs<EXT, MAG>(g, pc, E8, c, fx, fy, fz, vx, vy, vz, bad, i, j, k);
+}
+
+// Gather + kick + drift with E read from sE, the block's shared-memory copy
+// of the box of tile t (cic::stage_box), when the particle's stencil lies in
+// that box: eight 16-byte shared loads, a few shared wavefronts per warp
+// instead of one L1 wavefront per particle and 32-byte global read.  Other
+// particles, and every particle when sE is null, read the x-paired grid E8.
+// (i, j, k) receives the new stencil base.
+template <bool EXT, bool MAG>
+__device__ __forceinline__ void push_one_staged(const Geom &g, const PushConst &pc,
+                                                const float4 *__restrict__ E8, const float4 *sE,
+                                                const cic::Tile &t, int32_t &c, float &fx,
+                                                float &fy, float &fz, float &vx, float &vy,
+                                                float &vz, int &bad, int &i, int &j, int &k) {
+    decode_base(g, c, i, j, k, bad);
+    float ex, ey, ez;
+    int s0;
+    if (sE != nullptr && cic::box_base(t, g, i, j, k, s0))
+        gather_E_box(sE, s0, t.S0, t.S01, fx, fy, fz, ex, ey, ez);
+    else
+        gather_E_pairs(g, E8, i, j, k, fx, fy, fz, ex, ey, ez);
+    kick_drift<EXT, MAG>(g, pc, ex, ey, ez, i, j, k, c, fx, fy, fz, vx, vy, vz, bad);
 }
 
 }  // namespace pic
