@@ -53,13 +53,13 @@ __device__ __forceinline__ int table_slot(int32_t *hkey, int key, int size) {
 }
 
 #ifndef PIC_SORT_STAGE
-#define PIC_SORT_STAGE 512
+#define PIC_SORT_STAGE 1024
 #endif
 constexpr int kStage = PIC_SORT_STAGE;     // particles per staged slice
 constexpr int kHash = 256;                 // slots of the per-slice tile table
 constexpr int kPerThread = kStage / 256;   // the staged kernels run 256 threads per block
 #ifndef PIC_HIST_STAGE
-#define PIC_HIST_STAGE 2048
+#define PIC_HIST_STAGE 4096
 #endif
 constexpr int kHistStage = PIC_HIST_STAGE;   // particles per histogram slice
 constexpr int kHistPer = kHistStage / 256;
@@ -77,7 +77,7 @@ constexpr int kHistPer = kHistStage / 256;
 // particles in arbitrary order) falls back to per-warp claims.
 //
 // The slices a block walks are double-buffered: while one is processed, the
-// eight arrays of its next slice arrive by bulk asynchronous copies (2 KB
+// eight arrays of its next slice arrive by bulk asynchronous copies (4 KB
 // each, completion counted on an mbarrier); a partial last slice is loaded
 // with plain loads.  Every wait is bounded: a copy that never completes
 // raises PIC_FLAG_TIMEOUT and the block stops.
