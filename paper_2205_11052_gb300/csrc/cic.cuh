@@ -169,27 +169,38 @@ __device__ __forceinline__ int box_slot(int a, int o, int n, int G) {
     return s;
 }
 
+// Box extents: B > 0 says the box is B slots long on every axis (a constant
+// of the kernel, so slot offsets become immediates); B = 0 reads them from t.
+template <int B>
+__device__ __forceinline__ int box_row(const Tile &t) { return B > 0 ? B : t.S0; }
+template <int B>
+__device__ __forceinline__ int box_plane(const Tile &t) { return B > 0 ? B * B : t.S01; }
+
 // slot s of stencil base (i, j, k) in the box of tile t; true if the whole
 // 2x2x2 stencil lies inside the box
+template <int B = 0>
 __device__ __forceinline__ bool box_base(const Tile &t, const Geom &g, int i, int j, int k, int &s) {
     const int G = g.guard;
     const int si = box_slot(i, t.ox, g.n[0], G);
     const int sj = box_slot(j, t.oy, g.n[1], G);
     const int sk = box_slot(k, t.oz, g.n[2], G);
-    s = si + t.S0 * sj + t.S01 * sk;
+    s = si + box_row<B>(t) * sj + box_plane<B>(t) * sk;
+    if (B > 0)
+        return (unsigned)si < (unsigned)(B - 1) && (unsigned)sj < (unsigned)(B - 1) &&
+               (unsigned)sk < (unsigned)(B - 1);
     return (unsigned)si < (unsigned)(t.S0 - 1) && (unsigned)sj < (unsigned)(g.tile[1] + 2 * G) &&
            (unsigned)sk < (unsigned)(g.tile[2] + 2 * G);
 }
 
 // returns true if the particle went to the shared tile, false if to the grid
-template <bool FIXED>
+template <bool FIXED, int B = 0>
 __device__ __forceinline__ bool tile_add(uint32_t *acc, const Tile &t, const Geom &g, int i, int j,
                                          int k, float fx, float fy, float fz, float *rho,
                                          unsigned long long *rho64, float qscale) {
     int s;
-    if (box_base(t, g, i, j, k, s)) {
-        const int off[8] = {0, 1, t.S0, t.S0 + 1, t.S01, t.S01 + 1, t.S01 + t.S0,
-                            t.S01 + t.S0 + 1};
+    if (box_base<B>(t, g, i, j, k, s)) {
+        const int S0 = box_row<B>(t), S01 = box_plane<B>(t);
+        const int off[8] = {0, 1, S0, S0 + 1, S01, S01 + 1, S01 + S0, S01 + S0 + 1};
         if (FIXED) {
             uint32_t q[8];
             fixed_split(fx, fy, fz, q);

@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256, 3) k_gather_push(int64_t n, Geom g, PushC
 // ---------------------------------------------------------------------------
 // E from the block's shared copy of its tile's box when it holds one (see
 // push_one_staged), else from the x-paired grid.
-template <bool DIAG, bool EXT, bool MAG, bool FIXED>
+template <bool DIAG, bool EXT, bool MAG, bool FIXED, int B>
 __device__ __forceinline__ void pd_one(const Geom &g, const PushConst &pc, const float4 *E8,
                                        const float4 *sE, bool sparse, uint32_t *acc,
                                        const cic::Tile &t, float *rho, unsigned long long *rho64,
@@ -284,12 +284,12 @@ __device__ __forceinline__ void pd_one(const Geom &g, const PushConst &pc, const
                                        float &vx, float &vy, float &vz, int &bad,
                                        unsigned long long &strays, float (&a)[4]) {
     int i, j, k;
-    push_one_staged<EXT, MAG>(g, pc, E8, sE, t, c, fx, fy, fz, vx, vy, vz, bad, i, j, k);
+    push_one_staged<EXT, MAG, B>(g, pc, E8, sE, t, c, fx, fy, fz, vx, vy, vz, bad, i, j, k);
     if (sparse) {
         float w[8];
         cic::weights(fx, fy, fz, w);
         cic::deposit_global<FIXED>(rho, rho64, g, i, j, k, w, fx, fy, fz, qscale);
-    } else if (!cic::tile_add<FIXED>(acc, t, g, i, j, k, fx, fy, fz, rho, rho64, qscale)) {
+    } else if (!cic::tile_add<FIXED, B>(acc, t, g, i, j, k, fx, fy, fz, rho, rho64, qscale)) {
         ++strays;
     }
     if (DIAG) {
@@ -301,8 +301,9 @@ __device__ __forceinline__ void pd_one(const Geom &g, const PushConst &pc, const
 }
 
 // E4 not null: the block copies its tile's box of E4 to shared memory at
-// each change of tile and gathers there (see pd_one)
-template <bool DIAG, bool EXT, bool MAG, bool FIXED>
+// each change of tile and gathers there (see pd_one).  B > 0: every tile box
+// is B slots long on each axis (see cic::box_row).
+template <bool DIAG, bool EXT, bool MAG, bool FIXED, int B>
 __global__ void __launch_bounds__(PIC_PD_THREADS, PIC_PD_MIN_BLOCKS) k_push_deposit(Geom g, PushConst pc, Ctrl *ctrl,
                                                           const int4 *__restrict__ items,
                                                           const float4 *__restrict__ E4,
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(PIC_PD_THREADS, PIC_PD_MIN_BLOCKS) k_push_depo
                     __stcs(save.v[2] + p, vz);
                 }
             }
-            pd_one<DIAG, EXT, MAG, FIXED>(g, pc, E8, sEi, sparse, acc, t, rho, rho64, qscale, c,
+            pd_one<DIAG, EXT, MAG, FIXED, B>(g, pc, E8, sEi, sparse, acc, t, rho, rho64, qscale, c,
                                           fx, fy, fz, vx, vy, vz, bad, strays, a);
             __stcs(ps.cell + p, c);
             __stcs(ps.o[0] + p, fx);
@@ -737,6 +738,15 @@ size_t push_deposit_smem(const Geom &g) {
     return push_stages_E(g) ? cic::stage_offset(S) + 16 * (size_t)S : tile_deposit_smem(g);
 }
 
+// the box edge compiled as a constant into the fixed-point push: 8^3 tiles
+// with two guard layers (the default geometry)
+constexpr int kConstBox = 13;
+bool const_box(const Geom &g) {
+    for (int d = 0; d < 3; ++d)
+        if (g.tile[d] + 2 * g.guard + 1 != kConstBox) return false;
+    return true;
+}
+
 // Allow the fused kernels' shared memory (call outside any stream capture)
 cudaError_t push_deposit_prepare(const Geom &g) {
     cudaError_t e = cudaSuccess;
@@ -752,19 +762,18 @@ cudaError_t push_deposit_prepare(const Geom &g) {
     }
     const size_t smem = push_deposit_smem(g);
     if (smem <= 48 * 1024) return cudaSuccess;
-#define PIC_PDA(D, X, M, F)                                                                   \
-    if ((e = cudaFuncSetAttribute(k_push_deposit<D, X, M, F>,                                 \
+#define PIC_PDA(D, X, M, F, B)                                                                \
+    if ((e = cudaFuncSetAttribute(k_push_deposit<D, X, M, F, B>,                              \
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != \
         cudaSuccess)                                                                          \
         return e
-    PIC_PDA(false, false, false, false); PIC_PDA(false, false, false, true);
-    PIC_PDA(false, false, true, false);  PIC_PDA(false, false, true, true);
-    PIC_PDA(false, true, false, false);  PIC_PDA(false, true, false, true);
-    PIC_PDA(false, true, true, false);   PIC_PDA(false, true, true, true);
-    PIC_PDA(true, false, false, false);  PIC_PDA(true, false, false, true);
-    PIC_PDA(true, false, true, false);   PIC_PDA(true, false, true, true);
-    PIC_PDA(true, true, false, false);   PIC_PDA(true, true, false, true);
-    PIC_PDA(true, true, true, false);    PIC_PDA(true, true, true, true);
+#define PIC_PDA2(D, X, M) \
+    PIC_PDA(D, X, M, false, 0); PIC_PDA(D, X, M, true, 0); PIC_PDA(D, X, M, true, kConstBox)
+    PIC_PDA2(false, false, false); PIC_PDA2(false, false, true);
+    PIC_PDA2(false, true, false);  PIC_PDA2(false, true, true);
+    PIC_PDA2(true, false, false);  PIC_PDA2(true, false, true);
+    PIC_PDA2(true, true, false);   PIC_PDA2(true, true, true);
+#undef PIC_PDA2
 #undef PIC_PDA
     return cudaSuccess;
 }
@@ -781,12 +790,17 @@ cudaError_t launch_push_deposit(const Geom &g, const PushConst &pc, bool diag, b
     const int nb = std::max(1, std::min(blocks, max_items));
     const float qs = (float)qscale;
     cudaError_t e = cudaSuccess;
-#define PIC_PD(D, X, M, F)                                                                      \
-    k_push_deposit<D, X, M, F><<<nb, PIC_PD_THREADS, smem, st>>>(g, pc, ctrl, items, E4s, E8,    \
-                                                                 rho, rho64, qs, sparse_below,  \
-                                                                 part, save)
-#define PIC_PD_F(D, X, M) \
-    do { if (fixed) PIC_PD(D, X, M, true); else PIC_PD(D, X, M, false); } while (0)
+    const bool cbox = const_box(g);
+#define PIC_PD(D, X, M, F, B)                                                                   \
+    k_push_deposit<D, X, M, F, B><<<nb, PIC_PD_THREADS, smem, st>>>(g, pc, ctrl, items, E4s, E8, \
+                                                                    rho, rho64, qs,             \
+                                                                    sparse_below, part, save)
+#define PIC_PD_F(D, X, M)                                  \
+    do {                                                   \
+        if (!fixed) PIC_PD(D, X, M, false, 0);             \
+        else if (cbox) PIC_PD(D, X, M, true, kConstBox);   \
+        else PIC_PD(D, X, M, true, 0);                     \
+    } while (0)
     if (diag) {
         if (ext) { if (mag) PIC_PD_F(true, true, true); else PIC_PD_F(true, true, false); }
         else     { if (mag) PIC_PD_F(true, false, true); else PIC_PD_F(true, false, false); }

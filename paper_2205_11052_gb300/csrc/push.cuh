@@ -84,9 +84,11 @@ __device__ __forceinline__ void gather_E_pairs(const Geom &g, const float4 *__re
 // E at the particle from a copy of the field on a box in shared memory (one
 // float4 per slot; s0 is the stencil base's slot, rows S0 slots apart in y,
 // planes S01 apart in z)
-__device__ __forceinline__ void gather_E_box(const float4 *sE, int s0, int S0, int S01, float fx,
+template <int B = 0>
+__device__ __forceinline__ void gather_E_box(const float4 *sE, int s0, int S0r, int S01r, float fx,
                                              float fy, float fz, float &ex, float &ey,
                                              float &ez) {
+    const int S0 = B > 0 ? B : S0r, S01 = B > 0 ? B * B : S01r;   // B > 0: a constant box
     float4 e[8];
     e[0] = sE[s0];
     e[1] = sE[s0 + 1];
@@ -225,7 +227,7 @@ __device__ __forceinline__ void push_one_pairs(const Geom &g, const PushConst &p
 // instead of one L1 wavefront per particle and 32-byte global read.  Other
 // particles, and every particle when sE is null, read the x-paired grid E8.
 // (i, j, k) receives the new stencil base.
-template <bool EXT, bool MAG>
+template <bool EXT, bool MAG, int B = 0>
 __device__ __forceinline__ void push_one_staged(const Geom &g, const PushConst &pc,
                                                 const float4 *__restrict__ E8, const float4 *sE,
                                                 const cic::Tile &t, int32_t &c, float &fx,
@@ -234,8 +236,8 @@ __device__ __forceinline__ void push_one_staged(const Geom &g, const PushConst &
     decode_base(g, c, i, j, k, bad);
     float ex, ey, ez;
     int s0;
-    if (sE != nullptr && cic::box_base(t, g, i, j, k, s0))
-        gather_E_box(sE, s0, t.S0, t.S01, fx, fy, fz, ex, ey, ez);
+    if (sE != nullptr && cic::box_base<B>(t, g, i, j, k, s0))
+        gather_E_box<B>(sE, s0, t.S0, t.S01, fx, fy, fz, ex, ey, ez);
     else
         gather_E_pairs(g, E8, i, j, k, fx, fy, fz, ex, ey, ez);
     kick_drift<EXT, MAG>(g, pc, ex, ey, ez, i, j, k, c, fx, fy, fz, vx, vy, vz, bad);
