@@ -563,8 +563,9 @@ __device__ __forceinline__ void block_moments(const double (&d)[4], double *part
 }
 
 // the random move of every particle with the deposit of the new positions
-// (the work items and shared tiles of k_push_deposit); velocities untouched
-template <bool DIAG, bool FIXED>
+// (the work items and shared tiles of k_push_deposit); velocities untouched.
+// B > 0: every tile box is B slots long on each axis (see cic::box_row).
+template <bool DIAG, bool FIXED, int B>
 __global__ void __launch_bounds__(256, PIC_MV_MIN_BLOCKS) k_move_deposit(
     Geom g, uint64_t seed, Ctrl *ctrl, const int4 *__restrict__ items, float *rho,
     unsigned long long *rho64, float qscale, int sparse_below, double *__restrict__ part) {
@@ -622,7 +623,7 @@ __global__ void __launch_bounds__(256, PIC_MV_MIN_BLOCKS) k_move_deposit(
                 float w[8];
                 cic::weights(fx, fy, fz, w);
                 cic::deposit_global<FIXED>(rho, rho64, g, i, j, k, w, fx, fy, fz, qscale);
-            } else if (!cic::tile_add<FIXED>(acc, t, g, i, j, k, fx, fy, fz, rho, rho64, qscale)) {
+            } else if (!cic::tile_add<FIXED, B>(acc, t, g, i, j, k, fx, fy, fz, rho, rho64, qscale)) {
                 ++strays;
             }
             if (DIAG) {
@@ -689,6 +690,15 @@ __global__ void k_step_inc(Ctrl *ctrl) {
     ctrl->since_sort += 1;
 }
 
+// the box edge compiled as a constant into the fixed-point push and move:
+// 8^3 tiles with two guard layers (the default geometry)
+constexpr int kConstBox = 13;
+bool const_box(const Geom &g) {
+    for (int d = 0; d < 3; ++d)
+        if (g.tile[d] + 2 * g.guard + 1 != kConstBox) return false;
+    return true;
+}
+
 cudaError_t launch_move(int64_t np, const Geom &g, uint64_t seed, bool diag, bool fixed, bool deposit,
                         Ctrl *ctrl, const int4 *items, int max_items, float *rho,
                         unsigned long long *rho64, double qscale, int sparse_below, double *part,
@@ -697,13 +707,19 @@ cudaError_t launch_move(int64_t np, const Geom &g, uint64_t seed, bool diag, boo
     if (deposit) {
         const size_t smem = tile_deposit_smem(g);
         const float qs = (float)qscale;
+        const bool cbox = const_box(g);
+#define PIC_MV(D, F, B) \
+    k_move_deposit<D, F, B><<<nb, 256, smem, st>>>(g, seed, ctrl, items, rho, rho64, qs, sparse_below, part)
         if (diag) {
-            if (fixed) k_move_deposit<true, true><<<nb, 256, smem, st>>>(g, seed, ctrl, items, rho, rho64, qs, sparse_below, part);
-            else k_move_deposit<true, false><<<nb, 256, smem, st>>>(g, seed, ctrl, items, rho, rho64, qs, sparse_below, part);
+            if (!fixed) PIC_MV(true, false, 0);
+            else if (cbox) PIC_MV(true, true, kConstBox);
+            else PIC_MV(true, true, 0);
         } else {
-            if (fixed) k_move_deposit<false, true><<<nb, 256, smem, st>>>(g, seed, ctrl, items, rho, rho64, qs, sparse_below, part);
-            else k_move_deposit<false, false><<<nb, 256, smem, st>>>(g, seed, ctrl, items, rho, rho64, qs, sparse_below, part);
+            if (!fixed) PIC_MV(false, false, 0);
+            else if (cbox) PIC_MV(false, true, kConstBox);
+            else PIC_MV(false, true, 0);
         }
+#undef PIC_MV
     } else {
         if (diag) k_move<true><<<nb, 256, 0, st>>>(np, g, seed, ctrl, part);
         else k_move<false><<<nb, 256, 0, st>>>(np, g, seed, ctrl, part);
@@ -738,26 +754,18 @@ size_t push_deposit_smem(const Geom &g) {
     return push_stages_E(g) ? cic::stage_offset(S) + 16 * (size_t)S : tile_deposit_smem(g);
 }
 
-// the box edge compiled as a constant into the fixed-point push: 8^3 tiles
-// with two guard layers (the default geometry)
-constexpr int kConstBox = 13;
-bool const_box(const Geom &g) {
-    for (int d = 0; d < 3; ++d)
-        if (g.tile[d] + 2 * g.guard + 1 != kConstBox) return false;
-    return true;
-}
-
 // Allow the fused kernels' shared memory (call outside any stream capture)
 cudaError_t push_deposit_prepare(const Geom &g) {
     cudaError_t e = cudaSuccess;
     const size_t tsm = tile_deposit_smem(g);
     if (tsm > 48 * 1024) {
-#define PIC_MVA(D, F)                                                                          \
-        if ((e = cudaFuncSetAttribute(k_move_deposit<D, F>,                                     \
+#define PIC_MVA(D, F, B)                                                                       \
+        if ((e = cudaFuncSetAttribute(k_move_deposit<D, F, B>,                                  \
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)) != \
             cudaSuccess)                                                                        \
             return e
-        PIC_MVA(false, false); PIC_MVA(false, true); PIC_MVA(true, false); PIC_MVA(true, true);
+        PIC_MVA(false, false, 0); PIC_MVA(false, true, 0); PIC_MVA(true, false, 0);
+        PIC_MVA(true, true, 0); PIC_MVA(false, true, kConstBox); PIC_MVA(true, true, kConstBox);
 #undef PIC_MVA
     }
     const size_t smem = push_deposit_smem(g);
