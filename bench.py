@@ -61,6 +61,8 @@ def parse():
                          "0.5 h_min, i.e. 0.005 for its finest mesh)")
     ap.add_argument("--guard", type=int, default=None,
                     help="deposit tile guard layers (default 2; 3 for the Penning bunch)")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="deposit / binning tile edge in cells (default 8)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=1 << 21,
                     help="particles in the oracle's bounded sample")
@@ -819,7 +821,7 @@ def main():
     ng = args.grid ** 3
     sim = Simulation.from_workload(w, sort_period=args.sort_period, options=options,
                                    diag_every=args.diag_every, guard=args.guard, seed=2022 + rank,
-                                   stray_rebin=args.stray_rebin)
+                                   stray_rebin=args.stray_rebin, tile=(args.tile,) * 3)
     stream = sim.stream
 
     def barrier():
@@ -880,7 +882,8 @@ def main():
             ent = tj.get(kernel_names[dom])
             # the record is for the 128^3 x 64 workload in the default launch configuration
             same = (args.workload, args.grid, args.ppc, args.sort_period, args.options, args.guard,
-                    args.dt) == ("landau", 128, 64, LAUNCH["sort_period"], LAUNCH["options"], 0, 0.05)
+                    args.dt, args.tile) == ("landau", 128, 64, LAUNCH["sort_period"],
+                                            LAUNCH["options"], 0, 0.05, 0)
             if same and ent and ent.get("source_sha") == _source_sha(ent.get("source")):
                 traffic = ent["bytes_per_launch_full_size"]
         except Exception:
@@ -974,6 +977,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": workload_name(args), "n_particles": N,
                        "grid": [args.grid] * 3, "sort_period": args.sort_period,
+                       "tile": [args.tile or 8] * 3, "guard": args.guard or 2,
                        "deposit": "fixed-point" if args.options & 1 else "fp32",
                        "diag_every": args.diag_every,
                        "l2": f"inputs larger than L2 ({32 * N / 1e9:.2f} GB particle store "
