@@ -35,7 +35,8 @@ namespace {
 
 using namespace cic;
 
-template <bool FIXED>
+// B > 0: every tile box is B slots long on each axis (cic::box_row)
+template <bool FIXED, int B>
 __global__ void __launch_bounds__(256, PIC_DEP_MIN_BLOCKS) k_deposit_tiles(Geom g, const Ctrl *__restrict__ ctrl,
                                                            const int4 *__restrict__ items,
                                                            float qscale, float *rho,
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(256, PIC_DEP_MIN_BLOCKS) k_deposit_tiles(Geom 
             }
             int i, j, k;
             if (!decode_cell(c, g, i, j, k)) bad = 1;
-            if (!tile_add<FIXED>(acc, t, g, i, j, k, fx, fy, fz, rho, rho64, qscale)) ++strays;
+            if (!tile_add<FIXED, B>(acc, t, g, i, j, k, fx, fy, fz, rho, rho64, qscale)) ++strays;
         }
         __syncthreads();
         tile_fold<FIXED>(acc, sum, S);
@@ -151,24 +152,27 @@ cudaError_t launch_deposit(int64_t n, const Geom &g, const Ctrl *ctrl, const int
     const size_t smem = tile_deposit_smem(g);   // item tile + the block's tile sums
     const int blocks = grid_blocks < max_items ? grid_blocks : (max_items > 0 ? max_items : 1);
     cudaError_t e;
+    // the default geometry (8^3 tiles, two guard layers) as a constant box
+    bool cbox = true;
+    for (int d = 0; d < 3; ++d) cbox = cbox && g.tile[d] + 2 * g.guard + 1 == 13;
+#define PIC_DT(F, B)                                                                           \
+    do {                                                                                       \
+        if (smem > 48 * 1024 &&                                                                \
+            (e = cudaFuncSetAttribute(k_deposit_tiles<F, B>,                                   \
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,             \
+                                      (int)smem)) != cudaSuccess)                              \
+            return e;                                                                          \
+        k_deposit_tiles<F, B><<<blocks, 256, smem, st>>>(g, ctrl, items, qscale, rho, rho64,   \
+                                                         ctrl_w, sparse_below);                \
+    } while (0)
     if (fixed) {
-        if (smem > 48 * 1024 &&
-            (e = cudaFuncSetAttribute(k_deposit_tiles<true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-                cudaSuccess)
-            return e;
-        k_deposit_tiles<true><<<blocks, 256, smem, st>>>(g, ctrl, items, qscale, rho, rho64,
-                                                         ctrl_w, sparse_below);
+        if (cbox) PIC_DT(true, 13);
+        else PIC_DT(true, 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         return launch_rho_finish(g, rho64, rho, qscale_d, st);
     }
-    if (smem > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(k_deposit_tiles<false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
-        return e;
-    k_deposit_tiles<false><<<blocks, 256, smem, st>>>(g, ctrl, items, qscale, rho, rho64, ctrl_w,
-                                                      sparse_below);
+    PIC_DT(false, 0);
+#undef PIC_DT
     return cudaGetLastError();
 }
 

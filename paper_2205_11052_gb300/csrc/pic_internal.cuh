@@ -118,11 +118,11 @@ constexpr int kMaxSmemPerBlock = 227 * 1024;   // opt-in shared memory per block
 #endif
 // resident blocks per SM of the uniform-plasma move + deposit
 #ifndef PIC_MV_MIN_BLOCKS
-#define PIC_MV_MIN_BLOCKS 3
+#define PIC_MV_MIN_BLOCKS 4
 #endif
 // resident blocks per SM of the split-call deposit
 #ifndef PIC_DEP_MIN_BLOCKS
-#define PIC_DEP_MIN_BLOCKS 3
+#define PIC_DEP_MIN_BLOCKS 4
 #endif
 // read and write page-locked host particle arrays in place (no staging copies)
 #ifndef PIC_ZERO_COPY
