@@ -234,10 +234,11 @@ cudaError_t sort_pass(int64_t n, const Geom &g, int shift, int64_t nb, Ctrl *ctr
 
 // Shifts of the coarse passes that precede the full-key pass for particles in
 // arbitrary order.  Each pass sorts by the next kDigit bits of the tile key
-// (most significant first): a 512-particle slice of pass p spans one or two
-// buckets of pass p - 1, so it meets at most 2^(kDigit + 1) distinct keys
-// (never overflowing the staged table) and writes runs of ~512 / 2^kDigit
-// consecutive particles per key.
+// (most significant first): while the buckets of pass p - 1 hold at least a
+// slice (kStage particles) each, a slice of pass p spans one or two of them,
+// so it meets at most 2^(kDigit + 1) distinct keys (not overflowing the staged
+// table) and writes runs of ~kStage / 2^kDigit consecutive particles per key;
+// a slice that meets more keys takes the scatter's per-warp fallback.
 #ifndef PIC_PRESORT_DIGIT
 #define PIC_PRESORT_DIGIT 4
 #endif
