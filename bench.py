@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1 << 21,
                     help="particles in the oracle's bounded sample")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu-configs", dest="cpu_configs", action="store_false",
+                    help="skip the oracle timings of the other configurations")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
@@ -367,6 +369,45 @@ def cpu_baseline_figures(args, steps=2):
                                           f"in the parent"}
         except Exception as e:   # pragma: no cover - hosts without shared memory
             out["all_cores"] = {"unavailable": str(e)[:200]}
+    if getattr(args, "cpu_configs", True):
+        out["configs"] = cpu_config_figures(cores)
+        out["configs_unit"] = UNIT
+    return out
+
+
+# The survey's configurations for the CPU oracle: the small Landau case, the
+# Landau and Penning cases reduced to a 2M-particle sample, and the adjoint's
+# bump-on-tail case at full size (name, workload factory, timed steps).
+CPU_CONFIGS = [
+    ("landau 16^3 x 8 particles/cell (32,768 particles)",
+     lambda pi: pi.landau(n=16, ppc=8, seed=1000), 5),
+    ("landau 32^3 x 64 particles/cell (2,097,152 particles)",
+     lambda pi: pi.landau(n=32, ppc=64, seed=1001), 1),
+    ("penning 64^3, 2,097,152 particles",
+     lambda pi: pi.penning(n=64, n_particles=1 << 21, seed=1002), 1),
+    ("bump-on-tail 64^3 x 16 particles/cell (4,194,304 particles)",
+     lambda pi: pi.bump_on_tail(n=64, ppc=16, seed=1003), 1),
+]
+
+
+def cpu_config_figures(cores, configs=None):
+    """Single-thread and all-core oracle throughput (particle-steps/s) on each
+    configuration of `configs` (default CPU_CONFIGS)."""
+    import pic_inputs as pi
+
+    out = []
+    for name, make, steps in (configs or CPU_CONFIGS):
+        w = make(pi)
+        one, secs1 = time_oracle(w, steps)
+        ent = {"config": name, "steps": steps, "single": one, "single_s": round(secs1, 2)}
+        if cores > 1:
+            try:
+                allc, secs_a = time_oracle_parallel(w, steps, cores)
+                ent.update({"all_cores": allc, "all_cores_s": round(secs_a, 2)})
+            except Exception as e:   # pragma: no cover - hosts without shared memory
+                ent["all_cores"] = None
+                ent["all_cores_unavailable"] = str(e)[:200]
+        out.append(ent)
     return out
 
 

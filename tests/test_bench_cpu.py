@@ -48,3 +48,18 @@ def test_all_core_oracle_driver_reproduces_the_oracle_step():
     xo, vo, _ = po.run(w.x, w.v, po.Grid(w.n, w.L),
                        po.Params(dt=w.dt, q_over_m=w.q_over_m, Q=w.Q, B=w.B, wz2=w.wz2), 2)
     assert np.max(np.abs(x - xo)) < 1e-12 and np.max(np.abs(v - vo)) < 1e-12
+
+
+def test_cpu_configuration_figures_report_both_oracle_timings():
+    """The per-configuration CPU baseline times the oracle single-threaded and
+    over a process pool on each configuration it is given."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    tiny = [("landau 8^3 x 2", lambda pi: pi.landau(n=8, ppc=2, seed=5), 1),
+            ("penning 8^3, 1000 particles",
+             lambda pi: pi.penning(n=8, n_particles=1000, L=20.0, seed=6), 1)]
+    out = bench.cpu_config_figures(2, tiny)
+    assert [e["config"] for e in out] == [c[0] for c in tiny]
+    for e in out:
+        assert e["steps"] == 1 and e["single"] > 0 and e["all_cores"] > 0
