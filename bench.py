@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the side measurements of the default run (split-call deposit "
                          "roofline, FP32-deposit line, Penning line, 512-instance ensemble)")
+    ap.add_argument("--no-side-lines", action="store_true",
+                    help="skip the FP32-deposit, Penning and ensemble lines but keep the "
+                         "split-call deposit roofline")
     ap.add_argument("--side-steps", type=int, default=10,
                     help="timed steps of each side measurement")
     ap.add_argument("--workload", default="landau",
@@ -971,7 +974,8 @@ def main():
     # this workload, the Penning-trap bunch (256^3, 1.3e8 particles) and the
     # 512-instance batched ensemble
     fp32_line = penning_line = ens_line = None
-    if rank == 0 and world == 1 and not args.no_extras and args.workload == "landau":
+    if (rank == 0 and world == 1 and not args.no_extras and not args.no_side_lines
+            and args.workload == "landau"):
         sim.close()
         sim = None
         torch.cuda.empty_cache()
