@@ -109,7 +109,7 @@ constexpr int kMaxSmemPerBlock = 227 * 1024;   // opt-in shared memory per block
 #define PIC_PD_THREADS 256
 #endif
 #ifndef PIC_PD_WAVES
-#define PIC_PD_WAVES 2
+#define PIC_PD_WAVES 1
 #endif
 // the fused push + deposit gathers E from a shared-memory copy of its tile's
 // box when PIC_PD_MIN_BLOCKS blocks with that copy still fit on an SM
