@@ -400,8 +400,17 @@ int do_diag_finalize(pic_ctx *c, int push_blocks) {
     return timer_end(c, PIC_PHASE_DIAG, 1);
 }
 
+// waves of resident blocks in the grids of the uniform move + deposit and the
+// split-call deposit
+#ifndef PIC_MV_WAVES
+#define PIC_MV_WAVES 1
+#endif
+#ifndef PIC_DEP_WAVES
+#define PIC_DEP_WAVES 1
+#endif
+
 int fused_blocks_of(const pic_ctx *c) {
-    const int per = uniform_move(c) ? PIC_MV_MIN_BLOCKS * 2 : PIC_PD_MIN_BLOCKS * PIC_PD_WAVES;
+    const int per = uniform_move(c) ? PIC_MV_MIN_BLOCKS * PIC_MV_WAVES : PIC_PD_MIN_BLOCKS * PIC_PD_WAVES;
     return (int)std::max<int64_t>(1, std::min<int64_t>(c->max_items, std::min(kMaxPushBlocks, 152 * per)));
 }
 
@@ -874,7 +883,7 @@ int pic_create(const pic_grid_t *grid, const pic_species_t *species, const pic_p
     c->max_items = c->ntiles + (c->cap + c->chunk - 1) / c->chunk + 1;
     c->staging = std::max<int64_t>(1, std::min<int64_t>(c->cap, (int64_t)1 << 22));
     c->sparse_below = 64;
-    c->deposit_blocks = 152 * PIC_DEP_MIN_BLOCKS * 2;   // two waves of the resident blocks
+    c->deposit_blocks = 152 * PIC_DEP_MIN_BLOCKS * PIC_DEP_WAVES;   // waves of the resident blocks
 
     int m[3] = {p.mode[0], p.mode[1], p.mode[2]};
     c->mode_conj = 0;
